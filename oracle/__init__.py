@@ -1,0 +1,133 @@
+"""QuickMergesort oracle: ctypes binding of the single-threaded C++ reference.
+
+TEST INFRASTRUCTURE ONLY.  Only the tests, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this package.  It shares nothing
+with the CUDA library (no headers, helpers or constants) and never imports it.
+
+Paper: Edelkamp & Weiss, "QuickMergesort: Practically Efficient Constant-Factor
+Optimal Sorting" (arXiv 1804.10062).  ``qms_ref.cpp`` cites the sections each
+function follows (QuickXsort skeleton Sec. 2, Fig. 3 listing Sec. 3, MoM and
+hybrid variants Sec. 4, comparison counter Sec. 5).
+
+Parity status: every exported function is pinned by the ``-m "not gpu"``
+tests (exhaustive permutations against the exact-average recurrence derived
+from the proof of Thm. 1, duplicates, Mergesort closed forms, the Cor. 1 band,
+the worst-case bound of Sec. 4, the Fig. 1 worked example and a library sort).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "libqms_oracle.so")
+_SRC = os.path.join(_HERE, "qms_ref.cpp")
+_lock = threading.Lock()
+_lib = None
+
+DTYPES = {"u32": 0, "u64": 1, "i64": 2, "f32": 3}
+NP_DTYPES = {"u32": np.uint32, "u64": np.uint64, "i64": np.int64, "f32": np.float32}
+VARIANTS = {"m3": 0, "sqrtn": 1, "mom": 2, "hybrid": 3}
+MODES = {"analysis": 0, "paper": 1}
+
+
+def build(force: bool = False) -> str:
+    """Compiles qms_ref.cpp into a shared library (plain g++, -O2)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + ".tmp%d" % os.getpid()
+    subprocess.check_call(["g++", "-O2", "-std=c++17", "-shared", "-fPIC",
+                           _SRC, "-o", tmp])
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = ctypes.CDLL(build())
+            u64p = ctypes.POINTER(ctypes.c_uint64)
+            L.qms_ref_sort.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                                       ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                       u64p, u64p]
+            L.qms_ref_sort.restype = ctypes.c_int
+            L.qms_ref_out_u32.argtypes = [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_size_t,
+                                          ctypes.c_size_t, ctypes.c_int, u64p]
+            L.qms_ref_out_u32.restype = ctypes.c_int
+            L.qms_ref_dp.argtypes = [ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p]
+            L.qms_ref_dp.restype = ctypes.c_int
+            L.qms_ref_adversary_u32.argtypes = [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int,
+                                                ctypes.c_int, u64p]
+            L.qms_ref_adversary_u32.restype = ctypes.c_int
+            _lib = L
+    return _lib
+
+
+def _dtype_name(a: np.ndarray) -> str:
+    for k, v in NP_DTYPES.items():
+        if a.dtype == v:
+            return k
+    raise TypeError("unsupported key dtype %s" % a.dtype)
+
+
+def sort(keys: np.ndarray, vals: np.ndarray | None = None, variant: str = "m3",
+         mode: str = "analysis", side: int = 0):
+    """Sorts ``keys`` in place (and ``vals`` with them).
+
+    Returns ``(comparisons, rounds)``.
+    """
+    assert keys.flags.c_contiguous
+    d = _dtype_name(keys)
+    vp = None
+    if vals is not None:
+        assert vals.dtype == np.uint32 and vals.flags.c_contiguous and len(vals) == len(keys)
+        vp = vals.ctypes.data
+    c = ctypes.c_uint64(0)
+    r = ctypes.c_uint64(0)
+    rc = lib().qms_ref_sort(keys.ctypes.data, vp, len(keys), DTYPES[d], VARIANTS[variant],
+                            MODES[mode], side, ctypes.byref(c), ctypes.byref(r))
+    if rc != 0:
+        raise RuntimeError("qms_ref_sort failed: %d" % rc)
+    return c.value, r.value
+
+
+def out_u32(a: np.ndarray, b: int, e: int, temp: int, mode: str = "analysis") -> int:
+    """Fig. 3 ``out``: Mergesorts a[b:e] with the buffer at a[temp:]."""
+    assert a.dtype == np.uint32 and a.flags.c_contiguous
+    c = ctypes.c_uint64(0)
+    rc = lib().qms_ref_out_u32(a.ctypes.data, b, e, temp, MODES[mode], ctypes.byref(c))
+    if rc != 0:
+        raise RuntimeError("qms_ref_out_u32 failed: %d" % rc)
+    return c.value
+
+
+def dp(nmax: int):
+    """Exact-average tables (T, M) for n = 0..nmax (analysis-mode median-of-3)."""
+    T = np.zeros(nmax + 1, dtype=np.float64)
+    M = np.zeros(nmax + 1, dtype=np.float64)
+    rc = lib().qms_ref_dp(nmax, T.ctypes.data, M.ctypes.data)
+    if rc != 0:
+        raise RuntimeError("qms_ref_dp failed")
+    return T, M
+
+
+def adversary_u32(n: int, variant: str = "m3", mode: str = "analysis"):
+    """McIlroy-adversary input (a permutation of 0..n-1) against this oracle.
+
+    Returns ``(keys, comparisons the oracle made on it)``.
+    """
+    a = np.empty(n, dtype=np.uint32)
+    c = ctypes.c_uint64(0)
+    rc = lib().qms_ref_adversary_u32(a.ctypes.data, n, VARIANTS[variant], MODES[mode],
+                                     ctypes.byref(c))
+    if rc != 0:
+        raise RuntimeError("qms_ref_adversary_u32 failed")
+    return a, c.value

@@ -1,0 +1,562 @@
+// QuickMergesort oracle (Edelkamp & Weiss, "QuickMergesort: Practically
+// Efficient Constant-Factor Optimal Sorting", arXiv 1804.10062).
+//
+// TEST INFRASTRUCTURE ONLY.  This file is the plain, slow, single-threaded
+// reference that the CUDA path is checked against.  Only the tests, the
+// smoke check and the CPU-baseline leg of the benchmark may load it.  It
+// shares no code, header, table or helper with the CUDA library.
+//
+// What it computes (paper sections in brackets):
+//   * QuickXsort skeleton with X = Mergesort [Sec. 2]: choose a pivot,
+//     partition, sort one side with Mergesort using the other side as the
+//     swap buffer, continue on the remaining side.
+//   * merge / msort / out / sort as in the C++ implementation figure of
+//     Sec. 3 (Fig. 3), with two corrections:
+//       - msort for odd n uses r = n - floor(n/2) slots for the first half
+//         target (the printed version reads a buffer element as data);
+//       - merge does not read one slot past its target range on its last
+//         step (the printed version reads, then overwrites, that slot).
+//   * Pivot rules: median-of-3 [Sec. 2, proof of Thm. 1], median-of-sqrt(n)
+//     [Sec. 2, Thm. 2], MoMQuickMergesort (median of the n/3 medians of
+//     three, found with the groups-of-five median-of-medians selection)
+//     [Sec. 4], HybridQuickMergesort with delta = 1/16 [Sec. 4].
+//   * An element-comparison counter [Sec. 5]: every call of the order
+//     predicate adds one.
+//
+// Readings of points the paper leaves open (each also listed in the design
+// notes of the repository):
+//   * Median-of-3 samples positions b, b + floor(n/2), e - 1.  sort3 compares
+//     (mid, lo), then (hi, mid) and, only if that swapped, (mid, lo) again.
+//     The pivot is parked at b + 1 and the n - 3 non-sample elements are
+//     partitioned with one comparison each (Lomuto movement), so one round
+//     costs sort3 + (n - 3) comparisons as in the proof of Thm. 1.
+//   * The driver partitions only ranges of >= 3 elements; a range of 2 gets
+//     one compare-and-swap.  Side choice follows Fig. 3: Mergesort the left
+//     side iff the pivot index is below the integer midpoint.
+//   * "paper" mode adds what the experiments describe but the listing omits:
+//     insertion sort below 10 elements (driver and msort leaves) and a
+//     duplicate guard (a tie between the pivot and a neighbouring sample
+//     switches the round to a three-way partition whose equal block is
+//     final).  "analysis" mode is the listing alone (leaf n <= 1).
+//   * Median-of-sqrt(n): k = largest odd number <= ceil(sqrt n), samples at
+//     b + i * floor(n/k), moved to the front and sorted by this same sort.
+//   * MoM: triples (3i, 3i+1, 3i+2), i < floor(n/3), medians moved to slot
+//     b + i; median of medians by groups-of-five selection (6-comparison
+//     median of five); all n - 1 other elements are compared with the pivot.
+//     MoM rounds Mergesort the larger side when its ceil(m/2) buffer fits
+//     in the smaller side, else the smaller side.
+//   * HQMS: a median-of-3 pivot whose rank inside the current range lies
+//     outside [floor(n/16), n - 1 - floor(n/16)] makes the next round MoM;
+//     the round after that is median-of-3 again.
+//   * Key order: ascending; float keys use IEEE order with -0 < +0 (NaN is
+//     never generated); int64 is signed.
+
+#include <algorithm>
+#include <cmath>
+#include <cstddef>
+#include <cstdint>
+#include <cstring>
+#include <utility>
+#include <vector>
+
+namespace {
+
+enum Variant { M3 = 0, SQRTN = 1, MOM = 2, HYBRID = 3 };
+enum Mode { ANALYSIS = 0, PAPER = 1 };
+
+// ---- plain order predicates on the raw key types -------------------------
+
+struct LessU32 {
+  bool operator()(uint32_t x, uint32_t y) const { return x < y; }
+};
+struct LessU64 {
+  bool operator()(uint64_t x, uint64_t y) const { return x < y; }
+};
+struct LessI64 {
+  bool operator()(int64_t x, int64_t y) const { return x < y; }
+};
+struct LessF32 {
+  // IEEE "<" for non-NaN values, with -0 ordered before +0.
+  bool operator()(float x, float y) const {
+    if (x < y) return true;
+    if (y < x) return false;
+    return std::signbit(x) && !std::signbit(y);
+  }
+};
+
+// An element is a key, or a (key, payload) pair moved as one unit.
+template <class K>
+struct Pair {
+  K key;
+  uint32_t val;
+};
+
+template <class K, class KLess>
+struct ByKey {
+  KLess kl;
+  bool operator()(const K& x, const K& y) const { return kl(x, y); }
+  bool operator()(const Pair<K>& x, const Pair<K>& y) const {
+    return kl(x.key, y.key);
+  }
+};
+
+struct Split {
+  size_t lt, gt;  // [b,lt) left side, [lt,gt) pivot block, [gt,e) right side
+  bool mom;       // the round used a MoM pivot
+};
+
+template <class E, class Less>
+class QuickMergesort {
+ public:
+  QuickMergesort(E* a, Less less, int variant, int mode, int side)
+      : a_(a), less_(less), variant_(variant), mode_(mode), side_(side) {}
+
+  uint64_t comparisons() const { return cmps_; }
+  uint64_t rounds() const { return rounds_; }
+
+  // Sorts a[b, e) ascending.
+  void sort(size_t b, size_t e) {
+    bool mom_next = false;
+    const size_t stop = (mode_ == PAPER) ? 10 : 3;
+    while (e - b >= stop) {
+      ++rounds_;
+      const size_t n = e - b;
+      const bool mom_round =
+          variant_ == MOM || (variant_ == HYBRID && mom_next);
+      Split s;
+      if (variant_ == SQRTN) {
+        s = partition_sqrtn(b, e);
+      } else if (mom_round) {
+        s = partition_mom(b, e);
+      } else {
+        s = partition_m3(b, e);
+      }
+      if (variant_ == HYBRID) {
+        // Rank of the pivot block inside [b, e), 0-based.
+        const size_t d = n / 16;
+        const size_t r_lo = s.lt - b, r_hi = s.gt - 1 - b;
+        mom_next = !mom_round && (r_hi < d || r_lo > n - 1 - d);
+      }
+      const size_t nl = s.lt - b, nr = e - s.gt;
+      bool left;
+      if (s.mom || side_ == 1) {
+        // Larger side if its ceil(m/2) buffer fits in the other side.
+        const size_t big = std::max(nl, nr), small = std::min(nl, nr);
+        const bool big_fits = (big + 1) / 2 <= small;
+        left = big_fits ? (nl >= nr) : (nl < nr);
+      } else if (s.gt == s.lt + 1) {
+        // Fig. 3: Mergesort the left side iff the pivot is left of the
+        // integer midpoint.
+        left = s.lt < (b + e) / 2;
+      } else {
+        left = nl <= nr;  // three-way split: the smaller side
+      }
+      if (left) {
+        out(b, s.lt, s.gt);
+        b = s.gt;
+      } else {
+        out(s.gt, e, b);
+        e = s.lt;
+      }
+    }
+    if (mode_ == PAPER) {
+      insertion_sort(b, e);
+    } else if (e - b == 2) {
+      if (lt(a_[b + 1], a_[b])) std::swap(a_[b], a_[b + 1]);
+    }
+  }
+
+  // Internal Mergesort of a[b, e) using the ceil(n/2) slots at a[temp, ...)
+  // as swap buffer (Fig. 3, "out").  Buffer contents are permuted.
+  void out(size_t b, size_t e, size_t temp) {
+    const size_t n = e - b;
+    if (n > 1) {
+      const size_t q = n / 2, r = n - q;
+      msort(b + q, e, temp);
+      msort(b, b + q, b + r);
+      merge(temp, temp + r, b, e);
+    }
+  }
+
+ private:
+  bool lt(const E& x, const E& y) {
+    ++cmps_;
+    return less_(x, y);
+  }
+
+  // Fig. 3 "merge": run1 = a[b1, e1) (in the buffer), run2 sits at the tail
+  // of the target range a[t, et); the first (e1 - b1) target slots hold
+  // buffer elements.  One hole (temp) carries a buffer element; buffer
+  // elements end in run1's slots.
+  void merge(size_t b1, size_t e1, size_t t, size_t et) {
+    size_t i1 = b1, i2 = t + (e1 - b1), r = t;
+    E temp = a_[t];
+    while (i1 != e1 && i2 != et) {
+      size_t src = lt(a_[i1], a_[i2]) ? i1++ : i2++;
+      a_[r++] = a_[src];
+      a_[src] = a_[r];
+    }
+    while (i1 < e1) {
+      a_[r++] = a_[i1];
+      if (r != et) a_[i1] = a_[r];  // the printed loop reads a[et] here
+      ++i1;
+    }
+    a_[i1 - 1] = temp;
+  }
+
+  // Fig. 3 "msort": sorts a[b, e) into a[t, t + n); the old target contents
+  // end up in a[b, e).  r = n - floor(n/2) is used for the odd case.
+  void msort(size_t b, size_t e, size_t t) {
+    const size_t n = e - b;
+    const size_t leaf = (mode_ == PAPER) ? 10 : 2;
+    if (n < leaf) {
+      if (mode_ == PAPER) insertion_sort(b, e);
+      for (size_t i = 0; i < n; ++i) std::swap(a_[b + i], a_[t + i]);
+      return;
+    }
+    const size_t q = n / 2, r = n - q;
+    msort(b + q, e, t + q);
+    msort(b, b + q, b + r);
+    merge(b + r, b + n, t, t + n);
+  }
+
+  void insertion_sort(size_t b, size_t e) {
+    for (size_t i = b + 1; i < e; ++i) {
+      E x = a_[i];
+      size_t j = i;
+      while (j > b && lt(x, a_[j - 1])) {
+        a_[j] = a_[j - 1];
+        --j;
+      }
+      a_[j] = x;
+    }
+  }
+
+  // Lomuto partition of a[from, to) around the pivot parked at a[p]:
+  // elements less than the pivot are moved to a[from, i).  Returns i.
+  size_t lomuto(size_t p, size_t from, size_t to) {
+    size_t i = from;
+    for (size_t j = from; j < to; ++j) {
+      if (lt(a_[j], a_[p])) {
+        std::swap(a_[i], a_[j]);
+        ++i;
+      }
+    }
+    return i;
+  }
+
+  // Three-way partition of a[b, e) around the value v (Dijkstra): at most
+  // two comparisons per element.
+  Split three_way(size_t b, size_t e, E v) {
+    size_t l = b, i = b, g = e;
+    while (i < g) {
+      if (lt(a_[i], v)) {
+        std::swap(a_[l++], a_[i++]);
+      } else if (lt(v, a_[i])) {
+        std::swap(a_[i], a_[--g]);
+      } else {
+        ++i;
+      }
+    }
+    return Split{l, g, false};
+  }
+
+  // Two-way partition with the pivot at a[b]: the other n - 1 elements are
+  // compared once each; the pivot ends at its final index k.
+  Split two_way_front(size_t b, size_t e) {
+    size_t i = lomuto(b, b + 1, e);
+    std::swap(a_[b], a_[i - 1]);
+    return Split{i - 1, i, false};
+  }
+
+  // sort3 on positions lo, mid, hi; afterwards a[lo] <= a[mid] <= a[hi].
+  void sort3(size_t lo, size_t mid, size_t hi) {
+    if (lt(a_[mid], a_[lo])) std::swap(a_[mid], a_[lo]);
+    if (lt(a_[hi], a_[mid])) {
+      std::swap(a_[hi], a_[mid]);
+      if (lt(a_[mid], a_[lo])) std::swap(a_[mid], a_[lo]);
+    }
+  }
+
+  Split partition_m3(size_t b, size_t e) {
+    const size_t n = e - b, m = b + n / 2;
+    sort3(b, m, e - 1);
+    if (mode_ == PAPER) {
+      // Duplicate guard: a tie between the pivot and a neighbouring sample
+      // selects a three-way partition.
+      const bool strict = lt(a_[b], a_[m]) && lt(a_[m], a_[e - 1]);
+      if (!strict) return three_way(b, e, a_[m]);
+    }
+    std::swap(a_[m], a_[b + 1]);
+    size_t i = lomuto(b + 1, b + 2, e - 1);
+    std::swap(a_[b + 1], a_[i - 1]);
+    return Split{i - 1, i, false};
+  }
+
+  Split partition_sqrtn(size_t b, size_t e) {
+    const size_t n = e - b;
+    size_t c = static_cast<size_t>(std::sqrt(static_cast<double>(n)));
+    while (c * c < n) ++c;
+    while (c > 1 && (c - 1) * (c - 1) >= n) --c;  // c = ceil(sqrt(n))
+    size_t k = (c % 2 == 1) ? c : c - 1;
+    if (k == 0) k = 1;
+    const size_t step = n / k;
+    for (size_t i = 0; i < k; ++i) std::swap(a_[b + i], a_[b + i * step]);
+    // Sort the sample with this same algorithm (counted).
+    QuickMergesort inner(a_, less_, variant_, mode_, side_);
+    inner.sort(b, b + k);
+    cmps_ += inner.comparisons();
+    const size_t pm = b + k / 2;
+    if (mode_ == PAPER && k >= 3) {
+      const bool strict = lt(a_[pm - 1], a_[pm]) && lt(a_[pm], a_[pm + 1]);
+      if (!strict) return three_way(b, e, a_[pm]);
+    }
+    std::swap(a_[b], a_[pm]);
+    return two_way_front(b, e);
+  }
+
+  // Median of a[p0], a[p1], a[p2] with at most 3 comparisons; returns its
+  // position.
+  size_t median3_pos(size_t p0, size_t p1, size_t p2) {
+    if (lt(a_[p1], a_[p0])) std::swap(p0, p1);  // now a[p0] <= a[p1]
+    if (lt(a_[p2], a_[p1])) {
+      return lt(a_[p2], a_[p0]) ? p0 : p2;
+    }
+    return p1;
+  }
+
+  // Median of the five elements at a[b, b+5) with 6 comparisons; returns
+  // its position.
+  size_t median5_pos(size_t b) {
+    size_t p[5] = {b, b + 1, b + 2, b + 3, b + 4};
+    auto L = [&](size_t i, size_t j) { return lt(a_[p[i]], a_[p[j]]); };
+    if (L(1, 0)) std::swap(p[0], p[1]);  // p0 <= p1
+    if (L(3, 2)) std::swap(p[2], p[3]);  // p2 <= p3
+    if (L(2, 0)) {                       // make p0 the minimum of the four
+      std::swap(p[0], p[2]);
+      std::swap(p[1], p[3]);
+    }
+    // p0 is below p1, p2, p3 so it is not the median; the median is the
+    // second smallest of {p1, p2, p3, p4}, where p2 <= p3.
+    if (L(4, 1)) std::swap(p[1], p[4]);  // p1 <= p4
+    if (L(2, 1)) {                       // p2 is the minimum of the four
+      return L(3, 1) ? p[3] : p[1];
+    }
+    return L(4, 2) ? p[4] : p[2];  // p1 is the minimum of the four
+  }
+
+  // Groups-of-five selection (median of medians): rearranges a[b, e) and
+  // returns the position of an element of rank i (0-based) in it.
+  size_t select(size_t b, size_t e, size_t i) {
+    while (true) {
+      const size_t n = e - b;
+      if (n <= 5) {
+        insertion_sort(b, e);
+        return b + i;
+      }
+      const size_t g = n / 5;
+      for (size_t j = 0; j < g; ++j) {
+        std::swap(a_[b + j], a_[median5_pos(b + 5 * j)]);
+      }
+      const size_t mm = select(b, b + g, g / 2);
+      std::swap(a_[b], a_[mm]);
+      Split s = three_way(b, e, a_[b]);
+      if (i < s.lt - b) {
+        e = s.lt;
+      } else if (i < s.gt - b) {
+        return b + i;
+      } else {
+        i -= s.gt - b;
+        b = s.gt;
+      }
+    }
+  }
+
+  Split partition_mom(size_t b, size_t e) {
+    const size_t n = e - b, t = n / 3;
+    for (size_t i = 0; i < t; ++i) {
+      const size_t p = median3_pos(b + 3 * i, b + 3 * i + 1, b + 3 * i + 2);
+      std::swap(a_[b + i], a_[p]);
+    }
+    const size_t mm = select(b, b + t, t / 2);
+    std::swap(a_[b], a_[mm]);
+    Split s = (mode_ == PAPER) ? three_way(b, e, a_[b]) : two_way_front(b, e);
+    s.mom = true;
+    return s;
+  }
+
+  E* a_;
+  Less less_;
+  int variant_, mode_, side_;
+  uint64_t cmps_ = 0;
+  uint64_t rounds_ = 0;
+};
+
+template <class K, class KLess>
+int sort_typed(void* keys, uint32_t* vals, size_t n, int variant, int mode,
+               int side, uint64_t* cmps, uint64_t* rounds) {
+  using Less = ByKey<K, KLess>;
+  K* k = static_cast<K*>(keys);
+  uint64_t c = 0, r = 0;
+  if (vals == nullptr) {
+    QuickMergesort<K, Less> s(k, Less{}, variant, mode, side);
+    if (n > 1) s.sort(0, n);
+    c = s.comparisons();
+    r = s.rounds();
+  } else {
+    std::vector<Pair<K>> e(n);
+    for (size_t i = 0; i < n; ++i) e[i] = Pair<K>{k[i], vals[i]};
+    QuickMergesort<Pair<K>, Less> s(e.data(), Less{}, variant, mode, side);
+    if (n > 1) s.sort(0, n);
+    for (size_t i = 0; i < n; ++i) {
+      k[i] = e[i].key;
+      vals[i] = e[i].val;
+    }
+    c = s.comparisons();
+    r = s.rounds();
+  }
+  if (cmps) *cmps = c;
+  if (rounds) *rounds = r;
+  return 0;
+}
+
+// McIlroy's adversary ("a killer adversary for quicksort", 1999), written
+// here from its published description: every element starts as "gas"
+// (larger than all solid values); when two gas elements meet, the current
+// pivot candidate is frozen to the next solid value.  Run against this
+// oracle it yields an input on which that exact sort variant performs
+// badly.
+struct Adversary {
+  std::vector<uint32_t> val;
+  uint32_t gas, nsolid = 0;
+  size_t candidate = 0;
+  explicit Adversary(size_t n) : val(n, static_cast<uint32_t>(n)), gas(static_cast<uint32_t>(n)) {}
+  void freeze(uint32_t x) { val[x] = nsolid++; }
+};
+
+struct AdversaryLess {
+  Adversary* adv;
+  bool operator()(uint32_t x, uint32_t y) const {
+    Adversary& A = *adv;
+    if (A.val[x] == A.gas && A.val[y] == A.gas) {
+      if (x == A.candidate) {
+        A.freeze(x);
+      } else {
+        A.freeze(y);
+      }
+    }
+    if (A.val[x] == A.gas) {
+      A.candidate = x;
+    } else if (A.val[y] == A.gas) {
+      A.candidate = y;
+    }
+    return A.val[x] < A.val[y];
+  }
+};
+
+}  // namespace
+
+extern "C" {
+
+// dtype: 0 = uint32, 1 = uint64, 2 = int64, 3 = float32.
+// variant: 0 = median-of-3, 1 = median-of-sqrt(n), 2 = MoM, 3 = hybrid.
+// mode: 0 = analysis (Fig. 3 alone), 1 = paper (base cases + duplicate guard).
+// side: 0 = Fig. 3 (Mergesort the side left of the midpoint test),
+//       1 = larger side whenever its buffer fits.
+// vals: NULL for key-only sorts, else payloads moved with their keys.
+int qms_ref_sort(void* keys, uint32_t* vals, size_t n, int dtype, int variant,
+                 int mode, int side, uint64_t* cmps, uint64_t* rounds) {
+  if (keys == nullptr && n > 0) return -1;
+  if (variant < 0 || variant > 3 || mode < 0 || mode > 1) return -1;
+  switch (dtype) {
+    case 0:
+      return sort_typed<uint32_t, LessU32>(keys, vals, n, variant, mode, side, cmps, rounds);
+    case 1:
+      return sort_typed<uint64_t, LessU64>(keys, vals, n, variant, mode, side, cmps, rounds);
+    case 2:
+      return sort_typed<int64_t, LessI64>(keys, vals, n, variant, mode, side, cmps, rounds);
+    case 3:
+      return sort_typed<float, LessF32>(keys, vals, n, variant, mode, side, cmps, rounds);
+    default:
+      return -1;
+  }
+}
+
+// Mergesort alone (Fig. 3 "out"): sorts a[b, e) using the ceil((e-b)/2)
+// slots a[temp, ...) as swap buffer; the buffer contents are permuted.  The
+// buffer must not overlap [b, e).
+int qms_ref_out_u32(uint32_t* a, size_t b, size_t e, size_t temp, int mode,
+                    uint64_t* cmps) {
+  if (a == nullptr || e < b) return -1;
+  const size_t r = (e - b) - (e - b) / 2;
+  if (temp < e && temp + r > b) return -1;
+  using Less = ByKey<uint32_t, LessU32>;
+  QuickMergesort<uint32_t, Less> s(a, Less{}, M3, mode, 0);
+  s.out(b, e, temp);
+  if (cmps) *cmps = s.comparisons();
+  return 0;
+}
+
+// Exact average comparisons of the analysis-mode median-of-3 sort on
+// random permutations of distinct keys, derived from the proof of Thm. 1:
+// Pr[pivot rank = k] = (k-1)(n-k)/C(n,3), partitioning keeps both sides
+// uniformly random, and the Mergesort of m elements costs M(m) on average
+// with M(n) = M(floor(n/2)) + M(ceil(n/2)) + E(floor(n/2), ceil(n/2)),
+// E(a, b) = a + b - a/(b+1) - b/(a+1) (expected comparisons of a merge
+// that stops when one run is exhausted).  Fills T[0..nmax], M[0..nmax].
+int qms_ref_dp(size_t nmax, double* T, double* M) {
+  if (T == nullptr || M == nullptr) return -1;
+  for (size_t n = 0; n <= nmax; ++n) {
+    if (n <= 1) {
+      M[n] = 0.0;
+      continue;
+    }
+    const double a = static_cast<double>(n / 2), b = static_cast<double>(n - n / 2);
+    M[n] = M[n / 2] + M[n - n / 2] + a + b - a / (b + 1.0) - b / (a + 1.0);
+  }
+  for (size_t n = 0; n <= nmax; ++n) {
+    if (n <= 1) {
+      T[n] = 0.0;
+      continue;
+    }
+    if (n == 2) {
+      T[n] = 1.0;
+      continue;
+    }
+    const double nd = static_cast<double>(n);
+    const double c3 = nd * (nd - 1.0) * (nd - 2.0) / 6.0;
+    double s = 0.0;
+    for (size_t k = 1; k <= n; ++k) {
+      const double w = static_cast<double>(k - 1) * static_cast<double>(n - k);
+      if (w == 0.0) continue;
+      const double rest = (k - 1 < n / 2) ? (M[k - 1] + T[n - k]) : (M[n - k] + T[k - 1]);
+      s += w * rest;
+    }
+    T[n] = 8.0 / 3.0 + (nd - 3.0) + s / c3;
+  }
+  return 0;
+}
+
+// Builds an input of n distinct uint32 keys (a permutation of 0..n-1) by
+// running McIlroy's adversary against this oracle's sort with the given
+// variant and mode.  Returns the comparisons the sort made on it.
+int qms_ref_adversary_u32(uint32_t* out, size_t n, int variant, int mode,
+                          uint64_t* cmps) {
+  if (out == nullptr && n > 0) return -1;
+  Adversary adv(n);
+  std::vector<uint32_t> ids(n);
+  for (size_t i = 0; i < n; ++i) ids[i] = static_cast<uint32_t>(i);
+  AdversaryLess less{&adv};
+  QuickMergesort<uint32_t, AdversaryLess> s(ids.data(), less, variant, mode, 0);
+  if (n > 1) s.sort(0, n);
+  // Elements never frozen keep their relative gas order: freeze them now in
+  // index order so that the result is a permutation.
+  for (size_t i = 0; i < n; ++i) {
+    if (adv.val[i] == adv.gas) adv.freeze(static_cast<uint32_t>(i));
+  }
+  for (size_t i = 0; i < n; ++i) out[i] = adv.val[i];
+  if (cmps) *cmps = s.comparisons();
+  return 0;
+}
+
+}  // extern "C"
