@@ -1,0 +1,125 @@
+/* qms.h -- C ABI of the GB300 QuickMergesort library (libqms.so).
+ *
+ * The method is QuickMergesort (Edelkamp & Weiss, "QuickMergesort: Practically
+ * Efficient Constant-Factor Optimal Sorting", arXiv 1804.10062): choose a
+ * pivot (median-of-3, median-of-sqrt(n), median of medians, or the hybrid of
+ * Sec. 4), partition the array in place, Mergesort one side using the other
+ * side as a swap buffer (buffer elements are permuted, never overwritten),
+ * and continue on the remaining side (Sec. 2 and the Fig. 3 listing).  The
+ * problem statement is internal sorting: n elements, ascending, with only
+ * O(log n) extra words beyond the array (Sec. 1).  On the GPU the extra
+ * memory is O(n / 8192 + 1) words (one counter per 8192-key tile).
+ *
+ * Conventions for every call:
+ *   - Key and payload pointers are DEVICE pointers owned by the caller; sorts
+ *     are in place and ascending.  Keys: uint32, uint64, int64 (signed order)
+ *     or float32 (IEEE order with -0 < +0; NaN keys are not supported).
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls are stream-ordered; unless stated otherwise a call
+ *     returns after its work on `stream` has finished.
+ *   - Return value: QMS_OK (0) or a negative QMS_E* code.  Nothing aborts,
+ *     traps or exits.  n = 0 and n = 1 are valid no-ops.
+ *   - `opt` may be NULL (median-of-3, no counting).  `stats` may be NULL.
+ */
+#ifndef QMS_H_
+#define QMS_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Error codes. */
+#define QMS_OK 0
+#define QMS_EINVAL (-1)   /* null pointer, bad dtype/pivot, size out of range */
+#define QMS_ENOMEM (-2)   /* device workspace could not be allocated         */
+#define QMS_EBUDGET (-3)  /* server: request larger than the HBM budget      */
+#define QMS_ECUDA (-4)    /* a CUDA runtime call or kernel launch failed      */
+#define QMS_ETIMEOUT (-5) /* a bounded device or host wait gave up            */
+#define QMS_EAGAIN (-6)   /* server poll: request not finished yet            */
+#define QMS_EINTERNAL (-7)/* a device-side consistency check failed          */
+
+/* Key types (dtype arguments). */
+#define QMS_U32 0
+#define QMS_U64 1
+#define QMS_I64 2
+#define QMS_F32 3
+
+/* Pivot rules (qms_options.pivot).
+ *   M3     : median of positions b, b + floor(n/2), e - 1 (Sec. 2, Thm. 1).
+ *   SQRTN  : median of an evenly spaced sample of the largest odd k <=
+ *            ceil(sqrt n) elements, k capped at 8191 (Sec. 2, Thm. 2).
+ *   MOM    : exact median of the floor(n/3) medians of consecutive triples
+ *            (MoMQuickMergesort, Sec. 4; the selection is a radix select).
+ *   HYBRID : M3, but a pivot whose rank lies outside [n/16, n - 1 - n/16]
+ *            makes the next round MOM (HybridQuickMergesort, Sec. 4). */
+#define QMS_PIVOT_M3 0
+#define QMS_PIVOT_SQRTN 1
+#define QMS_PIVOT_MOM 2
+#define QMS_PIVOT_HYBRID 3
+
+typedef struct {
+  int pivot;       /* QMS_PIVOT_*                                              */
+  int count_cmps;  /* nonzero: use the counting kernels and report
+                      qms_stats.comparisons (element comparisons, Sec. 5)      */
+  int reserved0;
+  int reserved1;
+} qms_options;
+
+typedef struct {
+  uint64_t comparisons; /* element comparisons made (count_cmps only)          */
+  uint64_t aux_bytes;   /* device workspace used (O(n/8192 + 1) words)          */
+  uint64_t rounds;      /* partition rounds                                      */
+  uint64_t mom_rounds;  /* rounds that used a median-of-medians pivot            */
+  uint64_t launches;    /* kernels launched                                      */
+  double ms;            /* host wall time of the call                            */
+} qms_stats;
+
+/* Library version (major * 10000 + minor * 100 + patch). */
+int qms_version(void);
+/* Static string for an error code. */
+const char* qms_error_string(int code);
+
+/* Sorts d_keys[0, n) in place, ascending (the QuickMergesort driver loop of
+ * Fig. 3: partition, Mergesort the side left of the midpoint test, continue
+ * on the other side; ranges of at most 8192 keys are finished by the base
+ * case).  Errors: QMS_EINVAL (d_keys NULL with n > 1, bad dtype or pivot),
+ * QMS_ENOMEM, QMS_ECUDA, QMS_EINTERNAL. */
+int qms_sort(void* d_keys, size_t n, int dtype, const qms_options* opt, void* stream,
+             qms_stats* stats);
+
+/* As qms_sort, and moves the uint32 payload d_vals[i] with key d_keys[i].
+ * The order among equal keys is unspecified (QuickMergesort is not stable);
+ * the (key, payload) multiset is preserved.  n must be < 2^32. */
+int qms_sort_pairs(void* d_keys, uint32_t* d_vals, size_t n, int dtype, const qms_options* opt,
+                   void* stream, qms_stats* stats);
+
+/* ---- Step-level entry points (one step of a round each; used by the
+ * ---- parity tests of the individual kernels). ------------------------- */
+
+/* Base case X (Fig. 3 msort leaf): sorts d_keys[0, n), n <= 8192, in one
+ * thread block (d_vals may be NULL). */
+int qms_tile_sort(void* d_keys, uint32_t* d_vals, size_t n, int dtype, void* stream);
+
+/* One partition step (Sec. 2): chooses a pivot of d_keys[0, n) (n >= 3) with
+ * rule `pivot`, partitions in place and writes the pivot's final index to
+ * *k_out and the number of further keys equal to the pivot placed right
+ * after it to *eq_out (nonzero only when the duplicate guard ran the second
+ * pass).  Afterwards keys[0, k) < pivot, keys[k, k + 1 + eq) == pivot and
+ * keys[k + 1 + eq, n) >= pivot (> pivot when eq was computed). */
+int qms_partition(void* d_keys, uint32_t* d_vals, size_t n, int dtype, int pivot, void* stream,
+                  uint64_t* k_out, uint64_t* eq_out);
+
+/* Mergesort with a swap buffer (Fig. 3 "out", in its full-buffer form):
+ * sorts d_keys[0, m) using the m slots d_keys[buf, buf + m) as buffer
+ * (buf >= m, so the regions are disjoint); the buffer's multiset is preserved
+ * and its order permuted. */
+int qms_mergesort(void* d_keys, uint32_t* d_vals, size_t m, size_t buf, int dtype, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QMS_H_ */

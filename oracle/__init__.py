@@ -131,3 +131,24 @@ def adversary_u32(n: int, variant: str = "m3", mode: str = "analysis"):
     if rc != 0:
         raise RuntimeError("qms_ref_adversary_u32 failed")
     return a, c.value
+
+
+def reference_sorted(keys: np.ndarray) -> np.ndarray:
+    """The plain definition of the result (Sec. 1: the ascending order of the
+    input; floats in IEEE order with -0 before +0).  The ascending order is
+    unique, so any correct sort equals it byte for byte."""
+    if keys.dtype == np.float32:
+        order = np.lexsort((~np.signbit(keys), keys))
+        return keys[order]
+    return np.sort(keys, kind="stable")
+
+
+def canonical_pairs(keys: np.ndarray, vals: np.ndarray):
+    """(key, payload) pairs sorted by key order, then payload: the canonical
+    form used to compare key-value results whose order among equal keys is
+    not fixed (QuickMergesort is not stable)."""
+    if keys.dtype == np.float32:
+        order = np.lexsort((vals, ~np.signbit(keys), keys))
+    else:
+        order = np.lexsort((vals, keys))
+    return keys[order], vals[order]

@@ -1,0 +1,517 @@
+// Device primitives of the GB300 QuickMergesort path (sm_103a).
+//
+// Paper: Edelkamp & Weiss, "QuickMergesort: Practically Efficient
+// Constant-Factor Optimal Sorting", arXiv 1804.10062.
+//
+// Every routine here is CTA-scoped: one thread block works on one tile, and
+// the kernels in qms_kernels.cuh either spread tiles over a grid or loop over
+// them inside one block.  Keys are moved in their raw bit pattern and
+// compared as unsigned "order keys" (a bijection computed in registers):
+//   uint32 / uint64 : identity
+//   int64           : flip the sign bit
+//   float32         : IEEE totalOrder bits (negative: all bits flipped;
+//                     non-negative: sign bit set), so -0 < +0.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace qms {
+
+constexpr int NT = 512;          // threads per block
+constexpr int V = 16;            // items per thread
+constexpr int TILE = NT * V;     // keys per tile (leaf, partition, merge)
+constexpr int NWARP = NT / 32;
+
+enum : int { XF_NONE = 0, XF_F32 = 1, XF_I64 = 2 };
+
+// ---------------------------------------------------------------------------
+// Order keys
+
+__device__ __forceinline__ uint32_t enc_key(uint32_t b, int xf) {
+  if (xf == XF_F32) return b ^ (static_cast<uint32_t>(static_cast<int32_t>(b) >> 31) | 0x80000000u);
+  return b;
+}
+__device__ __forceinline__ uint32_t dec_key(uint32_t u, int xf) {
+  if (xf == XF_F32) return u ^ (((u >> 31) - 1u) | 0x80000000u);
+  return u;
+}
+__device__ __forceinline__ uint64_t enc_key(uint64_t b, int xf) {
+  return xf == XF_I64 ? (b ^ 0x8000000000000000ull) : b;
+}
+__device__ __forceinline__ uint64_t dec_key(uint64_t u, int xf) {
+  return xf == XF_I64 ? (u ^ 0x8000000000000000ull) : u;
+}
+
+template <class K>
+__device__ __forceinline__ K key_max() {
+  return static_cast<K>(~static_cast<K>(0));
+}
+
+// Shared-memory index with one padding element per 128 bytes, so that the
+// blocked (thread-contiguous) accesses of the sort do not conflict on banks.
+template <class K>
+__device__ __forceinline__ int sk_i(int i) {
+  return i + i / (128 / static_cast<int>(sizeof(K)));
+}
+__device__ __forceinline__ int sv_i(int i) { return i + (i >> 5); }
+
+template <class K>
+__host__ __device__ constexpr int sk_len() {
+  return TILE + TILE / (128 / static_cast<int>(sizeof(K))) + 4;
+}
+__host__ __device__ constexpr int sv_len() { return TILE + TILE / 32 + 4; }
+
+// Scratch words used by block scans and small per-block tables.
+constexpr int SCRATCH_WORDS = 64;
+
+template <class K, bool HV>
+__host__ __device__ constexpr size_t tile_smem_bytes() {
+  return static_cast<size_t>(sk_len<K>()) * sizeof(K) +
+         (HV ? static_cast<size_t>(sv_len()) * 4 : 0) + SCRATCH_WORDS * 8;
+}
+
+template <class K, bool HV>
+struct TileSmem {
+  K* k;
+  uint32_t* v;
+  uint32_t* scratch;  // SCRATCH_WORDS * 2 uint32 words
+  __device__ __forceinline__ static TileSmem carve(unsigned char* base) {
+    TileSmem s;
+    s.k = reinterpret_cast<K*>(base);
+    size_t off = static_cast<size_t>(sk_len<K>()) * sizeof(K);
+    s.v = HV ? reinterpret_cast<uint32_t*>(base + off) : nullptr;
+    if (HV) off += static_cast<size_t>(sv_len()) * 4;
+    s.scratch = reinterpret_cast<uint32_t*>(base + off);
+    return s;
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Block-wide scans (NT threads)
+
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  return x;
+}
+
+// Exclusive scan of x over the block; *total receives the block sum.
+// scratch needs NWARP + 1 words.  Contains __syncthreads.
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t x, uint32_t* scratch,
+                                                    uint32_t* total) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const uint32_t inc = warp_incl_scan(x);
+  if (lane == 31) scratch[w] = inc;
+  __syncthreads();
+  if (w == 0) {
+    const uint32_t s = lane < NWARP ? scratch[lane] : 0u;
+    const uint32_t si = warp_incl_scan(s);
+    if (lane < NWARP) scratch[lane] = si - s;
+    if (lane == 31) scratch[NWARP] = si;
+  }
+  __syncthreads();
+  const uint32_t r = scratch[w] + inc - x;
+  *total = scratch[NWARP];
+  __syncthreads();
+  return r;
+}
+
+__device__ __forceinline__ uint64_t warp_sum_u64(uint64_t x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+
+// Adds a per-thread comparison count to a global counter (one atomic per warp).
+__device__ __forceinline__ void flush_count(uint64_t c, unsigned long long* dst) {
+  c = warp_sum_u64(c);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(dst, static_cast<unsigned long long>(c));
+}
+
+// ---------------------------------------------------------------------------
+// Tile load / store (striped: item j of thread t is element j*NT + t)
+
+template <class K, bool HV>
+__device__ __forceinline__ void load_tile_enc(TileSmem<K, HV> s, const K* g, const uint32_t* gv,
+                                              int cnt, int xf) {
+#pragma unroll 4
+  for (int j = 0; j < V; ++j) {
+    const int i = j * NT + threadIdx.x;
+    s.k[sk_i<K>(i)] = (i < cnt) ? enc_key(g[i], xf) : key_max<K>();
+    if (HV) s.v[sv_i(i)] = (i < cnt) ? gv[i] : 0xffffffffu;
+  }
+}
+
+template <class K, bool HV>
+__device__ __forceinline__ void store_tile_dec(TileSmem<K, HV> s, K* g, uint32_t* gv, int cnt,
+                                               int xf) {
+#pragma unroll 4
+  for (int j = 0; j < V; ++j) {
+    const int i = j * NT + threadIdx.x;
+    if (i < cnt) {
+      g[i] = dec_key(s.k[sk_i<K>(i)], xf);
+      if (HV) gv[i] = s.v[sv_i(i)];
+    }
+  }
+}
+
+// Copies cnt elements src -> dst (global to global, no overlap), striped.
+template <class K, bool HV>
+__device__ __forceinline__ void copy_elems(K* dst, uint32_t* dv, const K* src, const uint32_t* sv,
+                                           int cnt) {
+  for (int i = threadIdx.x; i < cnt; i += NT) {
+    dst[i] = src[i];
+    if (HV) dv[i] = sv[i];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Merge path (stable: on equal keys the A element goes first)
+
+// Number of A elements among the first d outputs of merging sorted runs
+// A = s[a0, a0+la) and B = s[b0, b0+lb) held in shared memory.
+template <class K, bool CNT>
+__device__ __forceinline__ int merge_path_smem(const K* sk, int a0, int la, int b0, int lb, int d,
+                                               uint64_t& cmp) {
+  int lo = d > lb ? d - lb : 0;
+  int hi = d < la ? d : la;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (CNT) ++cmp;
+    if (!(sk[sk_i<K>(b0 + d - 1 - mid)] < sk[sk_i<K>(a0 + mid)])) {
+      lo = mid + 1;
+    } else {
+      hi = mid;
+    }
+  }
+  return lo;
+}
+
+// Serial stable merge of V outputs starting at A index ai / B index bi.
+// Keys land in k[], the source indices (for payloads) in src[].
+template <class K, bool CNT>
+__device__ __forceinline__ void serial_merge(const K* sk, int ai, int ae, int bi, int be, K (&k)[V],
+                                             int (&src)[V], uint64_t& cmp) {
+  K ka = (ai < ae) ? sk[sk_i<K>(ai)] : key_max<K>();
+  K kb = (bi < be) ? sk[sk_i<K>(bi)] : key_max<K>();
+#pragma unroll
+  for (int j = 0; j < V; ++j) {
+    const bool a_ok = ai < ae, b_ok = bi < be;
+    if (CNT && a_ok && b_ok) ++cmp;
+    const bool tb = b_ok && (!a_ok || kb < ka);
+    k[j] = tb ? kb : ka;
+    src[j] = tb ? bi : ai;
+    if (tb) {
+      ++bi;
+      if (bi < be) kb = sk[sk_i<K>(bi)];
+    } else {
+      ++ai;
+      if (ai < ae) ka = sk[sk_i<K>(ai)];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Base case X: stable sort of one full tile in shared memory.
+// Register odd-even transposition sort of V items per thread (compare-
+// exchange network, shuffles not needed since items are thread-local), then
+// log2(NT) rounds of merge-path merges in shared memory.
+
+template <class K, bool HV, bool CNT>
+__device__ void block_sort_tile(TileSmem<K, HV> s, uint64_t& cmp) {
+  const int tid = threadIdx.x;
+  K k[V];
+  uint32_t v[V];
+  int src[V];
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < V; ++j) {
+    k[j] = s.k[sk_i<K>(tid * V + j)];
+    if (HV) v[j] = s.v[sv_i(tid * V + j)];
+  }
+#pragma unroll
+  for (int r = 0; r < V; ++r) {
+#pragma unroll
+    for (int i = r & 1; i + 1 < V; i += 2) {
+      if (k[i + 1] < k[i]) {
+        const K t = k[i];
+        k[i] = k[i + 1];
+        k[i + 1] = t;
+        if (HV) {
+          const uint32_t u = v[i];
+          v[i] = v[i + 1];
+          v[i + 1] = u;
+        }
+      }
+    }
+  }
+  if (CNT) cmp += V * (V - 1) / 2;
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < V; ++j) {
+    s.k[sk_i<K>(tid * V + j)] = k[j];
+    if (HV) s.v[sv_i(tid * V + j)] = v[j];
+  }
+  __syncthreads();
+  for (int sp = 1; sp < NT; sp <<= 1) {
+    const int L = sp * V;
+    const int g = tid / (2 * sp), r = tid - g * 2 * sp;
+    const int a0 = g * 2 * L, b0 = a0 + L;
+    const int d = r * V;
+    const int ia = merge_path_smem<K, CNT>(s.k, a0, L, b0, L, d, cmp);
+    serial_merge<K, CNT>(s.k, a0 + ia, a0 + L, b0 + d - ia, b0 + L, k, src, cmp);
+    if (HV) {
+#pragma unroll
+      for (int j = 0; j < V; ++j) v[j] = s.v[sv_i(src[j])];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < V; ++j) {
+      s.k[sk_i<K>(a0 + d + j)] = k[j];
+      if (HV) s.v[sv_i(a0 + d + j)] = v[j];
+    }
+    __syncthreads();
+  }
+}
+
+// Sorts the tile g[0, cnt) (cnt <= TILE).  If buf != nullptr the sorted keys
+// are written to buf[0, cnt) and buf's old contents move to g[0, cnt) (the
+// Mergesort leaf "X then swap into the target", Fig. 3 msort); otherwise the
+// tile is sorted in place.
+template <class K, bool HV, bool CNT>
+__device__ void leaf_sort_tile(TileSmem<K, HV> s, K* g, uint32_t* gv, K* buf, uint32_t* bufv,
+                               int cnt, int xf, uint64_t& cmp) {
+  __syncthreads();
+  load_tile_enc<K, HV>(s, g, gv, cnt, xf);
+  __syncthreads();
+  if (buf != nullptr) copy_elems<K, HV>(g, gv, buf, bufv, cnt);
+  block_sort_tile<K, HV, CNT>(s, cmp);
+  if (buf != nullptr) {
+    store_tile_dec<K, HV>(s, buf, bufv, cnt, xf);
+  } else {
+    store_tile_dec<K, HV>(s, g, gv, cnt, xf);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Swap-merge of one output tile.
+//
+// X holds sorted runs of length L (the last one may be shorter) over m
+// elements; Y holds m buffer elements.  Output tile t covers Y[o0, o1) of the
+// merged runs of length 2L.  The block finds its merge-path window in X
+// (cooperative search in global memory), stages the A and B slices in shared
+// memory, moves the buffer elements Y[o0, o1) into exactly the X slots it
+// consumed, then writes the merged tile to Y.  Tiles consume disjoint X slots
+// and write disjoint Y slots, so a whole level runs without inter-block
+// synchronisation, and buffer elements are permuted, never overwritten.
+
+// Cooperative merge-path search over runs A[0, la) and B[0, lb) in global
+// memory for diagonal d: returns the number of A elements among the first d
+// outputs.  Each round every thread probes one candidate, so the window
+// shrinks NT-fold per round (about three rounds for runs of 2^26).
+template <class K, bool CNT>
+__device__ uint64_t merge_path_global(const K* A, uint64_t la, const K* B, uint64_t lb,
+                                      uint64_t d, int xf, uint64_t& cmp) {
+  uint64_t lo = d > lb ? d - lb : 0;
+  uint64_t hi = d < la ? d : la;
+  // The answer lies in [lo, hi]; P(m) = (A[m] <= B[d-1-m]) holds for every m
+  // below the answer and fails from the answer on.
+  while (hi > lo) {
+    const uint64_t span = hi - lo;
+    const uint64_t step = span <= static_cast<uint64_t>(NT) ? 1 : (span + NT - 1) / NT;
+    const uint64_t m = lo + static_cast<uint64_t>(threadIdx.x) * step;
+    bool p = false;
+    if (m < hi) {
+      if (CNT) ++cmp;
+      p = !(enc_key(B[d - 1 - m], xf) < enc_key(A[m], xf));
+    }
+    const int c = __syncthreads_count(p);
+    if (step == 1) {
+      lo += static_cast<uint64_t>(c);
+      break;
+    }
+    if (c == 0) break;  // P(lo) fails: the answer is lo
+    const uint64_t nhi = lo + static_cast<uint64_t>(c) * step;
+    lo = lo + static_cast<uint64_t>(c - 1) * step + 1;
+    if (nhi < hi) hi = nhi;
+  }
+  return lo;
+}
+
+// One output tile of a swap-merge level (see above).  X, Y: region bases;
+// m: elements per region; L: input run length; tile: output tile index.
+template <class K, bool HV, bool CNT>
+__device__ void merge_tile(TileSmem<K, HV> s, K* keys, uint32_t* vals, uint64_t X, uint64_t Y,
+                           uint64_t m, uint64_t L, uint64_t tile, int xf, uint64_t& cmp) {
+  const uint64_t o0 = tile * TILE;
+  const uint64_t o1 = (o0 + TILE < m) ? o0 + TILE : m;
+  const uint64_t pbase = (o0 / (2 * L)) * (2 * L);
+  const uint64_t la = (m - pbase < L) ? m - pbase : L;
+  const uint64_t rem = m - pbase - la;
+  const uint64_t lb = rem < L ? rem : L;
+  const uint64_t d0 = o0 - pbase, d1 = o1 - pbase;
+  K* A = keys + X + pbase;
+  K* B = A + la;
+  uint32_t* Av = HV ? vals + X + pbase : nullptr;
+  uint32_t* Bv = HV ? Av + la : nullptr;
+  __syncthreads();
+  const uint64_t a_lo = merge_path_global<K, CNT>(A, la, B, lb, d0, xf, cmp);
+  const uint64_t a_hi = (d1 == la + lb) ? la : merge_path_global<K, CNT>(A, la, B, lb, d1, xf, cmp);
+  const int cnt = static_cast<int>(o1 - o0);
+  const int na = static_cast<int>(a_hi - a_lo);
+  const int nb = cnt - na;
+  const uint64_t b_lo = d0 - a_lo;
+  // Stage A[a_lo, a_hi) then B[b_lo, b_lo + nb) in shared memory.
+  for (int i = threadIdx.x; i < cnt; i += NT) {
+    const bool fa = i < na;
+    const uint64_t gi = fa ? a_lo + i : b_lo + (i - na);
+    s.k[sk_i<K>(i)] = enc_key(fa ? A[gi] : B[gi], xf);
+    if (HV) s.v[sv_i(i)] = fa ? Av[gi] : Bv[gi];
+  }
+  __syncthreads();
+  // Buffer elements Y[o0, o1) move into the consumed X slots.
+  K* Yk = keys + Y + o0;
+  uint32_t* Yv = HV ? vals + Y + o0 : nullptr;
+  for (int i = threadIdx.x; i < cnt; i += NT) {
+    const bool fa = i < na;
+    const uint64_t gi = fa ? a_lo + i : b_lo + (i - na);
+    const K y = Yk[i];
+    if (fa) A[gi] = y; else B[gi] = y;
+    if (HV) {
+      const uint32_t yv = Yv[i];
+      if (fa) Av[gi] = yv; else Bv[gi] = yv;
+    }
+  }
+  // Merge the staged slices: thread t produces outputs [tV, tV + V).
+  K k[V];
+  uint32_t v[V];
+  int src[V];
+  const int d = threadIdx.x * V;
+  const bool active = d < cnt;
+  if (active) {
+    const int ia = merge_path_smem<K, CNT>(s.k, 0, na, na, nb, d, cmp);
+    serial_merge<K, CNT>(s.k, ia, na, na + d - ia, na + nb, k, src, cmp);
+    if (HV) {
+#pragma unroll
+      for (int j = 0; j < V; ++j) v[j] = s.v[sv_i(src[j] < cnt ? src[j] : 0)];
+    }
+  }
+  __syncthreads();  // all staged reads and all Y reads are complete
+  if (active) {
+#pragma unroll
+    for (int j = 0; j < V; ++j) {
+      if (d + j < cnt) {
+        s.k[sk_i<K>(d + j)] = k[j];
+        if (HV) s.v[sv_i(d + j)] = v[j];
+      }
+    }
+  }
+  __syncthreads();
+  store_tile_dec<K, HV>(s, Yk, Yv, cnt, xf);
+}
+
+// ---------------------------------------------------------------------------
+// Partition, step 1: local partition of one tile g[0, cnt) around the order
+// key piv (left = key < piv, or key <= piv when le).  Left elements are
+// gathered at the front of the tile; returns their number.
+
+template <class K, bool HV, bool CNT>
+__device__ uint32_t part_local_tile(TileSmem<K, HV> s, K* g, uint32_t* gv, int cnt, K piv, bool le,
+                                    int xf, uint64_t& cmp) {
+  K x[V];
+  uint32_t y[V];
+  uint32_t flags = 0, lc = 0, nc = 0;
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < V; ++j) {
+    const int i = j * NT + threadIdx.x;
+    if (i < cnt) {
+      x[j] = g[i];
+      if (HV) y[j] = gv[i];
+      const K u = enc_key(x[j], xf);
+      const bool l = le ? !(piv < u) : (u < piv);
+      flags |= static_cast<uint32_t>(l) << j;
+      lc += l;
+      ++nc;
+    }
+  }
+  if (CNT) cmp += nc;
+  uint32_t tot;
+  const uint32_t ex = block_excl_scan(lc | ((nc - lc) << 16), s.scratch, &tot);
+  const uint32_t c = tot & 0xffffu;
+  if (c == 0 || c == static_cast<uint32_t>(cnt)) return c;  // tile already partitioned
+  uint32_t offL = ex & 0xffffu, offR = c + (ex >> 16);
+#pragma unroll
+  for (int j = 0; j < V; ++j) {
+    const int i = j * NT + threadIdx.x;
+    if (i < cnt) {
+      const uint32_t dst = ((flags >> j) & 1u) ? offL++ : offR++;
+      s.k[sk_i<K>(dst)] = x[j];
+      if (HV) s.v[sv_i(dst)] = y[j];
+    }
+  }
+  __syncthreads();
+#pragma unroll 4
+  for (int j = 0; j < V; ++j) {
+    const int i = j * NT + threadIdx.x;
+    if (i < cnt) {
+      g[i] = s.k[sk_i<K>(i)];
+      if (HV) gv[i] = s.v[sv_i(i)];
+    }
+  }
+  return c;
+}
+
+// Partition, step 3: exchange misplaced elements by rank.  After step 1,
+// tile t = [ts, te) holds its c_t left elements first.  With s = lo + L the
+// final boundary, tile t's right elements inside [lo, s) form one run
+// starting at ts + c_t, and its left elements inside [s, hi) one run
+// starting at max(ts, s).  pml / pmr are the exclusive prefix sums of those
+// run lengths over tiles; the j-th misplaced right element is swapped with
+// the j-th misplaced left element.
+
+__device__ __forceinline__ uint32_t upper_bound_u64(const uint64_t* p, uint32_t n, uint64_t x) {
+  uint32_t lo = 0, hi = n;
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (p[mid] <= x) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+constexpr int EXV = 4;  // ranks per thread in the exchange
+
+template <class K, bool HV>
+__device__ __forceinline__ void exchange_ranks(K* keys, uint32_t* vals, uint64_t lo, uint64_t s,
+                                               const uint32_t* counts, const uint64_t* pml,
+                                               const uint64_t* pmr, uint32_t ntiles, uint64_t j0,
+                                               uint64_t mis) {
+  uint32_t tl = upper_bound_u64(pml, ntiles + 1, j0) - 1;
+  uint32_t tr = upper_bound_u64(pmr, ntiles + 1, j0) - 1;
+#pragma unroll
+  for (int q = 0; q < EXV; ++q) {
+    const uint64_t j = j0 + q;
+    if (j >= mis) break;
+    while (pml[tl + 1] <= j) ++tl;
+    while (pmr[tr + 1] <= j) ++tr;
+    const uint64_t lts = lo + static_cast<uint64_t>(tl) * TILE;
+    const uint64_t lpos = lts + counts[tl] + (j - pml[tl]);
+    const uint64_t rts = lo + static_cast<uint64_t>(tr) * TILE;
+    const uint64_t rpos = (rts > s ? rts : s) + (j - pmr[tr]);
+    const K a = keys[lpos];
+    keys[lpos] = keys[rpos];
+    keys[rpos] = a;
+    if (HV) {
+      const uint32_t b = vals[lpos];
+      vals[lpos] = vals[rpos];
+      vals[rpos] = b;
+    }
+  }
+}
+
+}  // namespace qms

@@ -1,0 +1,342 @@
+// Global kernels of the GB300 QuickMergesort path.  Each kernel is one step
+// of a QuickMergesort round (arXiv 1804.10062, Sec. 2 and the Fig. 3
+// listing): pivot selection, in-place partition (local partition, scan,
+// exchange, pivot placement), Mergesort leaves (base case X) and swap-merge
+// levels.  Round state that the device computes (pivot, left count, ...)
+// lives in a small device descriptor so that kernels can be queued without
+// the host knowing it.
+#pragma once
+
+#include "qms_device.cuh"
+
+namespace qms {
+
+// Device-side round descriptor (one per sort call; O(1) words).
+struct Desc {
+  unsigned long long cmp;         // comparisons (counting build only)
+  unsigned long long L;           // left elements of the last partition pass
+  unsigned long long mis;         // misplaced pairs of the last partition pass
+  unsigned long long pivot;       // order key of the pivot
+  unsigned long long sel_prefix;  // radix select state (MoM)
+  unsigned long long sel_mask;
+  unsigned long long sel_rank;
+  unsigned long long sel_eq;
+  unsigned long long pos;
+  unsigned int tie;  // pivot sample saw a tie: run the second (<=) pass
+  unsigned int err;  // nonzero: an internal consistency check failed
+  unsigned int hist[256];
+};
+
+// ---------------------------------------------------------------------------
+// Base case / Mergesort leaves: sort tiles of P[0, m); with to_buf the
+// sorted tiles go to the buffer region and the buffer's contents move into P.
+
+template <class K, bool HV, bool CNT>
+__global__ void __launch_bounds__(NT) k_leaf_sort(K* keys, uint32_t* vals, uint64_t P, uint64_t m,
+                                                  uint64_t Bb, int to_buf, int xf, Desc* desc) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const auto s = TileSmem<K, HV>::carve(smem);
+  uint64_t cmp = 0;
+  const uint64_t ntiles = (m + TILE - 1) / TILE;
+  for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const uint64_t off = t * TILE;
+    const int cnt = static_cast<int>((m - off) < static_cast<uint64_t>(TILE) ? (m - off) : TILE);
+    K* g = keys + P + off;
+    uint32_t* gv = HV ? vals + P + off : nullptr;
+    K* b = to_buf ? keys + Bb + off : nullptr;
+    uint32_t* bv = (HV && to_buf) ? vals + Bb + off : nullptr;
+    leaf_sort_tile<K, HV, CNT>(s, g, gv, b, bv, cnt, xf, cmp);
+  }
+  if (CNT) flush_count(cmp, &desc->cmp);
+}
+
+// One swap-merge level: runs of length L in region X -> runs of 2L in Y.
+template <class K, bool HV, bool CNT>
+__global__ void __launch_bounds__(NT) k_merge_level(K* keys, uint32_t* vals, uint64_t X, uint64_t Y,
+                                                    uint64_t m, uint64_t L, int xf, Desc* desc) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const auto s = TileSmem<K, HV>::carve(smem);
+  uint64_t cmp = 0;
+  const uint64_t ntiles = (m + TILE - 1) / TILE;
+  for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    merge_tile<K, HV, CNT>(s, keys, vals, X, Y, m, L, t, xf, cmp);
+  }
+  if (CNT) flush_count(cmp, &desc->cmp);
+}
+
+// ---------------------------------------------------------------------------
+// Pivot selection.  Each pivot kernel parks the chosen pivot element at
+// position e - 1 and records its order key and whether the sample held a
+// tie (duplicate guard: a tie selects the second, "<=", partition pass).
+
+// Median-of-3 at b, b + floor(n/2), e - 1 (proof of Thm. 1).
+template <class K, bool HV, bool CNT>
+__global__ void k_pivot_m3(K* keys, uint32_t* vals, uint64_t b, uint64_t e, int xf, Desc* desc) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const uint64_t n = e - b;
+  uint64_t p0 = b, p1 = b + n / 2, p2 = e - 1;
+  K u0 = enc_key(keys[p0], xf), u1 = enc_key(keys[p1], xf), u2 = enc_key(keys[p2], xf);
+  // sort3 on (key, position) pairs
+  if (u1 < u0) { K t = u0; u0 = u1; u1 = t; uint64_t q = p0; p0 = p1; p1 = q; }
+  unsigned c = 2;
+  if (u2 < u1) {
+    K t = u1; u1 = u2; u2 = t; uint64_t q = p1; p1 = p2; p2 = q;
+    ++c;
+    if (u1 < u0) { t = u0; u0 = u1; u1 = t; q = p0; p0 = p1; p1 = q; }
+  }
+  const bool tie = !(u0 < u1) || !(u1 < u2);
+  const uint64_t pm = p1, last = e - 1;
+  if (pm != last) {
+    const K a = keys[pm]; keys[pm] = keys[last]; keys[last] = a;
+    if (HV) { const uint32_t x = vals[pm]; vals[pm] = vals[last]; vals[last] = x; }
+  }
+  desc->pivot = static_cast<unsigned long long>(u1);
+  desc->tie = tie ? 1u : 0u;
+  if (CNT) desc->cmp += c + 2;
+}
+
+// Median of a sample of ks (odd, <= TILE - 1) elements at b + i*step
+// (median-of-sqrt(n), Sec. 2 / Thm. 2).  One block sorts the sample with the
+// base-case sort, carrying the sample index as payload.
+template <class K, bool HV, bool CNT>
+__global__ void __launch_bounds__(NT) k_pivot_sample(K* keys, uint32_t* vals, uint64_t b, uint64_t e,
+                                                     int ks, uint64_t step, int xf, Desc* desc) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const auto s = TileSmem<K, true>::carve(smem);
+  uint64_t cmp = 0;
+  for (int i = threadIdx.x; i < TILE; i += NT) {
+    s.k[sk_i<K>(i)] = (i < ks) ? enc_key(keys[b + static_cast<uint64_t>(i) * step], xf) : key_max<K>();
+    s.v[sv_i(i)] = static_cast<uint32_t>(i);
+  }
+  block_sort_tile<K, true, CNT>(s, cmp);
+  if (CNT) flush_count(cmp, &desc->cmp);
+  if (threadIdx.x == 0) {
+    const int h = ks / 2;
+    const K med = s.k[sk_i<K>(h)];
+    const uint64_t pm = b + static_cast<uint64_t>(s.v[sv_i(h)]) * step, last = e - 1;
+    bool tie = false;
+    if (ks >= 3) tie = !(s.k[sk_i<K>(h - 1)] < med) || !(med < s.k[sk_i<K>(h + 1)]);
+    if (pm != last) {
+      const K a = keys[pm]; keys[pm] = keys[last]; keys[last] = a;
+      if (HV) { const uint32_t x = vals[pm]; vals[pm] = vals[last]; vals[last] = x; }
+    }
+    desc->pivot = static_cast<unsigned long long>(med);
+    desc->tie = tie ? 1u : 0u;
+    if (CNT) desc->cmp += 2;
+  }
+}
+
+// MoM step 1 (Sec. 4): the median of each triple (3i, 3i+1, 3i+2), i < t,
+// is moved to the middle slot 3i+1 of its triple.
+template <class K, bool HV, bool CNT>
+__global__ void k_mom_triples(K* keys, uint32_t* vals, uint64_t b, uint64_t t, int xf, Desc* desc) {
+  uint64_t cmp = 0;
+  for (uint64_t i = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; i < t;
+       i += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
+    const uint64_t q = b + 3 * i;
+    const K x0 = keys[q], x1 = keys[q + 1], x2 = keys[q + 2];
+    const K u0 = enc_key(x0, xf), u1 = enc_key(x1, xf), u2 = enc_key(x2, xf);
+    int mi;
+    if (u1 < u0) {                     // u1 < u0
+      mi = (u2 < u1) ? 1 : ((u2 < u0) ? 2 : 0);
+    } else {                           // u0 <= u1
+      mi = (u2 < u1) ? ((u2 < u0) ? 0 : 2) : 1;
+    }
+    if (CNT) cmp += 3;
+    if (mi != 1) {
+      const uint64_t p = q + mi;
+      keys[q + 1] = (mi == 0) ? x0 : x2;
+      keys[p] = x1;
+      if (HV) { const uint32_t a = vals[p]; vals[p] = vals[q + 1]; vals[q + 1] = a; }
+    }
+  }
+  if (CNT) flush_count(cmp, &desc->cmp);
+}
+
+// MoM step 2: exact radix selection of the median of the medians (8 bits a
+// pass, most significant first).
+template <class K>
+__global__ void k_sel_hist(const K* keys, uint64_t b, uint64_t t, int xf, int shift, Desc* desc) {
+  __shared__ unsigned int h[256];
+  for (int i = threadIdx.x; i < 256; i += blockDim.x) h[i] = 0;
+  __syncthreads();
+  const K pre = static_cast<K>(desc->sel_prefix), msk = static_cast<K>(desc->sel_mask);
+  for (uint64_t i = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; i < t;
+       i += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
+    const K u = enc_key(keys[b + 3 * i + 1], xf);
+    if (((u ^ pre) & msk) == 0) atomicAdd(&h[static_cast<unsigned>(u >> shift) & 255u], 1u);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 256; i += blockDim.x)
+    if (h[i]) atomicAdd(&desc->hist[i], h[i]);
+}
+
+__global__ void k_sel_pick(int shift, Desc* desc) {
+  if (threadIdx.x != 0) return;
+  unsigned long long r = desc->sel_rank, acc = 0;
+  int bin = 255;
+  for (int i = 0; i < 256; ++i) {
+    const unsigned long long c = desc->hist[i];
+    if (r < acc + c) { bin = i; break; }
+    acc += c;
+  }
+  desc->sel_eq = desc->hist[bin];
+  desc->sel_prefix |= static_cast<unsigned long long>(bin) << shift;
+  desc->sel_mask |= 255ull << shift;
+  desc->sel_rank = r - acc;
+  for (int i = 0; i < 256; ++i) desc->hist[i] = 0;
+}
+
+// MoM step 3: locate a median equal to the selected value and park it.
+template <class K>
+__global__ void k_mom_locate(const K* keys, uint64_t b, uint64_t t, int xf, Desc* desc) {
+  const K v = static_cast<K>(desc->sel_prefix);
+  for (uint64_t i = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; i < t;
+       i += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
+    if (enc_key(keys[b + 3 * i + 1], xf) == v) atomicMin(&desc->pos, static_cast<unsigned long long>(i));
+  }
+}
+
+template <class K, bool HV>
+__global__ void k_mom_place(K* keys, uint32_t* vals, uint64_t b, uint64_t e, uint64_t t, Desc* desc) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (desc->pos >= t) {  // no median carried the selected key: report, touch nothing
+    desc->err |= 2u;
+    return;
+  }
+  const uint64_t pm = b + 3 * desc->pos + 1, last = e - 1;
+  if (pm != last) {
+    const K a = keys[pm]; keys[pm] = keys[last]; keys[last] = a;
+    if (HV) { const uint32_t x = vals[pm]; vals[pm] = vals[last]; vals[last] = x; }
+  }
+  desc->pivot = desc->sel_prefix;
+  desc->tie = desc->sel_eq > 1 ? 1u : 0u;
+}
+
+// ---------------------------------------------------------------------------
+// In-place partition of [lo, hi) around desc->pivot (Sec. 2; every element is
+// compared with the pivot once).
+
+// Step 1: local partition of every tile, left count per tile.
+template <class K, bool HV, bool CNT>
+__global__ void __launch_bounds__(NT) k_part_local(K* keys, uint32_t* vals, uint64_t lo, uint64_t hi,
+                                                   int le, int xf, Desc* desc, uint32_t* counts) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const auto s = TileSmem<K, HV>::carve(smem);
+  uint64_t cmp = 0;
+  const K piv = static_cast<K>(desc->pivot);
+  const uint64_t n = hi - lo, ntiles = (n + TILE - 1) / TILE;
+  for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const uint64_t off = t * TILE;
+    const int cnt = static_cast<int>((n - off) < static_cast<uint64_t>(TILE) ? (n - off) : TILE);
+    const uint32_t c = part_local_tile<K, HV, CNT>(s, keys + lo + off, HV ? vals + lo + off : nullptr,
+                                                   cnt, piv, le != 0, xf, cmp);
+    if (threadIdx.x == 0) counts[t] = c;
+  }
+  if (CNT) flush_count(cmp, &desc->cmp);
+}
+
+// Block-wide exclusive scan of 64-bit values (scratch: NWARP + 1 u64).
+__device__ __forceinline__ uint64_t block_excl_scan_u64(uint64_t x, uint64_t* scratch,
+                                                        uint64_t* total) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  uint64_t inc = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint64_t y = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += y;
+  }
+  if (lane == 31) scratch[w] = inc;
+  __syncthreads();
+  if (w == 0) {
+    const uint64_t s = lane < NWARP ? scratch[lane] : 0ull;
+    uint64_t si = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint64_t y = __shfl_up_sync(0xffffffffu, si, o);
+      if (lane >= o) si += y;
+    }
+    if (lane < NWARP) scratch[lane] = si - s;
+    if (lane == 31) scratch[NWARP] = si;
+  }
+  __syncthreads();
+  const uint64_t r = scratch[w] + inc - x;
+  *total = scratch[NWARP];
+  __syncthreads();
+  return r;
+}
+
+// Step 2 (one block): L = sum of counts, then the per-tile misplaced run
+// lengths and their exclusive prefix sums pml / pmr (ntiles + 1 entries).
+__global__ void __launch_bounds__(NT) k_part_scan(const uint32_t* counts, uint32_t ntiles, uint64_t lo,
+                                                  uint64_t hi, uint64_t* pml, uint64_t* pmr,
+                                                  Desc* desc) {
+  __shared__ uint64_t scr[NWARP + 1];
+  uint64_t sum = 0;
+  for (uint32_t t = threadIdx.x; t < ntiles; t += NT) sum += counts[t];
+  uint64_t L;
+  (void)block_excl_scan_u64(sum, scr, &L);
+  const uint64_t s = lo + L;
+  const uint32_t chunk = (ntiles + NT - 1) / NT;
+  const uint32_t t0 = threadIdx.x * chunk;
+  const uint32_t t1 = (t0 + chunk < ntiles) ? t0 + chunk : ntiles;
+  uint64_t sl = 0, sr = 0;
+  for (uint32_t t = t0; t < t1; ++t) {
+    const uint64_t ts = lo + static_cast<uint64_t>(t) * TILE;
+    const uint64_t te = (ts + TILE < hi) ? ts + TILE : hi;
+    const uint64_t cs = ts + counts[t];
+    const uint64_t lend = te < s ? te : s;
+    const uint64_t rbeg = ts > s ? ts : s;
+    sl += lend > cs ? lend - cs : 0;
+    sr += cs > rbeg ? cs - rbeg : 0;
+  }
+  uint64_t totl, totr;
+  uint64_t bl = block_excl_scan_u64(sl, scr, &totl);
+  uint64_t br = block_excl_scan_u64(sr, scr, &totr);
+  for (uint32_t t = t0; t < t1; ++t) {
+    pml[t] = bl;
+    pmr[t] = br;
+    const uint64_t ts = lo + static_cast<uint64_t>(t) * TILE;
+    const uint64_t te = (ts + TILE < hi) ? ts + TILE : hi;
+    const uint64_t cs = ts + counts[t];
+    const uint64_t lend = te < s ? te : s;
+    const uint64_t rbeg = ts > s ? ts : s;
+    bl += lend > cs ? lend - cs : 0;
+    br += cs > rbeg ? cs - rbeg : 0;
+  }
+  if (threadIdx.x == 0) {
+    pml[ntiles] = totl;
+    pmr[ntiles] = totr;
+    desc->L = L;
+    desc->mis = totl;
+    if (totl != totr) desc->err |= 1u;
+  }
+}
+
+// Step 3: exchange the misplaced elements by rank.
+template <class K, bool HV>
+__global__ void __launch_bounds__(NT) k_part_exchange(K* keys, uint32_t* vals, uint64_t lo,
+                                                      const uint32_t* counts, const uint64_t* pml,
+                                                      const uint64_t* pmr, uint32_t ntiles,
+                                                      const Desc* desc) {
+  const uint64_t mis = desc->mis;
+  const uint64_t s = lo + desc->L;
+  for (uint64_t j0 = (blockIdx.x * static_cast<uint64_t>(NT) + threadIdx.x) * EXV; j0 < mis;
+       j0 += static_cast<uint64_t>(gridDim.x) * NT * EXV) {
+    exchange_ranks<K, HV>(keys, vals, lo, s, counts, pml, pmr, ntiles, j0, mis);
+  }
+}
+
+// Step 4: the pivot parked at position `parked` moves to its final index
+// lo + L.
+template <class K, bool HV>
+__global__ void k_place_pivot(K* keys, uint32_t* vals, uint64_t lo, uint64_t parked, Desc* desc) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const uint64_t k = lo + desc->L;
+  if (k != parked) {
+    const K a = keys[k]; keys[k] = keys[parked]; keys[parked] = a;
+    if (HV) { const uint32_t x = vals[k]; vals[k] = vals[parked]; vals[parked] = x; }
+  }
+}
+
+}  // namespace qms

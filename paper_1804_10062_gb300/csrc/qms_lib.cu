@@ -1,0 +1,398 @@
+// Host side of the GB300 QuickMergesort library: the C ABI declared in
+// include/qms.h and the round driver that queues the kernels of
+// qms_kernels.cuh.
+//
+// Driver (Fig. 3 "sort" of arXiv 1804.10062): while the remaining range is
+// larger than one tile, choose a pivot, partition in place, Mergesort one
+// side using the other side as swap buffer, continue on the other side; a
+// last range of at most one tile is finished by the base case.  The host
+// reads the left count of each partition (one small device-to-host copy per
+// round) to size the Mergesort launches.
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cstdint>
+#include <cstring>
+#include <mutex>
+
+#include "../../include/qms.h"
+#include "qms_kernels.cuh"
+
+namespace qms {
+namespace {
+
+struct Err {
+  int code;
+};
+
+inline void ck(cudaError_t e) {
+  if (e != cudaSuccess) throw Err{QMS_ECUDA};
+}
+
+inline int xform_of(int dtype) {
+  return dtype == QMS_F32 ? XF_F32 : (dtype == QMS_I64 ? XF_I64 : XF_NONE);
+}
+
+// Raises the dynamic shared-memory limit of a kernel once per process.
+template <class F>
+void allow_smem(F* f, size_t bytes, bool& done) {
+  if (!done) {
+    ck(cudaFuncSetAttribute(reinterpret_cast<const void*>(f),
+                            cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes)));
+    done = true;
+  }
+}
+
+// Host mirror of the descriptor fields the driver reads back each round.
+struct DescHead {
+  unsigned long long cmp, L, mis, pivot;
+};
+
+// Device workspace for one sort: descriptor + per-tile counters.
+struct Workspace {
+  unsigned char* base = nullptr;
+  size_t bytes = 0;
+  Desc* desc = nullptr;
+  uint32_t* counts = nullptr;
+  uint64_t* pml = nullptr;
+  uint64_t* pmr = nullptr;
+  cudaStream_t st = nullptr;
+
+  static size_t size_for(uint64_t n) {
+    const uint64_t nt = n / TILE + 2;
+    return ((sizeof(Desc) + 255) / 256) * 256 + ((nt * 4 + 255) / 256) * 256 + 2 * (nt + 1) * 8;
+  }
+  void alloc(uint64_t n, cudaStream_t s) {
+    st = s;
+    bytes = size_for(n);
+    if (cudaMallocAsync(reinterpret_cast<void**>(&base), bytes, s) != cudaSuccess) {
+      base = nullptr;
+      (void)cudaGetLastError();
+      throw Err{QMS_ENOMEM};
+    }
+    const uint64_t nt = n / TILE + 2;
+    size_t off = 0;
+    desc = reinterpret_cast<Desc*>(base);
+    off += ((sizeof(Desc) + 255) / 256) * 256;
+    counts = reinterpret_cast<uint32_t*>(base + off);
+    off += ((nt * 4 + 255) / 256) * 256;
+    pml = reinterpret_cast<uint64_t*>(base + off);
+    off += (nt + 1) * 8;
+    pmr = reinterpret_cast<uint64_t*>(base + off);
+    ck(cudaMemsetAsync(desc, 0, sizeof(Desc), s));
+  }
+  ~Workspace() {
+    if (base) cudaFreeAsync(base, st);
+  }
+};
+
+template <class K, bool HV, bool CNT>
+class Sorter {
+ public:
+  Sorter(K* keys, uint32_t* vals, int xf, cudaStream_t st, Workspace& ws)
+      : keys_(keys), vals_(vals), xf_(xf), st_(st), ws_(ws) {
+    static bool a1 = false, a2 = false, a3 = false, a4 = false;
+    allow_smem(k_leaf_sort<K, HV, CNT>, tile_smem_bytes<K, HV>(), a1);
+    allow_smem(k_merge_level<K, HV, CNT>, tile_smem_bytes<K, HV>(), a2);
+    allow_smem(k_part_local<K, HV, CNT>, tile_smem_bytes<K, HV>(), a3);
+    allow_smem(k_pivot_sample<K, HV, CNT>, tile_smem_bytes<K, true>(), a4);
+  }
+
+  uint64_t rounds = 0, mom_rounds = 0, launches = 0;
+
+  // ---- steps ------------------------------------------------------------
+
+  void leaf(uint64_t P, uint64_t m, bool to_buf, uint64_t Bb) {
+    if (m == 0) return;
+    const uint64_t nt = (m + TILE - 1) / TILE;
+    k_leaf_sort<K, HV, CNT><<<grid_of(nt), NT, tile_smem_bytes<K, HV>(), st_>>>(
+        keys_, vals_, P, m, Bb, to_buf ? 1 : 0, xf_, ws_.desc);
+    launched();
+  }
+
+  // Mergesort of P[0, m) with the disjoint buffer Bb[0, m) (Fig. 3 "out"
+  // with a full-size buffer: every level merges one region into the other).
+  void mergesort(uint64_t P, uint64_t m, uint64_t Bb) {
+    if (m <= 1) return;
+    if (m <= static_cast<uint64_t>(TILE)) {
+      leaf(P, m, false, 0);
+      return;
+    }
+    const uint64_t leaves = (m + TILE - 1) / TILE;
+    int levels = 0;
+    while ((1ull << levels) < leaves) ++levels;
+    const bool to_buf = (levels & 1) != 0;
+    leaf(P, m, to_buf, Bb);
+    uint64_t X = to_buf ? Bb : P, Y = to_buf ? P : Bb;
+    for (int l = 0; l < levels; ++l) {
+      const uint64_t L = static_cast<uint64_t>(TILE) << l;
+      k_merge_level<K, HV, CNT><<<grid_of(leaves), NT, tile_smem_bytes<K, HV>(), st_>>>(
+          keys_, vals_, X, Y, m, L, xf_, ws_.desc);
+      launched();
+      std::swap(X, Y);
+    }
+  }
+
+  // Parks a pivot of [b, e) at e - 1 (rule: QMS_PIVOT_*, MOM for HYBRID's
+  // fallback rounds).
+  void pivot(uint64_t b, uint64_t e, int rule) {
+    const uint64_t n = e - b;
+    if (rule == QMS_PIVOT_SQRTN) {
+      uint64_t c = 1;
+      while (c * c < n) ++c;  // ceil(sqrt(n)); n < 2^40 here
+      uint64_t k = (c & 1) ? c : c - 1;
+      if (k > static_cast<uint64_t>(TILE - 1)) k = TILE - 1;
+      if (k < 1) k = 1;
+      const uint64_t step = n / k;
+      k_pivot_sample<K, HV, CNT><<<1, NT, tile_smem_bytes<K, true>(), st_>>>(
+          keys_, vals_, b, e, static_cast<int>(k), step, xf_, ws_.desc);
+      launched();
+    } else if (rule == QMS_PIVOT_MOM) {
+      const uint64_t t = n / 3;
+      const unsigned g = static_cast<unsigned>(std::min<uint64_t>((t + 255) / 256, 1u << 20));
+      k_mom_triples<K, HV, CNT><<<g, 256, 0, st_>>>(keys_, vals_, b, t, xf_, ws_.desc);
+      launched();
+      // radix select of rank floor(t/2) among the medians
+      unsigned long long init[4] = {0ull, 0ull, static_cast<unsigned long long>(t / 2), 0ull};
+      ck(cudaMemcpyAsync(&ws_.desc->sel_prefix, init, sizeof(init), cudaMemcpyHostToDevice, st_));
+      ck(cudaMemsetAsync(ws_.desc->hist, 0, sizeof(ws_.desc->hist), st_));
+      for (int shift = static_cast<int>(sizeof(K) * 8) - 8; shift >= 0; shift -= 8) {
+        k_sel_hist<K><<<g, 256, 0, st_>>>(keys_, b, t, xf_, shift, ws_.desc);
+        k_sel_pick<<<1, 32, 0, st_>>>(shift, ws_.desc);
+        launched(2);
+      }
+      const unsigned long long big = ~0ull;
+      ck(cudaMemcpyAsync(&ws_.desc->pos, &big, sizeof(big), cudaMemcpyHostToDevice, st_));
+      k_mom_locate<K><<<g, 256, 0, st_>>>(keys_, b, t, xf_, ws_.desc);
+      k_mom_place<K, HV><<<1, 32, 0, st_>>>(keys_, vals_, b, e, t, ws_.desc);
+      launched(2);
+      ++mom_rounds;
+    } else {
+      k_pivot_m3<K, HV, CNT><<<1, 32, 0, st_>>>(keys_, vals_, b, e, xf_, ws_.desc);
+      launched();
+    }
+  }
+
+  // Partitions [lo, hi) around the descriptor's pivot (le: "<=" pass);
+  // when parked != ~0 the pivot parked there moves to lo + L afterwards.
+  // Returns L, the number of left elements.
+  uint64_t partition(uint64_t lo, uint64_t hi, bool le, uint64_t parked, unsigned* tie) {
+    const uint64_t n = hi - lo;
+    const uint64_t nt = (n + TILE - 1) / TILE;
+    if (n > 0) {
+      k_part_local<K, HV, CNT><<<grid_of(nt), NT, tile_smem_bytes<K, HV>(), st_>>>(
+          keys_, vals_, lo, hi, le ? 1 : 0, xf_, ws_.desc, ws_.counts);
+      k_part_scan<<<1, NT, 0, st_>>>(ws_.counts, static_cast<uint32_t>(nt), lo, hi, ws_.pml,
+                                     ws_.pmr, ws_.desc);
+      const uint64_t maxmis = n / 2 + 1;
+      const uint64_t per = static_cast<uint64_t>(NT) * EXV;
+      k_part_exchange<K, HV><<<grid_of((maxmis + per - 1) / per), NT, 0, st_>>>(
+          keys_, vals_, lo, ws_.counts, ws_.pml, ws_.pmr, static_cast<uint32_t>(nt), ws_.desc);
+      launched(3);
+    } else {
+      ck(cudaMemsetAsync(&ws_.desc->L, 0, sizeof(unsigned long long), st_));
+    }
+    if (parked != ~0ull) {
+      k_place_pivot<K, HV><<<1, 32, 0, st_>>>(keys_, vals_, lo, parked, ws_.desc);
+      launched();
+    }
+    struct {
+      unsigned long long L;
+      unsigned tie, err;
+    } h;
+    ck(cudaMemcpyAsync(&h.L, &ws_.desc->L, sizeof(h.L), cudaMemcpyDeviceToHost, st_));
+    ck(cudaMemcpyAsync(&h.tie, &ws_.desc->tie, 2 * sizeof(unsigned), cudaMemcpyDeviceToHost, st_));
+    ck(cudaStreamSynchronize(st_));
+    ck(cudaGetLastError());
+    if (h.err) throw Err{QMS_EINTERNAL};
+    if (tie) *tie = h.tie;
+    return h.L;
+  }
+
+  // One round on [b, e): returns the pivot block [k, k + 1 + eq).
+  void split(uint64_t b, uint64_t e, int rule, uint64_t* k, uint64_t* eq) {
+    pivot(b, e, rule);
+    unsigned tie = 0;
+    const uint64_t L = partition(b, e - 1, false, e - 1, &tie);
+    *k = b + L;
+    *eq = 0;
+    if (tie && *k + 1 < e) *eq = partition(*k + 1, e, true, ~0ull, nullptr);
+  }
+
+  void sort(uint64_t n, int rule) {
+    uint64_t b = 0, e = n;
+    bool mom_next = false;
+    while (e - b > static_cast<uint64_t>(TILE)) {
+      ++rounds;
+      const uint64_t nn = e - b;
+      const bool mom = rule == QMS_PIVOT_MOM || (rule == QMS_PIVOT_HYBRID && mom_next);
+      const int r = mom ? QMS_PIVOT_MOM : (rule == QMS_PIVOT_SQRTN ? QMS_PIVOT_SQRTN : QMS_PIVOT_M3);
+      uint64_t k, eq;
+      split(b, e, r, &k, &eq);
+      if (rule == QMS_PIVOT_HYBRID) {
+        const uint64_t d = nn / 16, rlo = k - b, rhi = k + eq - b;
+        mom_next = !mom && (rhi < d || rlo > nn - 1 - d);
+      }
+      const uint64_t rb = k + 1 + eq;
+      const uint64_t nl = k - b, nr = e - rb;
+      // Two-way split: Fig. 3 rule (Mergesort the left side iff the pivot is
+      // left of the integer midpoint).  Three-way split: the smaller side.
+      const bool left = (eq == 0) ? (k < b + nn / 2) : (nl <= nr);
+      if (left) {
+        mergesort(b, nl, rb);
+        b = rb;
+      } else {
+        mergesort(rb, nr, b);
+        e = k;
+      }
+    }
+    if (e - b > 1) leaf(b, e - b, false, 0);
+  }
+
+  void launched(int c = 1) { launches += c; }
+
+ private:
+  static unsigned grid_of(uint64_t blocks) {
+    if (blocks < 1) blocks = 1;
+    return static_cast<unsigned>(std::min<uint64_t>(blocks, 1u << 30));
+  }
+
+  K* keys_;
+  uint32_t* vals_;
+  int xf_;
+  cudaStream_t st_;
+  Workspace& ws_;
+};
+
+struct Args {
+  void* keys;
+  uint32_t* vals;
+  uint64_t n;
+  int dtype;
+  int pivot;
+  bool count;
+  cudaStream_t st;
+};
+
+template <class K, bool HV, bool CNT, class Fn>
+int run_typed(const Args& a, qms_stats* stats, Fn&& fn) {
+  const auto t0 = std::chrono::steady_clock::now();
+  Workspace ws;
+  ws.alloc(a.n, a.st);
+  Sorter<K, HV, CNT> s(static_cast<K*>(a.keys), a.vals, xform_of(a.dtype), a.st, ws);
+  fn(s);
+  unsigned long long cmp = 0;
+  if (CNT) ck(cudaMemcpyAsync(&cmp, &ws.desc->cmp, sizeof(cmp), cudaMemcpyDeviceToHost, a.st));
+  ck(cudaStreamSynchronize(a.st));
+  ck(cudaGetLastError());
+  if (stats) {
+    stats->comparisons = cmp;
+    stats->aux_bytes = ws.bytes;
+    stats->rounds = s.rounds;
+    stats->mom_rounds = s.mom_rounds;
+    stats->launches = s.launches;
+    stats->ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  }
+  return QMS_OK;
+}
+
+template <class Fn>
+int dispatch(const Args& a, qms_stats* stats, Fn&& fn) {
+  try {
+    const bool u64 = (a.dtype == QMS_U64 || a.dtype == QMS_I64);
+    const bool hv = a.vals != nullptr;
+    if (u64) {
+      if (hv) return a.count ? run_typed<uint64_t, true, true>(a, stats, fn) : run_typed<uint64_t, true, false>(a, stats, fn);
+      return a.count ? run_typed<uint64_t, false, true>(a, stats, fn) : run_typed<uint64_t, false, false>(a, stats, fn);
+    }
+    if (hv) return a.count ? run_typed<uint32_t, true, true>(a, stats, fn) : run_typed<uint32_t, true, false>(a, stats, fn);
+    return a.count ? run_typed<uint32_t, false, true>(a, stats, fn) : run_typed<uint32_t, false, false>(a, stats, fn);
+  } catch (const Err& e) {
+    return e.code;
+  } catch (...) {
+    return QMS_EINTERNAL;
+  }
+}
+
+bool valid_dtype(int d) { return d >= QMS_U32 && d <= QMS_F32; }
+
+}  // namespace
+}  // namespace qms
+
+using namespace qms;
+
+extern "C" {
+
+int qms_version(void) { return 10000; }
+
+const char* qms_error_string(int code) {
+  switch (code) {
+    case QMS_OK: return "ok";
+    case QMS_EINVAL: return "invalid argument";
+    case QMS_ENOMEM: return "out of device memory";
+    case QMS_EBUDGET: return "request exceeds the HBM budget";
+    case QMS_ECUDA: return "CUDA error";
+    case QMS_ETIMEOUT: return "bounded wait timed out";
+    case QMS_EAGAIN: return "not finished";
+    case QMS_EINTERNAL: return "internal consistency check failed";
+    default: return "unknown error";
+  }
+}
+
+static int sort_common(void* d_keys, uint32_t* d_vals, size_t n, int dtype, const qms_options* opt,
+                       void* stream, qms_stats* stats) {
+  if (stats) std::memset(stats, 0, sizeof(*stats));
+  if (!valid_dtype(dtype)) return QMS_EINVAL;
+  const int pivot = opt ? opt->pivot : QMS_PIVOT_M3;
+  if (pivot < QMS_PIVOT_M3 || pivot > QMS_PIVOT_HYBRID) return QMS_EINVAL;
+  if (n <= 1) return QMS_OK;
+  if (d_keys == nullptr) return QMS_EINVAL;
+  if (d_vals != nullptr && n >= (1ull << 32)) return QMS_EINVAL;
+  Args a{d_keys, d_vals, n, dtype, pivot, opt && opt->count_cmps, static_cast<cudaStream_t>(stream)};
+  return dispatch(a, stats, [&](auto& s) { s.sort(n, pivot); });
+}
+
+int qms_sort(void* d_keys, size_t n, int dtype, const qms_options* opt, void* stream,
+             qms_stats* stats) {
+  return sort_common(d_keys, nullptr, n, dtype, opt, stream, stats);
+}
+
+int qms_sort_pairs(void* d_keys, uint32_t* d_vals, size_t n, int dtype, const qms_options* opt,
+                   void* stream, qms_stats* stats) {
+  if (d_vals == nullptr && n > 1) return QMS_EINVAL;
+  return sort_common(d_keys, d_vals, n, dtype, opt, stream, stats);
+}
+
+int qms_tile_sort(void* d_keys, uint32_t* d_vals, size_t n, int dtype, void* stream) {
+  if (!valid_dtype(dtype) || n > static_cast<size_t>(TILE)) return QMS_EINVAL;
+  if (n <= 1) return QMS_OK;
+  if (d_keys == nullptr) return QMS_EINVAL;
+  Args a{d_keys, d_vals, n, dtype, 0, false, static_cast<cudaStream_t>(stream)};
+  return dispatch(a, nullptr, [&](auto& s) { s.leaf(0, n, false, 0); });
+}
+
+int qms_partition(void* d_keys, uint32_t* d_vals, size_t n, int dtype, int pivot, void* stream,
+                  uint64_t* k_out, uint64_t* eq_out) {
+  if (!valid_dtype(dtype) || n < 3 || d_keys == nullptr || k_out == nullptr || eq_out == nullptr)
+    return QMS_EINVAL;
+  if (pivot < QMS_PIVOT_M3 || pivot > QMS_PIVOT_MOM) return QMS_EINVAL;
+  if (d_vals != nullptr && n >= (1ull << 32)) return QMS_EINVAL;
+  Args a{d_keys, d_vals, n, dtype, pivot, false, static_cast<cudaStream_t>(stream)};
+  return dispatch(a, nullptr, [&](auto& s) {
+    uint64_t k, eq;
+    s.split(0, n, pivot, &k, &eq);
+    *k_out = k;
+    *eq_out = eq;
+  });
+}
+
+int qms_mergesort(void* d_keys, uint32_t* d_vals, size_t m, size_t buf, int dtype, void* stream) {
+  if (!valid_dtype(dtype) || (m > 1 && d_keys == nullptr) || buf < m) return QMS_EINVAL;
+  if (m <= 1) return QMS_OK;
+  Args a{d_keys, d_vals, buf + m, dtype, 0, false, static_cast<cudaStream_t>(stream)};
+  return dispatch(a, nullptr, [&](auto& s) { s.mergesort(0, m, buf); });
+}
+
+}  // extern "C"

@@ -1,0 +1,167 @@
+"""ctypes binding of libqms.so (include/qms.h): argument marshalling only.
+
+Every function has the name of the C entry point it calls.  Key tensors are
+CUDA tensors (uint32, uint64, int64 or float32; any 4/8-byte dtype with an
+explicit ``dtype=`` names raw bit patterns); payload tensors are uint32 (or
+int32 bit views).  The stream is the current torch stream unless given.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import build as _build
+
+QMS_OK, QMS_EINVAL, QMS_ENOMEM, QMS_EBUDGET, QMS_ECUDA, QMS_ETIMEOUT, QMS_EAGAIN, QMS_EINTERNAL = \
+    0, -1, -2, -3, -4, -5, -6, -7
+DTYPE_CODES = {"u32": 0, "u64": 1, "i64": 2, "f32": 3}
+PIVOTS = {"m3": 0, "sqrtn": 1, "mom": 2, "hybrid": 3}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class QmsError(RuntimeError):
+    def __init__(self, code, what):
+        super().__init__("%s failed: %s (%d)" % (what, error_string(code), code))
+        self.code = code
+
+
+class qms_options(ctypes.Structure):
+    _fields_ = [("pivot", ctypes.c_int), ("count_cmps", ctypes.c_int),
+                ("reserved0", ctypes.c_int), ("reserved1", ctypes.c_int)]
+
+
+class qms_stats(ctypes.Structure):
+    _fields_ = [("comparisons", ctypes.c_uint64), ("aux_bytes", ctypes.c_uint64),
+                ("rounds", ctypes.c_uint64), ("mom_rounds", ctypes.c_uint64),
+                ("launches", ctypes.c_uint64), ("ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Loads libqms.so, building it first if it is missing or stale."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            L = ctypes.CDLL(path, mode=ctypes.RTLD_GLOBAL)
+            vp, sz, i, u64p = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(ctypes.c_uint64)
+            sig = {
+                "qms_version": ([], i),
+                "qms_error_string": ([i], ctypes.c_char_p),
+                "qms_sort": ([vp, sz, i, ctypes.POINTER(qms_options), vp, ctypes.POINTER(qms_stats)], i),
+                "qms_sort_pairs": ([vp, vp, sz, i, ctypes.POINTER(qms_options), vp,
+                                    ctypes.POINTER(qms_stats)], i),
+                "qms_tile_sort": ([vp, vp, sz, i, vp], i),
+                "qms_partition": ([vp, vp, sz, i, i, vp, u64p, u64p], i),
+                "qms_mergesort": ([vp, vp, sz, sz, i, vp], i),
+            }
+            for name, (args, res) in sig.items():
+                f = getattr(L, name)
+                f.argtypes = args
+                f.restype = res
+            _lib = L
+    return _lib
+
+
+def error_string(code: int) -> str:
+    return lib().qms_error_string(code).decode()
+
+
+def _dtype_code(t, dtype):
+    import torch
+    if dtype is not None:
+        return DTYPE_CODES[dtype]
+    m = {torch.uint32: "u32", torch.uint64: "u64", torch.int64: "i64", torch.float32: "f32"}
+    if t.dtype not in m:
+        raise TypeError("key dtype %s needs an explicit dtype=" % t.dtype)
+    return DTYPE_CODES[m[t.dtype]]
+
+
+def _check_keys(t, dtype):
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("keys must be a contiguous CUDA tensor")
+    code = _dtype_code(t, dtype)
+    want = 4 if code in (0, 3) else 8
+    if t.element_size() != want:
+        raise ValueError("element size %d does not match dtype" % t.element_size())
+    return code
+
+
+def _check_vals(v, n):
+    if v is None:
+        return None
+    if not v.is_cuda or not v.is_contiguous() or v.element_size() != 4 or v.numel() != n:
+        raise ValueError("payload must be a contiguous CUDA tensor of n 4-byte words")
+    return ctypes.c_void_p(v.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _raise(rc, what):
+    if rc != QMS_OK:
+        raise QmsError(rc, what)
+
+
+def qms_sort(keys, pivot: str = "m3", count_cmps: bool = False, stream=None, dtype=None):
+    """Sorts ``keys`` in place; returns the qms_stats fields as a dict."""
+    code = _check_keys(keys, dtype)
+    opt = qms_options(PIVOTS[pivot], 1 if count_cmps else 0, 0, 0)
+    st = qms_stats()
+    rc = lib().qms_sort(ctypes.c_void_p(keys.data_ptr()), keys.numel(), code, ctypes.byref(opt),
+                        _stream(stream), ctypes.byref(st))
+    _raise(rc, "qms_sort")
+    return st.as_dict()
+
+
+def qms_sort_pairs(keys, vals, pivot: str = "m3", count_cmps: bool = False, stream=None, dtype=None):
+    """Sorts ``keys`` in place, moving ``vals`` with them; returns stats."""
+    code = _check_keys(keys, dtype)
+    vp = _check_vals(vals, keys.numel())
+    opt = qms_options(PIVOTS[pivot], 1 if count_cmps else 0, 0, 0)
+    st = qms_stats()
+    rc = lib().qms_sort_pairs(ctypes.c_void_p(keys.data_ptr()), vp, keys.numel(), code,
+                              ctypes.byref(opt), _stream(stream), ctypes.byref(st))
+    _raise(rc, "qms_sort_pairs")
+    return st.as_dict()
+
+
+def qms_tile_sort(keys, vals=None, stream=None, dtype=None):
+    code = _check_keys(keys, dtype)
+    rc = lib().qms_tile_sort(ctypes.c_void_p(keys.data_ptr()), _check_vals(vals, keys.numel()),
+                             keys.numel(), code, _stream(stream))
+    _raise(rc, "qms_tile_sort")
+
+
+def qms_partition(keys, vals=None, pivot: str = "m3", stream=None, dtype=None):
+    """One partition step; returns (pivot index k, further equal keys eq)."""
+    code = _check_keys(keys, dtype)
+    k = ctypes.c_uint64(0)
+    eq = ctypes.c_uint64(0)
+    rc = lib().qms_partition(ctypes.c_void_p(keys.data_ptr()), _check_vals(vals, keys.numel()),
+                             keys.numel(), code, PIVOTS[pivot], _stream(stream), ctypes.byref(k),
+                             ctypes.byref(eq))
+    _raise(rc, "qms_partition")
+    return k.value, eq.value
+
+
+def qms_mergesort(keys, m: int, buf: int, vals=None, stream=None, dtype=None):
+    """Sorts keys[0:m] using keys[buf:buf+m] as swap buffer (buf >= m)."""
+    code = _check_keys(keys, dtype)
+    if buf + m > keys.numel():
+        raise ValueError("buffer out of range")
+    rc = lib().qms_mergesort(ctypes.c_void_p(keys.data_ptr()), _check_vals(vals, keys.numel()), m,
+                             buf, code, _stream(stream))
+    _raise(rc, "qms_mergesort")
