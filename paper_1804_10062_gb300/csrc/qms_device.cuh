@@ -310,27 +310,28 @@ __device__ void leaf_sort_tile(TileSmem<K, HV> s, K* g, uint32_t* gv, K* buf, ui
 // and write disjoint Y slots, so a whole level runs without inter-block
 // synchronisation, and buffer elements are permuted, never overwritten.
 
-// Cooperative merge-path search over runs A[0, la) and B[0, lb) in global
-// memory for diagonal d: returns the number of A elements among the first d
-// outputs.  Each round every thread probes one candidate, so the window
-// shrinks NT-fold per round (about three rounds for runs of 2^26).
+// Warp-cooperative merge-path search over runs A[0, la) and B[0, lb) in
+// global memory for diagonal d: returns the number of A elements among the
+// first d outputs.  Each round the 32 lanes probe evenly spaced candidates,
+// so the window shrinks 32-fold per round.
 template <class K, bool CNT>
-__device__ uint64_t merge_path_global(const K* A, uint64_t la, const K* B, uint64_t lb,
-                                      uint64_t d, int xf, uint64_t& cmp) {
+__device__ uint64_t merge_path_warp(const K* A, uint64_t la, const K* B, uint64_t lb, uint64_t d,
+                                    int xf, uint64_t& cmp) {
+  const unsigned lane = threadIdx.x & 31u;
   uint64_t lo = d > lb ? d - lb : 0;
   uint64_t hi = d < la ? d : la;
   // The answer lies in [lo, hi]; P(m) = (A[m] <= B[d-1-m]) holds for every m
   // below the answer and fails from the answer on.
   while (hi > lo) {
     const uint64_t span = hi - lo;
-    const uint64_t step = span <= static_cast<uint64_t>(NT) ? 1 : (span + NT - 1) / NT;
-    const uint64_t m = lo + static_cast<uint64_t>(threadIdx.x) * step;
+    const uint64_t step = span <= 32u ? 1 : (span + 31u) / 32u;
+    const uint64_t m = lo + static_cast<uint64_t>(lane) * step;
     bool p = false;
     if (m < hi) {
       if (CNT) ++cmp;
       p = !(enc_key(B[d - 1 - m], xf) < enc_key(A[m], xf));
     }
-    const int c = __syncthreads_count(p);
+    const int c = __popc(__ballot_sync(0xffffffffu, p));
     if (step == 1) {
       lo += static_cast<uint64_t>(c);
       break;
@@ -343,25 +344,51 @@ __device__ uint64_t merge_path_global(const K* A, uint64_t la, const K* B, uint6
   return lo;
 }
 
+// Geometry of output tile t of a level: its run pair and diagonals.
+struct MergeGeom {
+  uint64_t pbase, la, lb, d0, d1;
+  __device__ __forceinline__ MergeGeom(uint64_t m, uint64_t L, uint64_t t) {
+    const uint64_t o0 = t * TILE;
+    const uint64_t o1 = (o0 + TILE < m) ? o0 + TILE : m;
+    pbase = (o0 / (2 * L)) * (2 * L);
+    la = (m - pbase < L) ? m - pbase : L;
+    const uint64_t rem = m - pbase - la;
+    lb = rem < L ? rem : L;
+    d0 = o0 - pbase;
+    d1 = o1 - pbase;
+  }
+};
+
+// Split step of a swap-merge level: for every output tile t, the number of
+// A elements of its run pair that precede the tile's first output.  Runs
+// before any tile of the level moves a buffer element, so every search sees
+// the unmodified runs.  One warp per tile.
+template <class K, bool CNT>
+__device__ void merge_split_warp(const K* keys, uint64_t X, uint64_t m, uint64_t L, uint64_t t,
+                                 int xf, uint64_t* splits, uint64_t& cmp) {
+  const MergeGeom g(m, L, t);
+  const K* A = keys + X + g.pbase;
+  const uint64_t a = (g.d0 == 0) ? 0 : merge_path_warp<K, CNT>(A, g.la, A + g.la, g.lb, g.d0, xf, cmp);
+  if ((threadIdx.x & 31u) == 0) splits[t] = a;
+}
+
 // One output tile of a swap-merge level (see above).  X, Y: region bases;
 // m: elements per region; L: input run length; tile: output tile index.
 template <class K, bool HV, bool CNT>
 __device__ void merge_tile(TileSmem<K, HV> s, K* keys, uint32_t* vals, uint64_t X, uint64_t Y,
-                           uint64_t m, uint64_t L, uint64_t tile, int xf, uint64_t& cmp) {
+                           uint64_t m, uint64_t L, uint64_t tile, const uint64_t* splits, int xf,
+                           uint64_t& cmp) {
+  const MergeGeom gm(m, L, tile);
   const uint64_t o0 = tile * TILE;
-  const uint64_t o1 = (o0 + TILE < m) ? o0 + TILE : m;
-  const uint64_t pbase = (o0 / (2 * L)) * (2 * L);
-  const uint64_t la = (m - pbase < L) ? m - pbase : L;
-  const uint64_t rem = m - pbase - la;
-  const uint64_t lb = rem < L ? rem : L;
-  const uint64_t d0 = o0 - pbase, d1 = o1 - pbase;
-  K* A = keys + X + pbase;
+  const uint64_t o1 = gm.pbase + gm.d1;
+  const uint64_t la = gm.la, d0 = gm.d0, d1 = gm.d1;
+  K* A = keys + X + gm.pbase;
   K* B = A + la;
-  uint32_t* Av = HV ? vals + X + pbase : nullptr;
+  uint32_t* Av = HV ? vals + X + gm.pbase : nullptr;
   uint32_t* Bv = HV ? Av + la : nullptr;
   __syncthreads();
-  const uint64_t a_lo = merge_path_global<K, CNT>(A, la, B, lb, d0, xf, cmp);
-  const uint64_t a_hi = (d1 == la + lb) ? la : merge_path_global<K, CNT>(A, la, B, lb, d1, xf, cmp);
+  const uint64_t a_lo = splits[tile];
+  const uint64_t a_hi = (d1 == la + gm.lb) ? la : splits[tile + 1];
   const int cnt = static_cast<int>(o1 - o0);
   const int na = static_cast<int>(a_hi - a_lo);
   const int nb = cnt - na;

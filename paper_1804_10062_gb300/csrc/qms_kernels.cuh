@@ -51,15 +51,30 @@ __global__ void __launch_bounds__(NT) k_leaf_sort(K* keys, uint32_t* vals, uint6
 }
 
 // One swap-merge level: runs of length L in region X -> runs of 2L in Y.
+// k_merge_split first records every tile's merge-path window (one warp per
+// tile), then k_merge_level merges and swaps.
+template <class K, bool CNT>
+__global__ void __launch_bounds__(256) k_merge_split(const K* keys, uint64_t X, uint64_t m,
+                                                     uint64_t L, int xf, uint64_t* splits,
+                                                     Desc* desc) {
+  uint64_t cmp = 0;
+  const uint64_t ntiles = (m + TILE - 1) / TILE;
+  const uint64_t w0 = (blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x) >> 5;
+  const uint64_t nw = (static_cast<uint64_t>(gridDim.x) * blockDim.x) >> 5;
+  for (uint64_t t = w0; t < ntiles; t += nw) merge_split_warp<K, CNT>(keys, X, m, L, t, xf, splits, cmp);
+  if (CNT) flush_count(cmp, &desc->cmp);
+}
+
 template <class K, bool HV, bool CNT>
 __global__ void __launch_bounds__(NT) k_merge_level(K* keys, uint32_t* vals, uint64_t X, uint64_t Y,
-                                                    uint64_t m, uint64_t L, int xf, Desc* desc) {
+                                                    uint64_t m, uint64_t L, const uint64_t* splits,
+                                                    int xf, Desc* desc) {
   extern __shared__ __align__(16) unsigned char smem[];
   const auto s = TileSmem<K, HV>::carve(smem);
   uint64_t cmp = 0;
   const uint64_t ntiles = (m + TILE - 1) / TILE;
   for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    merge_tile<K, HV, CNT>(s, keys, vals, X, Y, m, L, t, xf, cmp);
+    merge_tile<K, HV, CNT>(s, keys, vals, X, Y, m, L, t, splits, xf, cmp);
   }
   if (CNT) flush_count(cmp, &desc->cmp);
 }

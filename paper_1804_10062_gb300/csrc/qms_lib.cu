@@ -58,11 +58,12 @@ struct Workspace {
   uint32_t* counts = nullptr;
   uint64_t* pml = nullptr;
   uint64_t* pmr = nullptr;
+  uint64_t* splits = nullptr;
   cudaStream_t st = nullptr;
 
   static size_t size_for(uint64_t n) {
     const uint64_t nt = n / TILE + 2;
-    return ((sizeof(Desc) + 255) / 256) * 256 + ((nt * 4 + 255) / 256) * 256 + 2 * (nt + 1) * 8;
+    return ((sizeof(Desc) + 255) / 256) * 256 + ((nt * 4 + 255) / 256) * 256 + 3 * (nt + 1) * 8;
   }
   void alloc(uint64_t n, cudaStream_t s) {
     st = s;
@@ -81,6 +82,8 @@ struct Workspace {
     pml = reinterpret_cast<uint64_t*>(base + off);
     off += (nt + 1) * 8;
     pmr = reinterpret_cast<uint64_t*>(base + off);
+    off += (nt + 1) * 8;
+    splits = reinterpret_cast<uint64_t*>(base + off);
     ck(cudaMemsetAsync(desc, 0, sizeof(Desc), s));
   }
   ~Workspace() {
@@ -128,9 +131,11 @@ class Sorter {
     uint64_t X = to_buf ? Bb : P, Y = to_buf ? P : Bb;
     for (int l = 0; l < levels; ++l) {
       const uint64_t L = static_cast<uint64_t>(TILE) << l;
+      k_merge_split<K, CNT><<<grid_of((leaves + 7) / 8), 256, 0, st_>>>(keys_, X, m, L, xf_,
+                                                                          ws_.splits, ws_.desc);
       k_merge_level<K, HV, CNT><<<grid_of(leaves), NT, tile_smem_bytes<K, HV>(), st_>>>(
-          keys_, vals_, X, Y, m, L, xf_, ws_.desc);
-      launched();
+          keys_, vals_, X, Y, m, L, ws_.splits, xf_, ws_.desc);
+      launched(2);
       std::swap(X, Y);
     }
   }
