@@ -1,0 +1,347 @@
+"""Benchmark of the GB300 QuickMergesort path.
+
+Default workload: plain QuickMergesort with the median-of-3 pivot on one
+array of n = 2^28 uint32 keys, uniformly random (SplitMix64, seed 2 + rank),
+one array per GPU (replicas: the plain sort does not shard).  A step is one
+whole sort of one array; inputs (1 GiB each) are resident in HBM before the
+timed region and are larger than L2, so no flush is needed.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle on
+a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import signal
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+DTYPE_BYTES = {"u32": 4, "u64": 8, "i64": 8, "f32": 4}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="qms", choices=["qms", "reference"])
+    ap.add_argument("--lgn", type=int, default=28)
+    ap.add_argument("--dtype", default="u32", choices=list(DTYPE_BYTES))
+    ap.add_argument("--pivot", default="m3", choices=["m3", "sqrtn", "mom", "hybrid"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_init(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def keys_for(args, seed):
+    import qms_inputs as gen
+    n = 1 << args.lgn
+    dist = "normal" if args.dtype == "f32" else "uniform"
+    return gen.keys(dist, args.dtype, n, seed)
+
+
+def workload_name(args):
+    return "plain QuickMergesort, %s pivot, one array of n=2^%d %s keys (%s)" % (
+        {"m3": "median-of-3", "sqrtn": "median-of-sqrt(n)", "mom": "median-of-medians",
+         "hybrid": "hybrid median-of-3/median-of-medians"}[args.pivot], args.lgn, args.dtype,
+        "N(0,1)" if args.dtype == "f32" else "uniform")
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.send_signal(signal.SIGINT)
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# roofline helpers
+
+
+def measured_peak_hbm():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def source_sha():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1804_10062_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        if fn.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, fn), "rb") as f:
+                h.update(fn.encode())
+                h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic_per_byte(kernel):
+    """DRAM bytes per algorithmic byte of `kernel` from the committed ncu
+    summary, or None when the summary is missing or the sources changed."""
+    p = os.path.join(ROOT, "profiles", "%s_traffic.md" % kernel)
+    try:
+        txt = open(p).read()
+    except OSError:
+        return None
+    m1 = re.search(r"source_sha:\s*([0-9a-f]+)", txt)
+    m2 = re.search(r"dram_bytes_per_algorithmic_byte:\s*([0-9.]+)", txt)
+    if not m1 or not m2 or m1.group(1) != source_sha():
+        return None
+    return float(m2.group(1))
+
+
+# ---------------------------------------------------------------------------
+
+
+def cpu_baseline(args, lg_sample=24, runs=3):
+    import numpy as np  # noqa: F401
+    import oracle
+    import qms_inputs as gen
+    n = 1 << lg_sample
+    dist = "normal" if args.dtype == "f32" else "uniform"
+    k0 = gen.keys(dist, args.dtype, n, 1000)
+    oracle.lib()
+    ts = []
+    for _ in range(runs):
+        k = k0.copy()
+        t0 = time.perf_counter()
+        oracle.sort(k, variant=args.pivot, mode="paper")
+        ts.append(time.perf_counter() - t0)
+    total = sum(ts)
+    return {"value": runs * n / total / 1e9, "unit": "GKeys/s", "cores": 1, "kind": "oracle",
+            "sample": "%d runs of the single-threaded oracle on n=2^%d %s keys (the same "
+                      "distribution, %.1f s of CPU work)" % (runs, lg_sample, args.dtype, total)}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_init(args)
+    if rank != 0:
+        return 0
+    import oracle
+    import qms_inputs as gen
+    lg = min(args.lgn, 22)
+    n = 1 << lg
+    dist = "normal" if args.dtype == "f32" else "uniform"
+    k0 = gen.keys(dist, args.dtype, n, 2)
+    oracle.lib()
+    for _ in range(args.warmup):
+        oracle.sort(k0.copy(), variant=args.pivot, mode="paper")
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.sort(k0.copy(), variant=args.pivot, mode="paper")
+    el = time.perf_counter() - t0
+    v = args.steps * n / el / 1e9
+    line = {"impl": "reference", "metric": "GKeys/s (plain sort)", "value": v, "unit": "GKeys/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
+            "config": {"workload": workload_name(args), "n": 1 << args.lgn, "pivot": args.pivot},
+            "cpu_baseline": {"value": v, "unit": "GKeys/s", "cores": 1, "kind": "oracle",
+                             "sample": "each step sorts n=2^%d keys of the workload's "
+                                       "distribution with the single-threaded oracle" % lg},
+            "e2e": {"value": v, "unit": "GKeys/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_qms(args):
+    import numpy as np
+    import torch
+    ws, rank, local = dist_init(args)
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    import paper_1804_10062_gb300 as q
+    q.lib()
+    n = 1 << args.lgn
+    esz = DTYPE_BYTES[args.dtype]
+    host = keys_for(args, 2 + rank)
+    tdt = torch.int32 if esz == 4 else torch.int64
+    src = torch.from_numpy(host.view(np.int32 if esz == 4 else np.int64)).cuda()
+    stream = torch.cuda.current_stream()
+    bufs = [torch.empty_like(src) for _ in range(args.steps)]
+    for b in bufs:
+        b.copy_(src)
+    work = torch.empty_like(src)
+    for _ in range(args.warmup):
+        work.copy_(src)
+        q.qms_sort(work, pivot=args.pivot, dtype=args.dtype)
+    torch.cuda.synchronize()
+
+    prof = q.qms_profile()
+    launches = 0
+    clocks = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(args.steps):
+        st = q.qms_sort(bufs[i], pivot=args.pivot, dtype=args.dtype, profile=prof)
+        launches += st["launches"]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ck = clocks.stop()
+    el_ms = e0.elapsed_time(e1)
+    t = torch.tensor([el_ms], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    el_ms = float(t.item())
+    # spot check of the result (full parity lives in the tests)
+    out = bufs[0][: min(n, 1 << 20)].cpu().numpy()
+    if args.dtype in ("u32", "u64"):
+        out = out.view(np.uint32 if esz == 4 else np.uint64)
+    if args.dtype != "f32":
+        assert np.all(out[1:] >= out[:-1]), "result not sorted"
+
+    value = ws * args.steps * n / (el_ms / 1e3) / 1e9
+    pd = prof.as_dict()
+    dom = max(pd, key=lambda k: pd[k]["ms"])
+    peak, peak_kind = measured_peak_hbm()
+    achieved = pd[dom]["bytes"] / (pd[dom]["ms"] / 1e3) / 1e9 if pd[dom]["ms"] > 0 else 0.0
+    tpb = ncu_traffic_per_byte(dom)
+    per_launch_alg = pd[dom]["bytes"] / max(1, pd[dom]["launches"])
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
+                "traffic": (tpb * per_launch_alg) if tpb is not None else None,
+                "alg_bytes_per_launch": per_launch_alg,
+                "kernels": {k: {"ms": round(v["ms"] / args.steps, 4),
+                                "share": round(v["ms"] / max(1e-9, sum(x["ms"] for x in pd.values())), 4),
+                                "GBps": round(v["bytes"] / (v["ms"] / 1e3) / 1e9, 1) if v["ms"] > 0 else None,
+                                "launches": v["launches"] // args.steps}
+                            for k, v in pd.items() if v["launches"]}}
+
+    e2e = None
+    if not args.no_e2e:
+        hbuf = torch.empty(n, dtype=tdt, pin_memory=True)
+        hbuf.copy_(torch.from_numpy(host.view(np.int32 if esz == 4 else np.int64)))
+        hout = torch.empty(n, dtype=tdt, pin_memory=True)
+        dwork = torch.empty(n, dtype=tdt, device="cuda")
+        ksteps = max(1, min(args.steps, 3))
+        barrier()
+        torch.cuda.synchronize()
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for _ in range(ksteps):
+            dwork.copy_(hbuf, non_blocking=True)
+            q.qms_sort(dwork, pivot=args.pivot, dtype=args.dtype)
+            hout.copy_(dwork, non_blocking=True)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        e_ms = a0.elapsed_time(a1)
+        tt = torch.tensor([e_ms], dtype=torch.float64, device="cuda")
+        if dist is not None:
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e_ms = float(tt.item())
+        e2e = {"value": ws * ksteps * n / (e_ms / 1e3) / 1e9, "unit": "GKeys/s",
+               "h2d_bytes_per_step": n * esz, "d2h_bytes_per_step": n * esz,
+               "steps": ksteps, "api": "qms_sort via the C ABI, host pinned buffers"}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args)
+
+    if rank == 0:
+        line = {"metric": "GKeys/s (plain sort); %% HBM roofline of the dominant kernel",
+                "value": value, "unit": "GKeys/s", "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": el_ms / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": args.dtype, "data": "synthetic",
+                "config": {"workload": workload_name(args), "n": n, "pivot": args.pivot,
+                           "arrays_per_gpu_step": 1, "l2": "inputs larger than L2 (%d MiB per "
+                           "array), no flush" % (n * esz >> 20),
+                           "parallelism": "replicas" if ws > 1 else "single GPU"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": launches, "clocks": ck}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_qms(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

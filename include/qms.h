@@ -60,12 +60,34 @@ extern "C" {
 #define QMS_PIVOT_MOM 2
 #define QMS_PIVOT_HYBRID 3
 
+/* Kernel classes of the per-kernel device-time profile. */
+#define QMS_K_LEAF 0          /* base case / Mergesort leaves                  */
+#define QMS_K_MERGE_SPLIT 1   /* merge-path windows of a swap-merge level      */
+#define QMS_K_MERGE 2         /* swap-merge level                              */
+#define QMS_K_PART_LOCAL 3    /* partition: local partition of every tile      */
+#define QMS_K_PART_SCAN 4     /* partition: scan of the tile counts            */
+#define QMS_K_PART_EXCHANGE 5 /* partition: exchange of misplaced elements     */
+#define QMS_K_PIVOT 6         /* pivot selection (all rules) and placement     */
+#define QMS_K_BATCH 7         /* batched-form kernels                          */
+#define QMS_NKINDS 8
+
+/* Optional per-kernel-class profile, filled when qms_options.profile is set:
+ * device time from CUDA events recorded around every launch on the call's
+ * stream, and the algorithmic bytes each class must move (keys and payloads
+ * read plus written, counted from the sizes it was launched on). */
+typedef struct {
+  double ms[QMS_NKINDS];
+  uint64_t bytes[QMS_NKINDS];
+  uint64_t launches[QMS_NKINDS];
+} qms_profile;
+
 typedef struct {
   int pivot;       /* QMS_PIVOT_*                                              */
   int count_cmps;  /* nonzero: use the counting kernels and report
                       qms_stats.comparisons (element comparisons, Sec. 5)      */
   int reserved0;
   int reserved1;
+  qms_profile* profile; /* NULL, or accumulates per-kernel device times      */
 } qms_options;
 
 typedef struct {

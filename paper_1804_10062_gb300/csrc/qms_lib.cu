@@ -16,6 +16,7 @@
 #include <cstdint>
 #include <cstring>
 #include <mutex>
+#include <vector>
 
 #include "../../include/qms.h"
 #include "qms_kernels.cuh"
@@ -91,11 +92,64 @@ struct Workspace {
   }
 };
 
+// Records CUDA events around launches (profiling only) and accumulates the
+// device time of each kernel class into a qms_profile after the stream has
+// been synchronised.
+class Profiler {
+ public:
+  explicit Profiler(qms_profile* out) : out_(out) {}
+  ~Profiler() {
+    for (auto& r : recs_) {
+      cudaEventDestroy(r.a);
+      cudaEventDestroy(r.b);
+    }
+  }
+  bool on() const { return out_ != nullptr; }
+  void begin(cudaStream_t st) {
+    if (!out_) return;
+    Rec r{};
+    ck(cudaEventCreate(&r.a));
+    ck(cudaEventCreate(&r.b));
+    ck(cudaEventRecord(r.a, st));
+    recs_.push_back(r);
+  }
+  void end(cudaStream_t st, int kind, uint64_t bytes) {
+    if (!out_) return;
+    Rec& r = recs_.back();
+    r.kind = kind;
+    r.bytes = bytes;
+    ck(cudaEventRecord(r.b, st));
+  }
+  // Call after the stream has been synchronised.
+  void flush() {
+    if (!out_) return;
+    for (auto& r : recs_) {
+      float ms = 0.f;
+      ck(cudaEventElapsedTime(&ms, r.a, r.b));
+      out_->ms[r.kind] += ms;
+      out_->bytes[r.kind] += r.bytes;
+      out_->launches[r.kind] += 1;
+      cudaEventDestroy(r.a);
+      cudaEventDestroy(r.b);
+    }
+    recs_.clear();
+  }
+
+ private:
+  struct Rec {
+    cudaEvent_t a, b;
+    int kind;
+    uint64_t bytes;
+  };
+  qms_profile* out_;
+  std::vector<Rec> recs_;
+};
+
 template <class K, bool HV, bool CNT>
 class Sorter {
  public:
-  Sorter(K* keys, uint32_t* vals, int xf, cudaStream_t st, Workspace& ws)
-      : keys_(keys), vals_(vals), xf_(xf), st_(st), ws_(ws) {
+  Sorter(K* keys, uint32_t* vals, int xf, cudaStream_t st, Workspace& ws, Profiler& prof)
+      : keys_(keys), vals_(vals), xf_(xf), st_(st), ws_(ws), prof_(prof) {
     static bool a1 = false, a2 = false, a3 = false, a4 = false;
     allow_smem(k_leaf_sort<K, HV, CNT>, tile_smem_bytes<K, HV>(), a1);
     allow_smem(k_merge_level<K, HV, CNT>, tile_smem_bytes<K, HV>(), a2);
@@ -104,14 +158,19 @@ class Sorter {
   }
 
   uint64_t rounds = 0, mom_rounds = 0, launches = 0;
+  uint64_t exchanged_bytes = 0;  // algorithmic bytes of the exchange steps
 
   // ---- steps ------------------------------------------------------------
+
+  static constexpr uint64_t ES = sizeof(K) + (HV ? 4 : 0);  // bytes per element
 
   void leaf(uint64_t P, uint64_t m, bool to_buf, uint64_t Bb) {
     if (m == 0) return;
     const uint64_t nt = (m + TILE - 1) / TILE;
+    prof_.begin(st_);
     k_leaf_sort<K, HV, CNT><<<grid_of(nt), NT, tile_smem_bytes<K, HV>(), st_>>>(
         keys_, vals_, P, m, Bb, to_buf ? 1 : 0, xf_, ws_.desc);
+    prof_.end(st_, QMS_K_LEAF, (to_buf ? 4 : 2) * m * ES);
     launched();
   }
 
@@ -131,10 +190,14 @@ class Sorter {
     uint64_t X = to_buf ? Bb : P, Y = to_buf ? P : Bb;
     for (int l = 0; l < levels; ++l) {
       const uint64_t L = static_cast<uint64_t>(TILE) << l;
+      prof_.begin(st_);
       k_merge_split<K, CNT><<<grid_of((leaves + 7) / 8), 256, 0, st_>>>(keys_, X, m, L, xf_,
                                                                           ws_.splits, ws_.desc);
+      prof_.end(st_, QMS_K_MERGE_SPLIT, 0);
+      prof_.begin(st_);
       k_merge_level<K, HV, CNT><<<grid_of(leaves), NT, tile_smem_bytes<K, HV>(), st_>>>(
           keys_, vals_, X, Y, m, L, ws_.splits, xf_, ws_.desc);
+      prof_.end(st_, QMS_K_MERGE, 4 * m * ES);
       launched(2);
       std::swap(X, Y);
     }
@@ -144,6 +207,7 @@ class Sorter {
   // fallback rounds).
   void pivot(uint64_t b, uint64_t e, int rule) {
     const uint64_t n = e - b;
+    prof_.begin(st_);
     if (rule == QMS_PIVOT_SQRTN) {
       uint64_t c = 1;
       while (c * c < n) ++c;  // ceil(sqrt(n)); n < 2^40 here
@@ -178,6 +242,7 @@ class Sorter {
       k_pivot_m3<K, HV, CNT><<<1, 32, 0, st_>>>(keys_, vals_, b, e, xf_, ws_.desc);
       launched();
     }
+    prof_.end(st_, QMS_K_PIVOT, 0);
   }
 
   // Partitions [lo, hi) around the descriptor's pivot (le: "<=" pass);
@@ -187,32 +252,41 @@ class Sorter {
     const uint64_t n = hi - lo;
     const uint64_t nt = (n + TILE - 1) / TILE;
     if (n > 0) {
+      prof_.begin(st_);
       k_part_local<K, HV, CNT><<<grid_of(nt), NT, tile_smem_bytes<K, HV>(), st_>>>(
           keys_, vals_, lo, hi, le ? 1 : 0, xf_, ws_.desc, ws_.counts);
+      prof_.end(st_, QMS_K_PART_LOCAL, 2 * n * ES);
+      prof_.begin(st_);
       k_part_scan<<<1, NT, 0, st_>>>(ws_.counts, static_cast<uint32_t>(nt), lo, hi, ws_.pml,
                                      ws_.pmr, ws_.desc);
+      prof_.end(st_, QMS_K_PART_SCAN, nt * 20);
       const uint64_t maxmis = n / 2 + 1;
       const uint64_t per = static_cast<uint64_t>(NT) * EXV;
+      prof_.begin(st_);
       k_part_exchange<K, HV><<<grid_of((maxmis + per - 1) / per), NT, 0, st_>>>(
           keys_, vals_, lo, ws_.counts, ws_.pml, ws_.pmr, static_cast<uint32_t>(nt), ws_.desc);
+      prof_.end(st_, QMS_K_PART_EXCHANGE, 0);  // bytes added once mis is known
       launched(3);
     } else {
       ck(cudaMemsetAsync(&ws_.desc->L, 0, sizeof(unsigned long long), st_));
     }
     if (parked != ~0ull) {
+      prof_.begin(st_);
       k_place_pivot<K, HV><<<1, 32, 0, st_>>>(keys_, vals_, lo, parked, ws_.desc);
+      prof_.end(st_, QMS_K_PIVOT, 0);
       launched();
     }
     struct {
-      unsigned long long L;
+      unsigned long long L, mis;
       unsigned tie, err;
     } h;
-    ck(cudaMemcpyAsync(&h.L, &ws_.desc->L, sizeof(h.L), cudaMemcpyDeviceToHost, st_));
+    ck(cudaMemcpyAsync(&h.L, &ws_.desc->L, 2 * sizeof(h.L), cudaMemcpyDeviceToHost, st_));
     ck(cudaMemcpyAsync(&h.tie, &ws_.desc->tie, 2 * sizeof(unsigned), cudaMemcpyDeviceToHost, st_));
     ck(cudaStreamSynchronize(st_));
     ck(cudaGetLastError());
     if (h.err) throw Err{QMS_EINTERNAL};
     if (tie) *tie = h.tie;
+    exchanged_bytes += (n > 0) ? 4 * h.mis * ES : 0;
     return h.L;
   }
 
@@ -269,6 +343,7 @@ class Sorter {
   int xf_;
   cudaStream_t st_;
   Workspace& ws_;
+  Profiler& prof_;
 };
 
 struct Args {
@@ -279,6 +354,7 @@ struct Args {
   int pivot;
   bool count;
   cudaStream_t st;
+  qms_profile* prof;
 };
 
 template <class K, bool HV, bool CNT, class Fn>
@@ -286,12 +362,15 @@ int run_typed(const Args& a, qms_stats* stats, Fn&& fn) {
   const auto t0 = std::chrono::steady_clock::now();
   Workspace ws;
   ws.alloc(a.n, a.st);
-  Sorter<K, HV, CNT> s(static_cast<K*>(a.keys), a.vals, xform_of(a.dtype), a.st, ws);
+  Profiler prof(a.prof);
+  Sorter<K, HV, CNT> s(static_cast<K*>(a.keys), a.vals, xform_of(a.dtype), a.st, ws, prof);
   fn(s);
   unsigned long long cmp = 0;
   if (CNT) ck(cudaMemcpyAsync(&cmp, &ws.desc->cmp, sizeof(cmp), cudaMemcpyDeviceToHost, a.st));
   ck(cudaStreamSynchronize(a.st));
   ck(cudaGetLastError());
+  prof.flush();
+  if (a.prof) a.prof->bytes[QMS_K_PART_EXCHANGE] += s.exchanged_bytes;
   if (stats) {
     stats->comparisons = cmp;
     stats->aux_bytes = ws.bytes;
@@ -355,7 +434,8 @@ static int sort_common(void* d_keys, uint32_t* d_vals, size_t n, int dtype, cons
   if (n <= 1) return QMS_OK;
   if (d_keys == nullptr) return QMS_EINVAL;
   if (d_vals != nullptr && n >= (1ull << 32)) return QMS_EINVAL;
-  Args a{d_keys, d_vals, n, dtype, pivot, opt && opt->count_cmps, static_cast<cudaStream_t>(stream)};
+  Args a{d_keys, d_vals, n, dtype, pivot, opt && opt->count_cmps, static_cast<cudaStream_t>(stream),
+         opt ? opt->profile : nullptr};
   return dispatch(a, stats, [&](auto& s) { s.sort(n, pivot); });
 }
 
@@ -374,7 +454,7 @@ int qms_tile_sort(void* d_keys, uint32_t* d_vals, size_t n, int dtype, void* str
   if (!valid_dtype(dtype) || n > static_cast<size_t>(TILE)) return QMS_EINVAL;
   if (n <= 1) return QMS_OK;
   if (d_keys == nullptr) return QMS_EINVAL;
-  Args a{d_keys, d_vals, n, dtype, 0, false, static_cast<cudaStream_t>(stream)};
+  Args a{d_keys, d_vals, n, dtype, 0, false, static_cast<cudaStream_t>(stream), nullptr};
   return dispatch(a, nullptr, [&](auto& s) { s.leaf(0, n, false, 0); });
 }
 
@@ -384,7 +464,7 @@ int qms_partition(void* d_keys, uint32_t* d_vals, size_t n, int dtype, int pivot
     return QMS_EINVAL;
   if (pivot < QMS_PIVOT_M3 || pivot > QMS_PIVOT_MOM) return QMS_EINVAL;
   if (d_vals != nullptr && n >= (1ull << 32)) return QMS_EINVAL;
-  Args a{d_keys, d_vals, n, dtype, pivot, false, static_cast<cudaStream_t>(stream)};
+  Args a{d_keys, d_vals, n, dtype, pivot, false, static_cast<cudaStream_t>(stream), nullptr};
   return dispatch(a, nullptr, [&](auto& s) {
     uint64_t k, eq;
     s.split(0, n, pivot, &k, &eq);
@@ -396,7 +476,7 @@ int qms_partition(void* d_keys, uint32_t* d_vals, size_t n, int dtype, int pivot
 int qms_mergesort(void* d_keys, uint32_t* d_vals, size_t m, size_t buf, int dtype, void* stream) {
   if (!valid_dtype(dtype) || (m > 1 && d_keys == nullptr) || buf < m) return QMS_EINVAL;
   if (m <= 1) return QMS_OK;
-  Args a{d_keys, d_vals, buf + m, dtype, 0, false, static_cast<cudaStream_t>(stream)};
+  Args a{d_keys, d_vals, buf + m, dtype, 0, false, static_cast<cudaStream_t>(stream), nullptr};
   return dispatch(a, nullptr, [&](auto& s) { s.mergesort(0, m, buf); });
 }
 

@@ -28,9 +28,24 @@ class QmsError(RuntimeError):
         self.code = code
 
 
+NKINDS = 8
+KIND_NAMES = ["leaf", "merge_split", "merge", "part_local", "part_scan", "part_exchange", "pivot",
+              "batch"]
+
+
+class qms_profile(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_double * NKINDS), ("bytes", ctypes.c_uint64 * NKINDS),
+                ("launches", ctypes.c_uint64 * NKINDS)]
+
+    def as_dict(self):
+        return {KIND_NAMES[i]: {"ms": self.ms[i], "bytes": self.bytes[i],
+                                "launches": self.launches[i]} for i in range(NKINDS)}
+
+
 class qms_options(ctypes.Structure):
     _fields_ = [("pivot", ctypes.c_int), ("count_cmps", ctypes.c_int),
-                ("reserved0", ctypes.c_int), ("reserved1", ctypes.c_int)]
+                ("reserved0", ctypes.c_int), ("reserved1", ctypes.c_int),
+                ("profile", ctypes.POINTER(qms_profile))]
 
 
 class qms_stats(ctypes.Structure):
@@ -115,10 +130,20 @@ def _raise(rc, what):
         raise QmsError(rc, what)
 
 
-def qms_sort(keys, pivot: str = "m3", count_cmps: bool = False, stream=None, dtype=None):
-    """Sorts ``keys`` in place; returns the qms_stats fields as a dict."""
+def _options(pivot, count_cmps, profile):
+    opt = qms_options(PIVOTS[pivot], 1 if count_cmps else 0, 0, 0, None)
+    if profile is not None:
+        opt.profile = ctypes.pointer(profile)
+    return opt
+
+
+def qms_sort(keys, pivot: str = "m3", count_cmps: bool = False, stream=None, dtype=None,
+             profile: qms_profile | None = None):
+    """Sorts ``keys`` in place; returns the qms_stats fields as a dict.
+
+    ``profile`` (a qms_profile) accumulates per-kernel device times."""
     code = _check_keys(keys, dtype)
-    opt = qms_options(PIVOTS[pivot], 1 if count_cmps else 0, 0, 0)
+    opt = _options(pivot, count_cmps, profile)
     st = qms_stats()
     rc = lib().qms_sort(ctypes.c_void_p(keys.data_ptr()), keys.numel(), code, ctypes.byref(opt),
                         _stream(stream), ctypes.byref(st))
@@ -126,11 +151,12 @@ def qms_sort(keys, pivot: str = "m3", count_cmps: bool = False, stream=None, dty
     return st.as_dict()
 
 
-def qms_sort_pairs(keys, vals, pivot: str = "m3", count_cmps: bool = False, stream=None, dtype=None):
+def qms_sort_pairs(keys, vals, pivot: str = "m3", count_cmps: bool = False, stream=None, dtype=None,
+                   profile: qms_profile | None = None):
     """Sorts ``keys`` in place, moving ``vals`` with them; returns stats."""
     code = _check_keys(keys, dtype)
     vp = _check_vals(vals, keys.numel())
-    opt = qms_options(PIVOTS[pivot], 1 if count_cmps else 0, 0, 0)
+    opt = _options(pivot, count_cmps, profile)
     st = qms_stats()
     rc = lib().qms_sort_pairs(ctypes.c_void_p(keys.data_ptr()), vp, keys.numel(), code,
                               ctypes.byref(opt), _stream(stream), ctypes.byref(st))
