@@ -140,6 +140,31 @@ int qms_partition(void* d_keys, uint32_t* d_vals, size_t n, int dtype, int pivot
  * and its order permuted. */
 int qms_mergesort(void* d_keys, uint32_t* d_vals, size_t m, size_t buf, int dtype, void* stream);
 
+/* ---- Allocation-free sort -------------------------------------------- */
+
+/* Largest n accepted by qms_sort_noalloc. */
+#define QMS_NOALLOC_MAX_N (1ull << 24)
+
+/* qms_sort without any device allocation.  The paper has no counterpart:
+ * this entry point exists for callers that cannot allocate device memory,
+ * e.g. an application that gives the whole GPU memory to its own pool
+ * allocator and forbids any other cudaMalloc, or a latency-critical loop in
+ * which an allocation could synchronise the device or fail under memory
+ * pressure.  The sort's round descriptor and per-tile counters live in one
+ * fixed file-scope device array of about 60 KB, which every GPU that loads
+ * the library holds until the process exits.  The caller passes the keys as
+ * with qms_sort (keys only; opt->profile must be NULL).
+ *   - n > QMS_NOALLOC_MAX_N (2^24) returns QMS_EINVAL; nothing runs.
+ *   - No cudaMalloc, cudaFree or allocating library routine is called.
+ *   - The first call on a device looks up the array's device address (with
+ *     that device current); make that first call before any stream capture.
+ *   - All calls share the one array and it keeps the last call's contents
+ *     (each call clears what must start at zero).  Calls that overlap on the
+ *     GPU (other streams, other host threads) race on it: serialise them.
+ * Returns as qms_sort. */
+int qms_sort_noalloc(void* d_keys, size_t n, int dtype, const qms_options* opt, void* stream,
+                     qms_stats* stats);
+
 #ifdef __cplusplus
 }
 #endif

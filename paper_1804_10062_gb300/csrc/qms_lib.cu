@@ -402,6 +402,96 @@ int dispatch(const Args& a, qms_stats* stats, Fn&& fn) {
 
 bool valid_dtype(int d) { return d >= QMS_U32 && d <= QMS_F32; }
 
+// ---------------------------------------------------------------------------
+// Allocation-free variant of qms_sort (qms_sort_noalloc).
+//
+// Some callers cannot allocate device memory: an application that gives all
+// of the GPU's memory to its own pool allocator and forbids any other
+// cudaMalloc, or a latency-critical loop in which an allocation could
+// synchronise the device or fail under memory pressure.  For them the round
+// descriptor and the per-tile counters of one sort live in a fixed-size
+// file-scope device array instead of a workspace allocated per call.
+
+constexpr size_t round256(size_t x) { return (x + 255) / 256 * 256; }
+constexpr uint64_t kNoallocMaxN = QMS_NOALLOC_MAX_N;
+constexpr size_t kNoallocTiles = kNoallocMaxN / TILE + 2;
+constexpr size_t kNoallocBytes =
+    round256(sizeof(Desc)) + round256(kNoallocTiles * 4) + 3 * (kNoallocTiles + 1) * 8;
+
+}  // namespace
+}  // namespace qms
+
+// Scratch of qms_sort_noalloc (about 60 KB).  Every GPU that loads this
+// library holds it until the process exits.  All calls share it.
+static __device__ __align__(256) unsigned char qms_noalloc_scratch[qms::kNoallocBytes];
+
+namespace qms {
+namespace {
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[256] = {};
+
+// Device address of the scratch array on the current device.  In host code
+// the array's name is only a host-side stand-in, so the address is looked up
+// once per device (with that device current) and cached.
+int noalloc_scratch(unsigned char** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) {
+    (void)cudaGetLastError();
+    return QMS_ECUDA;
+  }
+  std::lock_guard<std::mutex> g(g_noalloc_mu);
+  if (g_noalloc_ptr[dev] == nullptr) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, qms_noalloc_scratch);
+    if (e != cudaSuccess || p == nullptr) {
+      (void)cudaGetLastError();
+      return QMS_ECUDA;
+    }
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = static_cast<unsigned char*>(g_noalloc_ptr[dev]);
+  return QMS_OK;
+}
+
+template <class K, bool CNT>
+int run_noalloc(void* keys, uint64_t n, int dtype, int pivot, cudaStream_t st,
+                unsigned char* base, qms_stats* stats) {
+  const auto t0 = std::chrono::steady_clock::now();
+  Workspace ws;  // base stays null: nothing is allocated and nothing is freed
+  ws.st = st;
+  ws.bytes = kNoallocBytes;
+  size_t off = 0;
+  ws.desc = reinterpret_cast<Desc*>(base + off);
+  off += round256(sizeof(Desc));
+  ws.counts = reinterpret_cast<uint32_t*>(base + off);
+  off += round256(kNoallocTiles * 4);
+  ws.pml = reinterpret_cast<uint64_t*>(base + off);
+  off += (kNoallocTiles + 1) * 8;
+  ws.pmr = reinterpret_cast<uint64_t*>(base + off);
+  off += (kNoallocTiles + 1) * 8;
+  ws.splits = reinterpret_cast<uint64_t*>(base + off);
+  // The array keeps the previous call's contents: the descriptor (counters,
+  // flags, selection state) must start from zero.
+  ck(cudaMemsetAsync(ws.desc, 0, sizeof(Desc), st));
+  Profiler prof(nullptr);
+  Sorter<K, false, CNT> s(static_cast<K*>(keys), nullptr, xform_of(dtype), st, ws, prof);
+  s.sort(n, pivot);
+  unsigned long long cmp = 0;
+  if (CNT) ck(cudaMemcpyAsync(&cmp, &ws.desc->cmp, sizeof(cmp), cudaMemcpyDeviceToHost, st));
+  ck(cudaStreamSynchronize(st));
+  ck(cudaGetLastError());
+  if (stats) {
+    stats->comparisons = cmp;
+    stats->aux_bytes = kNoallocBytes;
+    stats->rounds = s.rounds;
+    stats->mom_rounds = s.mom_rounds;
+    stats->launches = s.launches;
+    stats->ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  }
+  return QMS_OK;
+}
+
 }  // namespace
 }  // namespace qms
 
@@ -478,6 +568,35 @@ int qms_mergesort(void* d_keys, uint32_t* d_vals, size_t m, size_t buf, int dtyp
   if (m <= 1) return QMS_OK;
   Args a{d_keys, d_vals, buf + m, dtype, 0, false, static_cast<cudaStream_t>(stream), nullptr};
   return dispatch(a, nullptr, [&](auto& s) { s.mergesort(0, m, buf); });
+}
+
+int qms_sort_noalloc(void* d_keys, size_t n, int dtype, const qms_options* opt, void* stream,
+                     qms_stats* stats) {
+  if (stats) std::memset(stats, 0, sizeof(*stats));
+  if (!valid_dtype(dtype)) return QMS_EINVAL;
+  const int pivot = opt ? opt->pivot : QMS_PIVOT_M3;
+  if (pivot < QMS_PIVOT_M3 || pivot > QMS_PIVOT_HYBRID) return QMS_EINVAL;
+  if (opt && opt->profile) return QMS_EINVAL;
+  if (n > kNoallocMaxN) return QMS_EINVAL;
+  if (n <= 1) return QMS_OK;
+  if (d_keys == nullptr) return QMS_EINVAL;
+  unsigned char* base = nullptr;
+  const int rc = noalloc_scratch(&base);
+  if (rc != QMS_OK) return rc;
+  const cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const bool cnt = opt && opt->count_cmps;
+  try {
+    if (dtype == QMS_U64 || dtype == QMS_I64) {
+      return cnt ? run_noalloc<uint64_t, true>(d_keys, n, dtype, pivot, st, base, stats)
+                 : run_noalloc<uint64_t, false>(d_keys, n, dtype, pivot, st, base, stats);
+    }
+    return cnt ? run_noalloc<uint32_t, true>(d_keys, n, dtype, pivot, st, base, stats)
+               : run_noalloc<uint32_t, false>(d_keys, n, dtype, pivot, st, base, stats);
+  } catch (const Err& e) {
+    return e.code;
+  } catch (...) {
+    return QMS_EINTERNAL;
+  }
 }
 
 }  // extern "C"

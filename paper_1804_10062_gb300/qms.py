@@ -78,6 +78,8 @@ def lib():
                 "qms_tile_sort": ([vp, vp, sz, i, vp], i),
                 "qms_partition": ([vp, vp, sz, i, i, vp, u64p, u64p], i),
                 "qms_mergesort": ([vp, vp, sz, sz, i, vp], i),
+                "qms_sort_noalloc": ([vp, sz, i, ctypes.POINTER(qms_options), vp,
+                                      ctypes.POINTER(qms_stats)], i),
             }
             for name, (args, res) in sig.items():
                 f = getattr(L, name)
@@ -191,3 +193,18 @@ def qms_mergesort(keys, m: int, buf: int, vals=None, stream=None, dtype=None):
     rc = lib().qms_mergesort(ctypes.c_void_p(keys.data_ptr()), _check_vals(vals, keys.numel()), m,
                              buf, code, _stream(stream))
     _raise(rc, "qms_mergesort")
+
+
+QMS_NOALLOC_MAX_N = 1 << 24
+
+
+def qms_sort_noalloc(keys, pivot: str = "m3", count_cmps: bool = False, stream=None, dtype=None):
+    """qms_sort without device allocation (n <= 2^24; scratch is a fixed
+    device array shared by all calls: do not overlap calls on the GPU)."""
+    code = _check_keys(keys, dtype)
+    opt = _options(pivot, count_cmps, None)
+    st = qms_stats()
+    rc = lib().qms_sort_noalloc(ctypes.c_void_p(keys.data_ptr()), keys.numel(), code,
+                                ctypes.byref(opt), _stream(stream), ctypes.byref(st))
+    _raise(rc, "qms_sort_noalloc")
+    return st.as_dict()
