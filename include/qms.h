@@ -118,6 +118,18 @@ int qms_sort(void* d_keys, size_t n, int dtype, const qms_options* opt, void* st
 int qms_sort_pairs(void* d_keys, uint32_t* d_vals, size_t n, int dtype, const qms_options* opt,
                    void* stream, qms_stats* stats);
 
+/* Batched form: sorts every segment d_keys[off[i], off[i+1]) independently,
+ * i < nseg, where off = d_offsets (DEVICE array of nseg + 1 non-decreasing
+ * uint64 offsets into d_keys).  Each segment is one QuickMergesort (the same
+ * method as qms_sort).  Segments of up to 64 * 8192 keys are sorted by one
+ * thread block each in one persistent launch, longest first (an atomic ticket
+ * hands out the next segment); longer segments run through the grid-wide
+ * driver.  d_vals may be NULL; with payloads the total length must be < 2^32.
+ * Extra device memory: O(nseg) words.  Errors: QMS_EINVAL (decreasing
+ * offsets, bad dtype/pivot), QMS_ENOMEM, QMS_ECUDA, QMS_EINTERNAL. */
+int qms_sort_batched(void* d_keys, uint32_t* d_vals, const uint64_t* d_offsets, size_t nseg,
+                     int dtype, const qms_options* opt, void* stream, qms_stats* stats);
+
 /* ---- Step-level entry points (one step of a round each; used by the
  * ---- parity tests of the individual kernels). ------------------------- */
 

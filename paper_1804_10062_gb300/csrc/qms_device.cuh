@@ -223,60 +223,77 @@ __device__ __forceinline__ void serial_merge(const K* sk, int ai, int ae, int bi
 // log2(NT) rounds of merge-path merges in shared memory.
 
 template <class K, bool HV, bool CNT>
-__device__ void block_sort_tile(TileSmem<K, HV> s, uint64_t& cmp) {
+__device__ void block_sort_tile(TileSmem<K, HV> s, uint64_t& cmp, int P = NT) {
+  // P (a power of two <= NT): threads holding data; items beyond the data
+  // are padding keys, so the first P*V items end up sorted.
   const int tid = threadIdx.x;
   K k[V];
   uint32_t v[V];
   int src[V];
   __syncthreads();
+  if (tid < P) {
 #pragma unroll
-  for (int j = 0; j < V; ++j) {
-    k[j] = s.k[sk_i<K>(tid * V + j)];
-    if (HV) v[j] = s.v[sv_i(tid * V + j)];
-  }
+    for (int j = 0; j < V; ++j) {
+      k[j] = s.k[sk_i<K>(tid * V + j)];
+      if (HV) v[j] = s.v[sv_i(tid * V + j)];
+    }
 #pragma unroll
-  for (int r = 0; r < V; ++r) {
+    for (int r = 0; r < V; ++r) {
 #pragma unroll
-    for (int i = r & 1; i + 1 < V; i += 2) {
-      if (k[i + 1] < k[i]) {
-        const K t = k[i];
-        k[i] = k[i + 1];
-        k[i + 1] = t;
-        if (HV) {
-          const uint32_t u = v[i];
-          v[i] = v[i + 1];
-          v[i + 1] = u;
+      for (int i = r & 1; i + 1 < V; i += 2) {
+        if (k[i + 1] < k[i]) {
+          const K t = k[i];
+          k[i] = k[i + 1];
+          k[i + 1] = t;
+          if (HV) {
+            const uint32_t u = v[i];
+            v[i] = v[i + 1];
+            v[i + 1] = u;
+          }
         }
       }
     }
+    if (CNT) cmp += V * (V - 1) / 2;
   }
-  if (CNT) cmp += V * (V - 1) / 2;
   __syncthreads();
+  if (tid < P) {
 #pragma unroll
-  for (int j = 0; j < V; ++j) {
-    s.k[sk_i<K>(tid * V + j)] = k[j];
-    if (HV) s.v[sv_i(tid * V + j)] = v[j];
+    for (int j = 0; j < V; ++j) {
+      s.k[sk_i<K>(tid * V + j)] = k[j];
+      if (HV) s.v[sv_i(tid * V + j)] = v[j];
+    }
   }
   __syncthreads();
-  for (int sp = 1; sp < NT; sp <<= 1) {
+  for (int sp = 1; sp < P; sp <<= 1) {
     const int L = sp * V;
     const int g = tid / (2 * sp), r = tid - g * 2 * sp;
     const int a0 = g * 2 * L, b0 = a0 + L;
     const int d = r * V;
-    const int ia = merge_path_smem<K, CNT>(s.k, a0, L, b0, L, d, cmp);
-    serial_merge<K, CNT>(s.k, a0 + ia, a0 + L, b0 + d - ia, b0 + L, k, src, cmp);
-    if (HV) {
+    if (tid < P) {
+      const int ia = merge_path_smem<K, CNT>(s.k, a0, L, b0, L, d, cmp);
+      serial_merge<K, CNT>(s.k, a0 + ia, a0 + L, b0 + d - ia, b0 + L, k, src, cmp);
+      if (HV) {
 #pragma unroll
-      for (int j = 0; j < V; ++j) v[j] = s.v[sv_i(src[j])];
+        for (int j = 0; j < V; ++j) v[j] = s.v[sv_i(src[j])];
+      }
     }
     __syncthreads();
+    if (tid < P) {
 #pragma unroll
-    for (int j = 0; j < V; ++j) {
-      s.k[sk_i<K>(a0 + d + j)] = k[j];
-      if (HV) s.v[sv_i(a0 + d + j)] = v[j];
+      for (int j = 0; j < V; ++j) {
+        s.k[sk_i<K>(a0 + d + j)] = k[j];
+        if (HV) s.v[sv_i(a0 + d + j)] = v[j];
+      }
     }
     __syncthreads();
   }
+}
+
+// Smallest power of two P with P * V >= cnt (cnt <= TILE).
+__device__ __forceinline__ int threads_for(int cnt) {
+  int P = 1;
+  while (P * V < cnt) P <<= 1;
+  return P;
 }
 
 // Sorts the tile g[0, cnt) (cnt <= TILE).  If buf != nullptr the sorted keys
@@ -284,13 +301,21 @@ __device__ void block_sort_tile(TileSmem<K, HV> s, uint64_t& cmp) {
 // Mergesort leaf "X then swap into the target", Fig. 3 msort); otherwise the
 // tile is sorted in place.
 template <class K, bool HV, bool CNT>
-__device__ void leaf_sort_tile(TileSmem<K, HV> s, K* g, uint32_t* gv, K* buf, uint32_t* bufv,
+__device__ __noinline__ void leaf_sort_tile(TileSmem<K, HV> s, K* g, uint32_t* gv, K* buf, uint32_t* bufv,
                                int cnt, int xf, uint64_t& cmp) {
+  const int P = threads_for(cnt);
   __syncthreads();
-  load_tile_enc<K, HV>(s, g, gv, cnt, xf);
+  if (P == NT) {
+    load_tile_enc<K, HV>(s, g, gv, cnt, xf);
+  } else {
+    for (int i = threadIdx.x; i < P * V; i += NT) {
+      s.k[sk_i<K>(i)] = (i < cnt) ? enc_key(g[i], xf) : key_max<K>();
+      if (HV) s.v[sv_i(i)] = (i < cnt) ? gv[i] : 0xffffffffu;
+    }
+  }
   __syncthreads();
   if (buf != nullptr) copy_elems<K, HV>(g, gv, buf, bufv, cnt);
-  block_sort_tile<K, HV, CNT>(s, cmp);
+  block_sort_tile<K, HV, CNT>(s, cmp, P);
   if (buf != nullptr) {
     store_tile_dec<K, HV>(s, buf, bufv, cnt, xf);
   } else {
@@ -375,7 +400,7 @@ __device__ void merge_split_warp(const K* keys, uint64_t X, uint64_t m, uint64_t
 // One output tile of a swap-merge level (see above).  X, Y: region bases;
 // m: elements per region; L: input run length; tile: output tile index.
 template <class K, bool HV, bool CNT>
-__device__ void merge_tile(TileSmem<K, HV> s, K* keys, uint32_t* vals, uint64_t X, uint64_t Y,
+__device__ __noinline__ void merge_tile(TileSmem<K, HV> s, K* keys, uint32_t* vals, uint64_t X, uint64_t Y,
                            uint64_t m, uint64_t L, uint64_t tile, const uint64_t* splits, int xf,
                            uint64_t& cmp) {
   const MergeGeom gm(m, L, tile);
@@ -448,7 +473,7 @@ __device__ void merge_tile(TileSmem<K, HV> s, K* keys, uint32_t* vals, uint64_t 
 // gathered at the front of the tile; returns their number.
 
 template <class K, bool HV, bool CNT>
-__device__ uint32_t part_local_tile(TileSmem<K, HV> s, K* g, uint32_t* gv, int cnt, K piv, bool le,
+__device__ __noinline__ uint32_t part_local_tile(TileSmem<K, HV> s, K* g, uint32_t* gv, int cnt, K piv, bool le,
                                     int xf, uint64_t& cmp) {
   K x[V];
   uint32_t y[V];

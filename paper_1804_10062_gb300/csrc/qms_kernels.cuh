@@ -22,6 +22,7 @@ struct Desc {
   unsigned long long sel_rank;
   unsigned long long sel_eq;
   unsigned long long pos;
+  unsigned long long bytes;       // algorithmic bytes reported by the batched form
   unsigned int tie;  // pivot sample saw a tie: run the second (<=) pass
   unsigned int err;  // nonzero: an internal consistency check failed
   unsigned int hist[256];

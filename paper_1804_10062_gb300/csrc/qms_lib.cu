@@ -19,7 +19,7 @@
 #include <vector>
 
 #include "../../include/qms.h"
-#include "qms_kernels.cuh"
+#include "qms_cta.cuh"
 
 namespace qms {
 namespace {
@@ -403,6 +403,133 @@ int dispatch(const Args& a, qms_stats* stats, Fn&& fn) {
 bool valid_dtype(int d) { return d >= QMS_U32 && d <= QMS_F32; }
 
 // ---------------------------------------------------------------------------
+// Batched form: many independent segments of one array.  Segments of at most
+// CTA_MAX_TILES tiles are sorted in one persistent launch (one block per
+// segment, longest first, taken from an atomic ticket); longer segments run
+// through the grid-wide driver one after the other on the same stream.
+
+template <class K, bool HV, bool CNT>
+int run_batched(void* keys, uint32_t* vals, const uint64_t* d_off, size_t nseg, int dtype,
+                int pivot, cudaStream_t st, qms_profile* profile, qms_stats* stats) {
+  const auto t0 = std::chrono::steady_clock::now();
+  std::vector<uint64_t> off(nseg + 1);
+  ck(cudaMemcpyAsync(off.data(), d_off, (nseg + 1) * sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+  ck(cudaStreamSynchronize(st));
+  for (size_t i = 0; i < nseg; ++i)
+    if (off[i + 1] < off[i]) throw Err{QMS_EINVAL};
+  if (HV && off[nseg] >= (1ull << 32)) throw Err{QMS_EINVAL};
+  // Longest first: bucket by floor(log2(length)), buckets in descending order.
+  const uint64_t cta_max = static_cast<uint64_t>(CTA_MAX_TILES) * TILE;
+  std::vector<uint32_t> bucket_cnt(65, 0);
+  std::vector<uint32_t> big;
+  uint64_t big_max = 0;
+  auto lg = [](uint64_t x) { int l = 0; while ((2ull << l) <= x) ++l; return l; };
+  for (size_t i = 0; i < nseg; ++i) {
+    const uint64_t len = off[i + 1] - off[i];
+    if (len <= 1) continue;
+    if (len > cta_max) {
+      big.push_back(static_cast<uint32_t>(i));
+      big_max = std::max(big_max, len);
+      continue;
+    }
+    ++bucket_cnt[lg(len)];
+  }
+  std::vector<uint32_t> start(65, 0);
+  uint32_t acc = 0;
+  for (int b = 64; b >= 0; --b) {
+    start[b] = acc;
+    acc += bucket_cnt[b];
+  }
+  const uint32_t nsmall = acc;
+  std::vector<uint32_t> order(nsmall ? nsmall : 1);
+  for (size_t i = 0; i < nseg; ++i) {
+    const uint64_t len = off[i + 1] - off[i];
+    if (len <= 1 || len > cta_max) continue;
+    order[start[lg(len)]++] = static_cast<uint32_t>(i);
+  }
+  // Workspace: descriptor, ticket and order (O(segments) words), plus the
+  // grid driver's workspace for the longest large segment.
+  const size_t hdr = 256 * ((sizeof(Desc) + 255) / 256) + 256;
+  const size_t bbytes = hdr + static_cast<size_t>(nsmall) * 4;
+  unsigned char* bws = nullptr;
+  if (cudaMallocAsync(reinterpret_cast<void**>(&bws), bbytes, st) != cudaSuccess) {
+    (void)cudaGetLastError();
+    throw Err{QMS_ENOMEM};
+  }
+  struct Free {
+    unsigned char* p;
+    cudaStream_t s;
+    ~Free() { cudaFreeAsync(p, s); }
+  } free_bws{bws, st};
+  Desc* desc = reinterpret_cast<Desc*>(bws);
+  unsigned int* ticket = reinterpret_cast<unsigned int*>(bws + 256 * ((sizeof(Desc) + 255) / 256));
+  uint32_t* d_order = reinterpret_cast<uint32_t*>(bws + hdr);
+  ck(cudaMemsetAsync(bws, 0, hdr, st));
+  uint64_t launches = 0;
+  Profiler prof(profile);
+  const int xf = xform_of(dtype);
+  if (nsmall) {
+    ck(cudaMemcpyAsync(d_order, order.data(), static_cast<size_t>(nsmall) * 4, cudaMemcpyHostToDevice, st));
+    static bool attr = false;
+    allow_smem(k_batched<K, HV, CNT>, tile_smem_bytes<K, HV>(), attr);
+    int dev = 0, sms = 0, occ = 0;
+    ck(cudaGetDevice(&dev));
+    ck(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    ck(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batched<K, HV, CNT>, NT,
+                                                     tile_smem_bytes<K, HV>()));
+    const unsigned grid = static_cast<unsigned>(
+        std::max<uint64_t>(1, std::min<uint64_t>(nsmall, static_cast<uint64_t>(sms) * std::max(occ, 1))));
+    prof.begin(st);
+    k_batched<K, HV, CNT><<<grid, NT, tile_smem_bytes<K, HV>(), st>>>(
+        static_cast<K*>(keys), vals, d_off, d_order, nsmall, ticket, pivot, xf, desc);
+    prof.end(st, QMS_K_BATCH, 0);
+    ck(cudaGetLastError());
+    ++launches;
+  }
+  uint64_t rounds = 0, mom_rounds = 0, big_cmp = 0;
+  if (!big.empty()) {
+    Workspace ws;
+    ws.alloc(big_max, st);
+    for (uint32_t i : big) {
+      ck(cudaMemsetAsync(ws.desc, 0, sizeof(Desc), st));
+      Sorter<K, HV, CNT> srt(static_cast<K*>(keys) + off[i], HV ? vals + off[i] : nullptr, xf, st, ws,
+                             prof);
+      srt.sort(off[i + 1] - off[i], pivot);
+      rounds += srt.rounds;
+      mom_rounds += srt.mom_rounds;
+      launches += srt.launches;
+      unsigned long long c = 0;
+      if (CNT) {
+        ck(cudaMemcpyAsync(&c, &ws.desc->cmp, sizeof(c), cudaMemcpyDeviceToHost, st));
+        ck(cudaStreamSynchronize(st));
+      }
+      big_cmp += c;
+    }
+  }
+  struct {
+    unsigned long long cmp, bytes;
+    unsigned err;
+  } h{};
+  ck(cudaMemcpyAsync(&h.cmp, &desc->cmp, sizeof(h.cmp), cudaMemcpyDeviceToHost, st));
+  ck(cudaMemcpyAsync(&h.bytes, &desc->bytes, sizeof(h.bytes), cudaMemcpyDeviceToHost, st));
+  ck(cudaMemcpyAsync(&h.err, &desc->err, sizeof(h.err), cudaMemcpyDeviceToHost, st));
+  ck(cudaStreamSynchronize(st));
+  ck(cudaGetLastError());
+  prof.flush();
+  if (profile) profile->bytes[QMS_K_BATCH] += h.bytes;
+  if (h.err) throw Err{QMS_EINTERNAL};
+  if (stats) {
+    stats->comparisons = h.cmp + big_cmp;
+    stats->aux_bytes = bbytes + (big.empty() ? 0 : Workspace::size_for(big_max));
+    stats->rounds = rounds;
+    stats->mom_rounds = mom_rounds;
+    stats->launches = launches;
+    stats->ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  }
+  return QMS_OK;
+}
+
+// ---------------------------------------------------------------------------
 // Allocation-free variant of qms_sort (qms_sort_noalloc).
 //
 // Some callers cannot allocate device memory: an application that gives all
@@ -592,6 +719,35 @@ int qms_sort_noalloc(void* d_keys, size_t n, int dtype, const qms_options* opt, 
     }
     return cnt ? run_noalloc<uint32_t, true>(d_keys, n, dtype, pivot, st, base, stats)
                : run_noalloc<uint32_t, false>(d_keys, n, dtype, pivot, st, base, stats);
+  } catch (const Err& e) {
+    return e.code;
+  } catch (...) {
+    return QMS_EINTERNAL;
+  }
+}
+
+int qms_sort_batched(void* d_keys, uint32_t* d_vals, const uint64_t* d_offsets, size_t nseg,
+                     int dtype, const qms_options* opt, void* stream, qms_stats* stats) {
+  if (stats) std::memset(stats, 0, sizeof(*stats));
+  if (!valid_dtype(dtype)) return QMS_EINVAL;
+  const int pivot = opt ? opt->pivot : QMS_PIVOT_M3;
+  if (pivot < QMS_PIVOT_M3 || pivot > QMS_PIVOT_HYBRID) return QMS_EINVAL;
+  if (nseg == 0) return QMS_OK;
+  if (d_keys == nullptr || d_offsets == nullptr || nseg >= (1ull << 32)) return QMS_EINVAL;
+  const cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const bool cnt = opt && opt->count_cmps;
+  qms_profile* prof = opt ? opt->profile : nullptr;
+  try {
+    const bool u64 = (dtype == QMS_U64 || dtype == QMS_I64);
+    const bool hv = d_vals != nullptr;
+#define QMS_B(K, H, C) run_batched<K, H, C>(d_keys, d_vals, d_offsets, nseg, dtype, pivot, st, prof, stats)
+    if (u64) {
+      if (hv) return cnt ? QMS_B(uint64_t, true, true) : QMS_B(uint64_t, true, false);
+      return cnt ? QMS_B(uint64_t, false, true) : QMS_B(uint64_t, false, false);
+    }
+    if (hv) return cnt ? QMS_B(uint32_t, true, true) : QMS_B(uint32_t, true, false);
+    return cnt ? QMS_B(uint32_t, false, true) : QMS_B(uint32_t, false, false);
+#undef QMS_B
   } catch (const Err& e) {
     return e.code;
   } catch (...) {

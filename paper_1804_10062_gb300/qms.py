@@ -76,6 +76,8 @@ def lib():
                 "qms_sort_pairs": ([vp, vp, sz, i, ctypes.POINTER(qms_options), vp,
                                     ctypes.POINTER(qms_stats)], i),
                 "qms_tile_sort": ([vp, vp, sz, i, vp], i),
+                "qms_sort_batched": ([vp, vp, vp, sz, i, ctypes.POINTER(qms_options), vp,
+                                      ctypes.POINTER(qms_stats)], i),
                 "qms_partition": ([vp, vp, sz, i, i, vp, u64p, u64p], i),
                 "qms_mergesort": ([vp, vp, sz, sz, i, vp], i),
                 "qms_sort_noalloc": ([vp, sz, i, ctypes.POINTER(qms_options), vp,
@@ -163,6 +165,22 @@ def qms_sort_pairs(keys, vals, pivot: str = "m3", count_cmps: bool = False, stre
     rc = lib().qms_sort_pairs(ctypes.c_void_p(keys.data_ptr()), vp, keys.numel(), code,
                               ctypes.byref(opt), _stream(stream), ctypes.byref(st))
     _raise(rc, "qms_sort_pairs")
+    return st.as_dict()
+
+
+def qms_sort_batched(keys, offsets, vals=None, pivot: str = "m3", count_cmps: bool = False,
+                     stream=None, dtype=None, profile: qms_profile | None = None):
+    """Sorts every segment keys[offsets[i]:offsets[i+1]] (offsets: CUDA int64/uint64
+    tensor of nseg + 1 entries); returns stats."""
+    code = _check_keys(keys, dtype)
+    if not offsets.is_cuda or not offsets.is_contiguous() or offsets.element_size() != 8:
+        raise ValueError("offsets must be a contiguous CUDA tensor of 8-byte integers")
+    opt = _options(pivot, count_cmps, profile)
+    st = qms_stats()
+    rc = lib().qms_sort_batched(ctypes.c_void_p(keys.data_ptr()), _check_vals(vals, keys.numel()),
+                                ctypes.c_void_p(offsets.data_ptr()), offsets.numel() - 1, code,
+                                ctypes.byref(opt), _stream(stream), ctypes.byref(st))
+    _raise(rc, "qms_sort_batched")
     return st.as_dict()
 
 
