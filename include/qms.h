@@ -130,6 +130,63 @@ int qms_sort_pairs(void* d_keys, uint32_t* d_vals, size_t n, int dtype, const qm
 int qms_sort_batched(void* d_keys, uint32_t* d_vals, const uint64_t* d_offsets, size_t nseg,
                      int dtype, const qms_options* opt, void* stream, qms_stats* stats);
 
+/* ---- Served form --------------------------------------------------------
+ * A request server with continuous batching (no counterpart in the paper,
+ * which sorts one array; each request is one QuickMergesort).  Requests are
+ * admitted in arrival order against a device-memory budget -- the bytes the
+ * server itself holds for a request: a device slot for its keys, unless the
+ * keys are a device array sorted in place (in == out), plus the sort's
+ * O(n/8192 + 1)-word workspace -- and a maximum number of admitted requests.
+ * Worker threads, each with its own stream, run admitted work concurrently:
+ * a request longer than 64 * 8192 keys runs alone through the grid-wide
+ * rounds; shorter ones waiting at the head of the queue are sorted together
+ * in one persistent launch (one block each, longest first).  Requests never
+ * share memory, so each result equals that request's sort alone. */
+typedef struct qms_server qms_server;
+
+typedef struct {
+  int status;         /* QMS_OK or the error of this request              */
+  int batch_size;     /* requests sorted in the same launch (1 = alone)    */
+  uint64_t n;
+  double queue_ms;    /* submit -> admitted                                */
+  double latency_ms;  /* submit -> result written                          */
+} qms_request_info;
+
+typedef struct {
+  uint64_t completed, keys, batches, batched_requests, pending, in_flight, peak_in_flight;
+  uint64_t used_bytes, peak_used_bytes, budget_bytes;
+} qms_server_stats;
+
+/* Creates a server on the current device.  hbm_budget_bytes: device bytes
+ * the server may hold for admitted requests; max_slots: admitted requests at
+ * once; workers: worker threads/streams (1..64); max_batch: requests per
+ * batched launch.  Errors: QMS_EINVAL, QMS_ENOMEM, QMS_ECUDA. */
+int qms_server_create(size_t hbm_budget_bytes, int max_slots, int workers, int max_batch,
+                      qms_server** out);
+
+/* Queues a request to sort n keys of `dtype` read from `in` and written
+ * sorted to `out`; in/out may be host or device pointers (unified
+ * addressing decides the copy direction) and must stay valid until the
+ * request is done.  in == out on a device array sorts it in place.
+ * Non-blocking.  *ticket identifies the request.  Errors: QMS_EINVAL,
+ * QMS_EBUDGET (the request alone exceeds the budget), QMS_ENOMEM. */
+int qms_server_submit(qms_server* srv, const void* in, void* out, size_t n, int dtype, int pivot,
+                      uint64_t* ticket);
+
+/* Non-blocking: *done = 1 and QMS_OK when the request has finished (info
+ * filled; the ticket is then released), else *done = 0 and QMS_EAGAIN.
+ * QMS_EINVAL for an unknown ticket. */
+int qms_server_poll(qms_server* srv, uint64_t ticket, int* done, qms_request_info* info);
+
+/* Blocks up to timeout_ms for the request; QMS_ETIMEOUT if it has not
+ * finished by then (the ticket stays valid). */
+int qms_server_wait(qms_server* srv, uint64_t ticket, double timeout_ms, qms_request_info* info);
+
+int qms_server_get_stats(qms_server* srv, qms_server_stats* out);
+
+/* Finishes every queued request, stops the workers and frees the server. */
+int qms_server_destroy(qms_server* srv);
+
 /* ---- Step-level entry points (one step of a round each; used by the
  * ---- parity tests of the individual kernels). ------------------------- */
 

@@ -331,4 +331,40 @@ __global__ void __launch_bounds__(NT) k_batched(K* keys, uint32_t* vals, const u
   }
 }
 
+// Served form: the segments are separate arrays (one per request), listed by
+// pointer, length and key transform.
+struct SegDesc {
+  void* keys;
+  unsigned long long n;
+  int xf;
+  int pad;
+};
+
+template <class K, bool CNT>
+__global__ void __launch_bounds__(NT) k_batched_ptrs(const SegDesc* segs, uint32_t nseg,
+                                                     unsigned int* ticket, int pivot, Desc* desc) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ CtaState cs;
+  const auto s = TileSmem<K, false>::carve(smem);
+  uint64_t cmp = 0;
+  if (threadIdx.x == 0) {
+    cs.err = 0;
+    cs.bytes = 0;
+  }
+  while (true) {
+    __syncthreads();
+    if (threadIdx.x == 0) cs.seg = atomicAdd(ticket, 1u);
+    __syncthreads();
+    const uint32_t t = cs.seg;
+    if (t >= nseg || cs.err) break;
+    const SegDesc sd = segs[t];
+    cta_qms<K, false, CNT>(s, cs, static_cast<K*>(sd.keys), nullptr, 0, sd.n, pivot, sd.xf, cmp);
+  }
+  if (CNT) flush_count(cmp, &desc->cmp);
+  if (threadIdx.x == 0) {
+    if (cs.err) atomicOr(&desc->err, cs.err);
+    atomicAdd(&desc->bytes, static_cast<unsigned long long>(cs.bytes));
+  }
+}
+
 }  // namespace qms

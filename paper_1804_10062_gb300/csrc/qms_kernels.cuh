@@ -187,7 +187,7 @@ __global__ void k_sel_hist(const K* keys, uint64_t b, uint64_t t, int xf, int sh
     if (h[i]) atomicAdd(&desc->hist[i], h[i]);
 }
 
-__global__ void k_sel_pick(int shift, Desc* desc) {
+static __global__ void k_sel_pick(int shift, Desc* desc) {
   if (threadIdx.x != 0) return;
   unsigned long long r = desc->sel_rank, acc = 0;
   int bin = 255;
@@ -284,7 +284,7 @@ __device__ __forceinline__ uint64_t block_excl_scan_u64(uint64_t x, uint64_t* sc
 
 // Step 2 (one block): L = sum of counts, then the per-tile misplaced run
 // lengths and their exclusive prefix sums pml / pmr (ntiles + 1 entries).
-__global__ void __launch_bounds__(NT) k_part_scan(const uint32_t* counts, uint32_t ntiles, uint64_t lo,
+static __global__ void __launch_bounds__(NT) k_part_scan(const uint32_t* counts, uint32_t ntiles, uint64_t lo,
                                                   uint64_t hi, uint64_t* pml, uint64_t* pmr,
                                                   Desc* desc) {
   __shared__ uint64_t scr[NWARP + 1];

@@ -57,6 +57,23 @@ class qms_stats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class qms_request_info(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("batch_size", ctypes.c_int), ("n", ctypes.c_uint64),
+                ("queue_ms", ctypes.c_double), ("latency_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class qms_server_stats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_uint64) for k in (
+        "completed", "keys", "batches", "batched_requests", "pending", "in_flight",
+        "peak_in_flight", "used_bytes", "peak_used_bytes", "budget_bytes")]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 def library_path() -> str:
     return _build.LIB
 
@@ -82,6 +99,14 @@ def lib():
                 "qms_mergesort": ([vp, vp, sz, sz, i, vp], i),
                 "qms_sort_noalloc": ([vp, sz, i, ctypes.POINTER(qms_options), vp,
                                       ctypes.POINTER(qms_stats)], i),
+                "qms_server_create": ([sz, i, i, i, ctypes.POINTER(vp)], i),
+                "qms_server_submit": ([vp, vp, vp, sz, i, i, u64p], i),
+                "qms_server_poll": ([vp, ctypes.c_uint64, ctypes.POINTER(i),
+                                     ctypes.POINTER(qms_request_info)], i),
+                "qms_server_wait": ([vp, ctypes.c_uint64, ctypes.c_double,
+                                     ctypes.POINTER(qms_request_info)], i),
+                "qms_server_get_stats": ([vp, ctypes.POINTER(qms_server_stats)], i),
+                "qms_server_destroy": ([vp], i),
             }
             for name, (args, res) in sig.items():
                 f = getattr(L, name)
@@ -226,3 +251,56 @@ def qms_sort_noalloc(keys, pivot: str = "m3", count_cmps: bool = False, stream=N
                                 ctypes.byref(opt), _stream(stream), ctypes.byref(st))
     _raise(rc, "qms_sort_noalloc")
     return st.as_dict()
+
+
+class QmsServer:
+    """The qms_server_* calls.  ``submit`` takes raw addresses (host or
+    device) so that callers keep full control of where the data lives."""
+
+    def __init__(self, hbm_budget_bytes: int, max_slots: int = 256, workers: int = 4,
+                 max_batch: int = 4096):
+        self._h = ctypes.c_void_p()
+        rc = lib().qms_server_create(hbm_budget_bytes, max_slots, workers, max_batch,
+                                     ctypes.byref(self._h))
+        _raise(rc, "qms_server_create")
+
+    def qms_server_submit(self, in_ptr: int, out_ptr: int, n: int, dtype: str,
+                          pivot: str = "m3") -> int:
+        t = ctypes.c_uint64(0)
+        rc = lib().qms_server_submit(self._h, ctypes.c_void_p(in_ptr), ctypes.c_void_p(out_ptr), n,
+                                     DTYPE_CODES[dtype], PIVOTS[pivot], ctypes.byref(t))
+        _raise(rc, "qms_server_submit")
+        return t.value
+
+    def qms_server_poll(self, ticket: int):
+        """Returns the request info dict when done, else None."""
+        d = ctypes.c_int(0)
+        info = qms_request_info()
+        rc = lib().qms_server_poll(self._h, ticket, ctypes.byref(d), ctypes.byref(info))
+        if rc == QMS_EAGAIN:
+            return None
+        _raise(rc, "qms_server_poll")
+        return info.as_dict()
+
+    def qms_server_wait(self, ticket: int, timeout_ms: float = 60000.0):
+        info = qms_request_info()
+        rc = lib().qms_server_wait(self._h, ticket, timeout_ms, ctypes.byref(info))
+        _raise(rc, "qms_server_wait")
+        return info.as_dict()
+
+    def qms_server_get_stats(self):
+        st = qms_server_stats()
+        _raise(lib().qms_server_get_stats(self._h, ctypes.byref(st)), "qms_server_get_stats")
+        return st.as_dict()
+
+    def qms_server_destroy(self):
+        if self._h:
+            rc = lib().qms_server_destroy(self._h)
+            self._h = ctypes.c_void_p()
+            _raise(rc, "qms_server_destroy")
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.qms_server_destroy()
