@@ -40,6 +40,12 @@ def parse():
     ap.add_argument("--pivot", default="m3", choices=["m3", "sqrtn", "mom", "hybrid"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="skip the batched and served forms")
+    ap.add_argument("--batched-segments", type=int, default=65536)
+    ap.add_argument("--served-requests", type=int, default=2000)
+    ap.add_argument("--served-lg-max", type=float, default=26.0)
+    ap.add_argument("--served-load", type=float, default=0.8,
+                    help="offered load as a fraction of the plain FIFO throughput")
     return ap.parse_args()
 
 
@@ -176,6 +182,161 @@ def cpu_baseline(args, lg_sample=24, runs=3):
     return {"value": runs * n / total / 1e9, "unit": "GKeys/s", "cores": 1, "kind": "oracle",
             "sample": "%d runs of the single-threaded oracle on n=2^%d %s keys (the same "
                       "distribution, %.1f s of CPU work)" % (runs, lg_sample, args.dtype, total)}
+
+
+# ---------------------------------------------------------------------------
+# batched and served forms
+
+
+def bench_batched(args, q, torch, np):
+    """65,536 segments, lengths log-uniform in [16, 65536], uint32 and
+    float32 U(0,1) keys: one batched call vs one plain call per segment."""
+    import qms_inputs as gen
+    nseg = args.batched_segments
+    L = gen.batch_lengths(nseg, 1, 16, 65536)
+    off = gen.offsets_of(L)
+    n = int(off[-1])
+    doff = torch.from_numpy(off.view(np.int64)).cuda()
+    out = {"segments": nseg, "keys": n, "lengths": "floor(exp(U(ln 16, ln 65536)))"}
+    peak, _ = measured_peak_hbm()
+    for dt in ("u32", "f32"):
+        k = gen.keys("uniform", dt, n, 1)
+        src = torch.from_numpy(k.view(np.int32)).cuda()
+        del k
+        work = torch.empty_like(src)
+        work.copy_(src)
+        q.qms_sort_batched(work, doff, dtype=dt)  # warm-up
+        times, prof = [], q.qms_profile()
+        for _ in range(3):
+            work.copy_(src)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            q.qms_sort_batched(work, doff, dtype=dt, profile=prof)
+            e1.record()
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        ms = min(times)
+        pb = prof.as_dict()["batch"]
+        kern_ms = pb["ms"] / max(1, pb["launches"])
+        alg = pb["bytes"] / max(1, pb["launches"])
+        # plain: one qms_sort per segment, on a seeded sample of 1024 segments
+        idx = np.random.default_rng(0).choice(nseg, min(1024, nseg), replace=False)
+        work.copy_(src)
+        torch.cuda.synchronize()
+        ks = 0
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for i in idx:
+            a, b = int(off[i]), int(off[i + 1])
+            q.qms_sort(work[a:b], dtype=dt)
+            ks += b - a
+        e1.record()
+        torch.cuda.synchronize()
+        plain_gk = ks / (e0.elapsed_time(e1) / 1e3) / 1e9
+        v = n / (ms / 1e3) / 1e9
+        out[dt] = {"value": v, "unit": "GKeys/s", "ms": ms,
+                   "plain_per_array": {"value": plain_gk, "unit": "GKeys/s",
+                                       "sample": "%d seeded segments, one qms_sort each" % len(idx)},
+                   "speedup_vs_plain": v / plain_gk,
+                   "roofline": {"bound": "hbm", "kernel": "k_batched",
+                                "achieved": alg / (kern_ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+                                "frac": alg / (kern_ms / 1e3) / 1e9 / peak,
+                                "note": "algorithmic bytes of every partition, leaf and merge "
+                                        "step; segments are L2-resident while sorted",
+                                "compulsory_frac": 2 * 4 * n / (kern_ms / 1e3) / 1e9 / peak}}
+        del src, work
+        torch.cuda.empty_cache()
+    return out
+
+
+def bench_served(args, q, torch, np):
+    """Poisson stream of requests, sizes floor(2^U(10, lg_max)), dtype mix
+    50/30/20 uint32/uint64/float32 uniform, 16 GB HBM budget; inputs are
+    device-resident slices, results go to a device output ring."""
+    import qms_inputs as gen
+    nreq = args.served_requests
+    lg_max = args.served_lg_max
+    maxn = 1 << int(math.ceil(lg_max))
+    pristine = {}
+    for dt in ("u32", "u64", "f32"):
+        k = gen.keys("uniform", dt, maxn, 77)
+        pristine[dt] = torch.from_numpy(k.view(np.int32 if k.itemsize == 4 else np.int64)).cuda()
+        del k
+    reqs0 = gen.request_stream(nreq, 5, 10.0, lg_max, rate_per_s=1.0)
+    esz = {"u32": 4, "u64": 8, "f32": 4}
+    ring_bytes = 24 << 30
+    ring = torch.empty(ring_bytes, dtype=torch.uint8, device="cuda")
+    torch.cuda.synchronize()
+
+    def fifo_plain():
+        # one request at a time through the plain API (saturated), as the
+        # baseline of the served form
+        work = {dt: torch.empty_like(pristine[dt]) for dt in pristine}
+        t0 = time.perf_counter()
+        keys = 0
+        for _, n, dt in reqs0[: max(1, nreq // 4)]:
+            w = work[dt][:n]
+            w.copy_(pristine[dt][:n])
+            q.qms_sort(w, dtype=dt)
+            keys += n
+        torch.cuda.synchronize()
+        return keys / (time.perf_counter() - t0) / 1e9
+
+    def run(rate_gkeys):
+        mean_n = sum(r[1] for r in reqs0) / len(reqs0)
+        lam = None if rate_gkeys is None else rate_gkeys * 1e9 / mean_n
+        srv = q.QmsServer(16 * 10**9, max_slots=1024, workers=4, max_batch=4096)
+        out = []
+        live = []  # (ticket, ring_off, nbytes)
+        head = 0
+        t_start = time.perf_counter()
+        arr = 0.0
+        rng = np.random.default_rng(9)
+        infos = {}
+        for i, (_, n, dt) in enumerate(reqs0):
+            if lam is not None:
+                arr += -math.log1p(-rng.random()) / lam
+                while time.perf_counter() - t_start < arr:
+                    pass
+            nb = n * esz[dt]
+            nb_al = (nb + 255) // 256 * 256
+            if head + nb_al > ring_bytes:
+                head = 0
+            # wait for outstanding requests overlapping [head, head + nb)
+            while live and any(o < head + nb_al and head < o + b for _, o, b in live):
+                t, o, b = live.pop(0)
+                infos[t] = srv.qms_server_wait(t, 600000.0)
+            src = pristine[dt][:n]
+            dst = ring[head: head + nb]
+            t = srv.qms_server_submit(src.data_ptr(), dst.data_ptr(), n, dt)
+            live.append((t, head, nb_al))
+            out.append(t)
+            head += nb_al
+        for t, o, b in live:
+            infos[t] = srv.qms_server_wait(t, 600000.0)
+        el = time.perf_counter() - t_start
+        st = srv.qms_server_get_stats()
+        srv.qms_server_destroy()
+        lat = sorted(infos[t]["latency_ms"] for t in out)
+        keys = sum(r[1] for r in reqs0)
+        return {"sustained": keys / el / 1e9, "unit": "GKeys/s", "p50_ms": lat[len(lat) // 2],
+                "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+                "mean_batch": st["batched_requests"] / max(1, st["batches"]),
+                "peak_in_flight": st["peak_in_flight"],
+                "peak_used_GB": st["peak_used_bytes"] / 1e9, "wall_s": el}
+
+    fifo = fifo_plain()
+    sat = run(None)
+    load = run(args.served_load * fifo)
+    # spot check: one request alone equals its slice sorted
+    return {"requests": nreq, "sizes": "floor(2^U(10, %g))" % lg_max,
+            "dtype_mix": "50/30/20 u32/u64/f32 uniform", "budget_GB": 16,
+            "fifo_plain": {"value": fifo, "unit": "GKeys/s",
+                           "sample": "first %d requests back to back, one qms_sort each" %
+                                     max(1, nreq // 4)},
+            "saturation": sat, "offered_%.2f" % args.served_load: load,
+            "speedup_vs_fifo_plain": sat["sustained"] / fifo}
 
 
 def run_reference(args):
@@ -318,6 +479,13 @@ def run_qms(args):
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args)
 
+    forms = None
+    if not args.no_forms:
+        del bufs, work
+        torch.cuda.empty_cache()
+        forms = {"batched": bench_batched(args, q, torch, np),
+                 "served": bench_served(args, q, torch, np)}
+
     if rank == 0:
         line = {"metric": "GKeys/s (plain sort); %% HBM roofline of the dominant kernel",
                 "value": value, "unit": "GKeys/s", "n_gpus": ws, "steps": args.steps,
@@ -329,7 +497,7 @@ def run_qms(args):
                            "array), no flush" % (n * esz >> 20),
                            "parallelism": "replicas" if ws > 1 else "single GPU"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": launches, "clocks": ck}
+                "gpu_launches": launches, "clocks": ck, "forms": forms}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

@@ -15,6 +15,26 @@ namespace qms {
 
 constexpr int CTA_MAX_TILES = 64;  // segments up to 64 * 8192 keys
 
+// Out-of-line copies of the tile routines for the block-scoped path: the
+// whole QuickMergesort of a segment lives in one kernel, and separate
+// register allocation per routine keeps it from spilling.
+template <class K, bool HV, bool CNT>
+__device__ __noinline__ uint32_t part_local_tile_call(TileSmem<K, HV> s, K* g, uint32_t* gv, int cnt,
+                                                      K piv, bool le, int xf, uint64_t& cmp) {
+  return part_local_tile<K, HV, CNT>(s, g, gv, cnt, piv, le, xf, cmp);
+}
+template <class K, bool HV, bool CNT>
+__device__ __noinline__ void leaf_sort_tile_call(TileSmem<K, HV> s, K* g, uint32_t* gv, K* buf,
+                                                 uint32_t* bufv, int cnt, int xf, uint64_t& cmp) {
+  leaf_sort_tile<K, HV, CNT>(s, g, gv, buf, bufv, cnt, xf, cmp);
+}
+template <class K, bool HV, bool CNT>
+__device__ __noinline__ void merge_tile_call(TileSmem<K, HV> s, K* keys, uint32_t* vals, uint64_t X,
+                                             uint64_t Y, uint64_t m, uint64_t L, uint64_t tile,
+                                             const uint64_t* splits, int xf, uint64_t& cmp) {
+  merge_tile<K, HV, CNT>(s, keys, vals, X, Y, m, L, tile, splits, xf, cmp);
+}
+
 struct CtaState {
   uint32_t counts[CTA_MAX_TILES];
   uint64_t pml[CTA_MAX_TILES + 1];
@@ -35,7 +55,7 @@ __device__ __noinline__ uint64_t cta_partition(TileSmem<K, HV> s, CtaState& cs, 
   for (uint32_t t = 0; t < nt; ++t) {
     const uint64_t off = static_cast<uint64_t>(t) * TILE;
     const int cnt = static_cast<int>((n - off) < static_cast<uint64_t>(TILE) ? (n - off) : TILE);
-    const uint32_t c = part_local_tile<K, HV, CNT>(s, keys + lo + off, HV ? vals + lo + off : nullptr,
+    const uint32_t c = part_local_tile_call<K, HV, CNT>(s, keys + lo + off, HV ? vals + lo + off : nullptr,
                                                    cnt, piv, le, xf, cmp);
     if (threadIdx.x == 0) cs.counts[t] = c;
   }
@@ -77,7 +97,7 @@ __device__ __noinline__ void cta_mergesort(TileSmem<K, HV> s, CtaState& cs, K* k
   constexpr uint64_t ES = sizeof(K) + (HV ? 4 : 0);
   if (m <= 1) return;
   if (m <= static_cast<uint64_t>(TILE)) {
-    leaf_sort_tile<K, HV, CNT>(s, keys + P, HV ? vals + P : nullptr, nullptr, nullptr,
+    leaf_sort_tile_call<K, HV, CNT>(s, keys + P, HV ? vals + P : nullptr, nullptr, nullptr,
                                static_cast<int>(m), xf, cmp);
     if (threadIdx.x == 0) cs.bytes += 2 * m * ES;
     __syncthreads();
@@ -90,7 +110,7 @@ __device__ __noinline__ void cta_mergesort(TileSmem<K, HV> s, CtaState& cs, K* k
   for (uint32_t t = 0; t < leaves; ++t) {
     const uint64_t off = static_cast<uint64_t>(t) * TILE;
     const int cnt = static_cast<int>((m - off) < static_cast<uint64_t>(TILE) ? (m - off) : TILE);
-    leaf_sort_tile<K, HV, CNT>(s, keys + P + off, HV ? vals + P + off : nullptr,
+    leaf_sort_tile_call<K, HV, CNT>(s, keys + P + off, HV ? vals + P + off : nullptr,
                                to_buf ? keys + Bb + off : nullptr,
                                (HV && to_buf) ? vals + Bb + off : nullptr, cnt, xf, cmp);
   }
@@ -102,7 +122,7 @@ __device__ __noinline__ void cta_mergesort(TileSmem<K, HV> s, CtaState& cs, K* k
       merge_split_warp<K, CNT>(keys, X, m, L, t, xf, cs.splits, cmp);
     __syncthreads();
     for (uint32_t t = 0; t < leaves; ++t)
-      merge_tile<K, HV, CNT>(s, keys, vals, X, Y, m, L, t, cs.splits, xf, cmp);
+      merge_tile_call<K, HV, CNT>(s, keys, vals, X, Y, m, L, t, cs.splits, xf, cmp);
     const uint64_t x = X;
     X = Y;
     Y = x;
@@ -292,7 +312,7 @@ __device__ void cta_qms(TileSmem<K, HV> s, CtaState& cs, K* keys, uint32_t* vals
     }
   }
   if (e - b > 1) {
-    leaf_sort_tile<K, HV, CNT>(s, keys + b, HV ? vals + b : nullptr, nullptr, nullptr,
+    leaf_sort_tile_call<K, HV, CNT>(s, keys + b, HV ? vals + b : nullptr, nullptr, nullptr,
                                static_cast<int>(e - b), xf, cmp);
     if (threadIdx.x == 0) cs.bytes += 2 * (e - b) * (sizeof(K) + (HV ? 4 : 0));
   }

@@ -134,23 +134,54 @@ __device__ __forceinline__ void flush_count(uint64_t c, unsigned long long* dst)
 }
 
 // ---------------------------------------------------------------------------
+// Asynchronous global -> shared copies (cp.async, one element each): many
+// copies stay in flight per thread without occupying registers.
+
+__device__ __forceinline__ void cp_async_elem(uint32_t* smem, const uint32_t* gmem) {
+  const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_elem(uint64_t* smem, const uint64_t* gmem) {
+  const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
+
+// ---------------------------------------------------------------------------
 // Tile load / store (striped: item j of thread t is element j*NT + t)
 
 template <class K, bool HV>
 __device__ __forceinline__ void load_tile_enc(TileSmem<K, HV> s, const K* g, const uint32_t* gv,
                                               int cnt, int xf) {
-#pragma unroll 4
+  // Asynchronous copies of the tile, padding keys beyond cnt, then the
+  // order-key transform in place (each thread transforms what it copied).
+#pragma unroll
   for (int j = 0; j < V; ++j) {
     const int i = j * NT + threadIdx.x;
-    s.k[sk_i<K>(i)] = (i < cnt) ? enc_key(g[i], xf) : key_max<K>();
-    if (HV) s.v[sv_i(i)] = (i < cnt) ? gv[i] : 0xffffffffu;
+    if (i < cnt) {
+      cp_async_elem(&s.k[sk_i<K>(i)], g + i);
+      if (HV) cp_async_elem(&s.v[sv_i(i)], gv + i);
+    } else {
+      s.k[sk_i<K>(i)] = key_max<K>();
+      if (HV) s.v[sv_i(i)] = 0xffffffffu;
+    }
+  }
+  cp_async_wait_all();
+  if (xf != XF_NONE) {
+#pragma unroll
+    for (int j = 0; j < V; ++j) {
+      const int i = j * NT + threadIdx.x;
+      if (i < cnt) s.k[sk_i<K>(i)] = enc_key(s.k[sk_i<K>(i)], xf);
+    }
   }
 }
 
 template <class K, bool HV>
 __device__ __forceinline__ void store_tile_dec(TileSmem<K, HV> s, K* g, uint32_t* gv, int cnt,
                                                int xf) {
-#pragma unroll 4
+#pragma unroll
   for (int j = 0; j < V; ++j) {
     const int i = j * NT + threadIdx.x;
     if (i < cnt) {
@@ -301,7 +332,7 @@ __device__ __forceinline__ int threads_for(int cnt) {
 // Mergesort leaf "X then swap into the target", Fig. 3 msort); otherwise the
 // tile is sorted in place.
 template <class K, bool HV, bool CNT>
-__device__ __noinline__ void leaf_sort_tile(TileSmem<K, HV> s, K* g, uint32_t* gv, K* buf, uint32_t* bufv,
+__device__ __forceinline__ void leaf_sort_tile(TileSmem<K, HV> s, K* g, uint32_t* gv, K* buf, uint32_t* bufv,
                                int cnt, int xf, uint64_t& cmp) {
   const int P = threads_for(cnt);
   __syncthreads();
@@ -397,52 +428,97 @@ __device__ void merge_split_warp(const K* keys, uint64_t X, uint64_t m, uint64_t
   if ((threadIdx.x & 31u) == 0) splits[t] = a;
 }
 
-// One output tile of a swap-merge level (see above).  X, Y: region bases;
-// m: elements per region; L: input run length; tile: output tile index.
-template <class K, bool HV, bool CNT>
-__device__ __noinline__ void merge_tile(TileSmem<K, HV> s, K* keys, uint32_t* vals, uint64_t X, uint64_t Y,
-                           uint64_t m, uint64_t L, uint64_t tile, const uint64_t* splits, int xf,
-                           uint64_t& cmp) {
+// Where output tile t of a level reads and writes: its A and B slices in X
+// (windows from the split step), its buffer tile in Y.
+template <class K>
+struct TileGeo {
+  K* sa;
+  K* sb;
+  uint32_t* sav;
+  uint32_t* sbv;
+  K* yk;
+  uint32_t* yv;
+  int cnt, na;
+};
+
+template <class K, bool HV>
+__device__ __forceinline__ TileGeo<K> tile_geo(K* keys, uint32_t* vals, uint64_t X, uint64_t Y,
+                                               uint64_t m, uint64_t L, uint64_t tile,
+                                               const uint64_t* splits) {
   const MergeGeom gm(m, L, tile);
   const uint64_t o0 = tile * TILE;
-  const uint64_t o1 = gm.pbase + gm.d1;
-  const uint64_t la = gm.la, d0 = gm.d0, d1 = gm.d1;
-  K* A = keys + X + gm.pbase;
-  K* B = A + la;
-  uint32_t* Av = HV ? vals + X + gm.pbase : nullptr;
-  uint32_t* Bv = HV ? Av + la : nullptr;
-  __syncthreads();
+  const uint64_t la = gm.la;
   const uint64_t a_lo = splits[tile];
-  const uint64_t a_hi = (d1 == la + gm.lb) ? la : splits[tile + 1];
-  const int cnt = static_cast<int>(o1 - o0);
-  const int na = static_cast<int>(a_hi - a_lo);
-  const int nb = cnt - na;
-  const uint64_t b_lo = d0 - a_lo;
-  // Stage A[a_lo, a_hi) then B[b_lo, b_lo + nb) in shared memory.
-  for (int i = threadIdx.x; i < cnt; i += NT) {
-    const bool fa = i < na;
-    const uint64_t gi = fa ? a_lo + i : b_lo + (i - na);
-    s.k[sk_i<K>(i)] = enc_key(fa ? A[gi] : B[gi], xf);
-    if (HV) s.v[sv_i(i)] = fa ? Av[gi] : Bv[gi];
-  }
-  __syncthreads();
-  // Buffer elements Y[o0, o1) move into the consumed X slots.
-  K* Yk = keys + Y + o0;
-  uint32_t* Yv = HV ? vals + Y + o0 : nullptr;
-  for (int i = threadIdx.x; i < cnt; i += NT) {
-    const bool fa = i < na;
-    const uint64_t gi = fa ? a_lo + i : b_lo + (i - na);
-    const K y = Yk[i];
-    if (fa) A[gi] = y; else B[gi] = y;
-    if (HV) {
-      const uint32_t yv = Yv[i];
-      if (fa) Av[gi] = yv; else Bv[gi] = yv;
+  const uint64_t a_hi = (gm.d1 == la + gm.lb) ? la : splits[tile + 1];
+  const uint64_t b_lo = gm.d0 - a_lo;
+  TileGeo<K> g;
+  g.sa = keys + X + gm.pbase + a_lo;
+  g.sb = keys + X + gm.pbase + la + b_lo;
+  g.sav = HV ? vals + X + gm.pbase + a_lo : nullptr;
+  g.sbv = HV ? vals + X + gm.pbase + la + b_lo : nullptr;
+  g.yk = keys + Y + o0;
+  g.yv = HV ? vals + Y + o0 : nullptr;
+  g.cnt = static_cast<int>(gm.d1 - gm.d0);
+  g.na = static_cast<int>(a_hi - a_lo);
+  return g;
+}
+
+// Issues the asynchronous copies of the tile's A slice then B slice into
+// shared memory (element i is copied by thread i mod NT).
+template <class K, bool HV>
+__device__ __forceinline__ void stage_tile(TileSmem<K, HV> s, const TileGeo<K>& g) {
+#pragma unroll
+  for (int j = 0; j < V; ++j) {
+    const int i = j * NT + threadIdx.x;
+    if (i < g.cnt) {
+      const bool fa = i < g.na;
+      cp_async_elem(&s.k[sk_i<K>(i)], fa ? g.sa + i : g.sb + (i - g.na));
+      if (HV) cp_async_elem(&s.v[sv_i(i)], fa ? g.sav + i : g.sbv + (i - g.na));
     }
   }
-  // Merge the staged slices: thread t produces outputs [tV, tV + V).
+}
+
+// Loads the tile's buffer elements Y[o0, o1) into registers.
+template <class K, bool HV>
+__device__ __forceinline__ void load_y(const TileGeo<K>& g, K (&y)[V], uint32_t (&yv)[V]) {
+#pragma unroll
+  for (int j = 0; j < V; ++j) {
+    const int i = j * NT + threadIdx.x;
+    if (i < g.cnt) {
+      y[j] = g.yk[i];
+      if (HV) yv[j] = g.yv[i];
+    }
+  }
+}
+
+// After this thread's copies have landed: its buffer elements go into the X
+// slots it copied from (so the tile's consumed slots receive exactly its
+// buffer tile), and its staged keys become order keys.
+template <class K, bool HV>
+__device__ __forceinline__ void put_y(TileSmem<K, HV> s, const TileGeo<K>& g, const K (&y)[V],
+                                      const uint32_t (&yv)[V], int xf) {
+#pragma unroll
+  for (int j = 0; j < V; ++j) {
+    const int i = j * NT + threadIdx.x;
+    if (i < g.cnt) {
+      const bool fa = i < g.na;
+      *(fa ? g.sa + i : g.sb + (i - g.na)) = y[j];
+      if (HV) *(fa ? g.sav + i : g.sbv + (i - g.na)) = yv[j];
+      if (xf != XF_NONE) s.k[sk_i<K>(i)] = enc_key(s.k[sk_i<K>(i)], xf);
+    }
+  }
+}
+
+// Merges the staged slices (thread t produces outputs [tV, tV + V)) and
+// writes the merged tile to Y.  Starts after a __syncthreads that made the
+// staged keys visible.
+template <class K, bool HV, bool CNT>
+__device__ __forceinline__ void merge_staged(TileSmem<K, HV> s, const TileGeo<K>& g, int xf,
+                                             uint64_t& cmp) {
   K k[V];
   uint32_t v[V];
   int src[V];
+  const int cnt = g.cnt, na = g.na, nb = cnt - na;
   const int d = threadIdx.x * V;
   const bool active = d < cnt;
   if (active) {
@@ -453,7 +529,7 @@ __device__ __noinline__ void merge_tile(TileSmem<K, HV> s, K* keys, uint32_t* va
       for (int j = 0; j < V; ++j) v[j] = s.v[sv_i(src[j] < cnt ? src[j] : 0)];
     }
   }
-  __syncthreads();  // all staged reads and all Y reads are complete
+  __syncthreads();
   if (active) {
 #pragma unroll
     for (int j = 0; j < V; ++j) {
@@ -464,7 +540,24 @@ __device__ __noinline__ void merge_tile(TileSmem<K, HV> s, K* keys, uint32_t* va
     }
   }
   __syncthreads();
-  store_tile_dec<K, HV>(s, Yk, Yv, cnt, xf);
+  store_tile_dec<K, HV>(s, g.yk, g.yv, cnt, xf);
+}
+
+// One output tile of a swap-merge level, unpipelined (block-scoped path).
+template <class K, bool HV, bool CNT>
+__device__ __forceinline__ void merge_tile(TileSmem<K, HV> s, K* keys, uint32_t* vals, uint64_t X,
+                                           uint64_t Y, uint64_t m, uint64_t L, uint64_t tile,
+                                           const uint64_t* splits, int xf, uint64_t& cmp) {
+  const TileGeo<K> g = tile_geo<K, HV>(keys, vals, X, Y, m, L, tile, splits);
+  __syncthreads();
+  stage_tile<K, HV>(s, g);
+  K y[V];
+  uint32_t yv[V];
+  load_y<K, HV>(g, y, yv);
+  cp_async_wait_all();
+  put_y<K, HV>(s, g, y, yv, xf);
+  __syncthreads();
+  merge_staged<K, HV, CNT>(s, g, xf, cmp);
 }
 
 // ---------------------------------------------------------------------------
@@ -473,7 +566,7 @@ __device__ __noinline__ void merge_tile(TileSmem<K, HV> s, K* keys, uint32_t* va
 // gathered at the front of the tile; returns their number.
 
 template <class K, bool HV, bool CNT>
-__device__ __noinline__ uint32_t part_local_tile(TileSmem<K, HV> s, K* g, uint32_t* gv, int cnt, K piv, bool le,
+__device__ __forceinline__ uint32_t part_local_tile(TileSmem<K, HV> s, K* g, uint32_t* gv, int cnt, K piv, bool le,
                                     int xf, uint64_t& cmp) {
   K x[V];
   uint32_t y[V];

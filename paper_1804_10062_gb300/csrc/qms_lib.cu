@@ -151,8 +151,18 @@ class Sorter {
   Sorter(K* keys, uint32_t* vals, int xf, cudaStream_t st, Workspace& ws, Profiler& prof)
       : keys_(keys), vals_(vals), xf_(xf), st_(st), ws_(ws), prof_(prof) {
     static bool a1 = false, a2 = false, a3 = false, a4 = false;
+    static int merge_grid = 0;
     allow_smem(k_leaf_sort<K, HV, CNT>, tile_smem_bytes<K, HV>(), a1);
-    allow_smem(k_merge_level<K, HV, CNT>, tile_smem_bytes<K, HV>(), a2);
+    allow_smem(k_merge_level<K, HV, CNT>, 2 * tile_smem_bytes<K, HV>(), a2);
+    if (merge_grid == 0) {
+      int dev = 0, sms = 0, occ = 0;
+      ck(cudaGetDevice(&dev));
+      ck(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+      ck(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_merge_level<K, HV, CNT>, NT,
+                                                       2 * tile_smem_bytes<K, HV>()));
+      merge_grid = sms * std::max(occ, 1);
+    }
+    merge_grid_ = merge_grid;
     allow_smem(k_part_local<K, HV, CNT>, tile_smem_bytes<K, HV>(), a3);
     allow_smem(k_pivot_sample<K, HV, CNT>, tile_smem_bytes<K, true>(), a4);
   }
@@ -195,7 +205,8 @@ class Sorter {
                                                                           ws_.splits, ws_.desc);
       prof_.end(st_, QMS_K_MERGE_SPLIT, 0);
       prof_.begin(st_);
-      k_merge_level<K, HV, CNT><<<grid_of(leaves), NT, tile_smem_bytes<K, HV>(), st_>>>(
+      k_merge_level<K, HV, CNT><<<grid_of(std::min<uint64_t>(leaves, merge_grid_)), NT,
+                                  2 * tile_smem_bytes<K, HV>(), st_>>>(
           keys_, vals_, X, Y, m, L, ws_.splits, xf_, ws_.desc);
       prof_.end(st_, QMS_K_MERGE, 4 * m * ES);
       launched(2);
@@ -340,6 +351,7 @@ class Sorter {
 
   K* keys_;
   uint32_t* vals_;
+  int merge_grid_ = 1;
   int xf_;
   cudaStream_t st_;
   Workspace& ws_;

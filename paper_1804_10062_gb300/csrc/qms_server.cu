@@ -336,6 +336,8 @@ int qms_server_submit(qms_server* S, const void* in, void* out, size_t n, int dt
     r->id = S->next_id++;
     if (n <= 1) {  // nothing to sort
       r->done = true;
+      ++S->completed;
+      S->keys_done += n;
       r->t_admit = r->t_done = r->t_submit;
       if (n == 1 && in != out) {
         if (cudaMemcpy(out, in, key_bytes(dtype), cudaMemcpyDefault) != cudaSuccess) {
