@@ -184,6 +184,11 @@ int qms_server_wait(qms_server* srv, uint64_t ticket, double timeout_ms, qms_req
 
 int qms_server_get_stats(qms_server* srv, qms_server_stats* out);
 
+/* Host-side control for failure handling and tests: while paused, workers
+ * take no new request (work already on the GPU finishes); waits on queued
+ * requests then run into their timeouts.  paused = 0 resumes. */
+int qms_server_pause(qms_server* srv, int paused);
+
 /* Finishes every queued request, stops the workers and frees the server. */
 int qms_server_destroy(qms_server* srv);
 

@@ -84,6 +84,7 @@ struct qms_server {
   int in_flight = 0, peak_in_flight = 0;
   uint64_t completed = 0, keys_done = 0, batches = 0, batched_reqs = 0;
   bool stop = false;
+  bool paused = false;
   std::vector<std::thread> workers;
 };
 
@@ -217,7 +218,8 @@ void worker_loop(qms_server* S) {
     {
       std::unique_lock<std::mutex> lk(S->mu);
       S->cv_work.wait(lk, [&] {
-        return (S->stop && S->pending.empty()) || (!S->pending.empty() && fits(S, S->pending.front()));
+        return (S->stop && S->pending.empty()) ||
+               (!S->paused && !S->pending.empty() && fits(S, S->pending.front()));
       });
       if (S->pending.empty()) break;  // stopping and drained
       Req* h = S->pending.front();
@@ -401,11 +403,22 @@ int qms_server_get_stats(qms_server* S, qms_server_stats* out) {
   return QMS_OK;
 }
 
+int qms_server_pause(qms_server* S, int paused) {
+  if (!S) return QMS_EINVAL;
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->paused = paused != 0;
+  }
+  S->cv_work.notify_all();
+  return QMS_OK;
+}
+
 int qms_server_destroy(qms_server* S) {
   if (!S) return QMS_EINVAL;
   {
     std::lock_guard<std::mutex> lk(S->mu);
     S->stop = true;
+    S->paused = false;
   }
   S->cv_work.notify_all();
   for (auto& t : S->workers) t.join();

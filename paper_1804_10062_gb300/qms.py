@@ -107,6 +107,7 @@ def lib():
                                      ctypes.POINTER(qms_request_info)], i),
                 "qms_server_get_stats": ([vp, ctypes.POINTER(qms_server_stats)], i),
                 "qms_server_destroy": ([vp], i),
+                "qms_server_pause": ([vp, i], i),
             }
             for name, (args, res) in sig.items():
                 f = getattr(L, name)
@@ -292,6 +293,9 @@ class QmsServer:
         st = qms_server_stats()
         _raise(lib().qms_server_get_stats(self._h, ctypes.byref(st)), "qms_server_get_stats")
         return st.as_dict()
+
+    def qms_server_pause(self, paused: bool = True):
+        _raise(lib().qms_server_pause(self._h, 1 if paused else 0), "qms_server_pause")
 
     def qms_server_destroy(self):
         if self._h:

@@ -113,3 +113,21 @@ def test_poll_releases_ticket(q):
         assert info is not None and info["status"] == 0
         with pytest.raises(q.QmsError):
             srv.qms_server_poll(t)
+
+
+def test_bounded_wait_times_out_while_paused(q):
+    # Failure made on the host: the server is paused, so a queued request
+    # cannot finish; the bounded wait returns QMS_ETIMEOUT and the request
+    # completes normally once the server resumes.
+    with q.QmsServer(1 << 28, workers=2) as srv:
+        srv.qms_server_pause(True)
+        k = gen.keys("uniform", "u32", 50000, 5)
+        d = _t(k, "cuda")
+        t = srv.qms_server_submit(d.data_ptr(), d.data_ptr(), len(k), "u32")
+        with pytest.raises(q.QmsError) as e:
+            srv.qms_server_wait(t, 50.0)
+        assert e.value.code == q.QMS_ETIMEOUT
+        assert srv.qms_server_poll(t) is None
+        srv.qms_server_pause(False)
+        assert srv.qms_server_wait(t, 60000.0)["status"] == 0
+        assert d.cpu().numpy().view(np.uint32).tobytes() == np.sort(k).tobytes()
