@@ -225,7 +225,7 @@ int qms_mergesort(void* d_keys, uint32_t* d_vals, size_t m, size_t buf, int dtyp
  * allocator and forbids any other cudaMalloc, or a latency-critical loop in
  * which an allocation could synchronise the device or fail under memory
  * pressure.  The sort's round descriptor and per-tile counters live in one
- * fixed file-scope device array of about 60 KB, which every GPU that loads
+ * fixed file-scope device array of about 170 KB, which every GPU that loads
  * the library holds until the process exits.  The caller passes the keys as
  * with qms_sort (keys only; opt->profile must be NULL).
  *   - n > QMS_NOALLOC_MAX_N (2^24) returns QMS_EINVAL; nothing runs.

@@ -155,26 +155,11 @@ __device__ __forceinline__ void cp_async_wait_all() {
 template <class K, bool HV>
 __device__ __forceinline__ void load_tile_enc(TileSmem<K, HV> s, const K* g, const uint32_t* gv,
                                               int cnt, int xf) {
-  // Asynchronous copies of the tile, padding keys beyond cnt, then the
-  // order-key transform in place (each thread transforms what it copied).
-#pragma unroll
+#pragma unroll 4
   for (int j = 0; j < V; ++j) {
     const int i = j * NT + threadIdx.x;
-    if (i < cnt) {
-      cp_async_elem(&s.k[sk_i<K>(i)], g + i);
-      if (HV) cp_async_elem(&s.v[sv_i(i)], gv + i);
-    } else {
-      s.k[sk_i<K>(i)] = key_max<K>();
-      if (HV) s.v[sv_i(i)] = 0xffffffffu;
-    }
-  }
-  cp_async_wait_all();
-  if (xf != XF_NONE) {
-#pragma unroll
-    for (int j = 0; j < V; ++j) {
-      const int i = j * NT + threadIdx.x;
-      if (i < cnt) s.k[sk_i<K>(i)] = enc_key(s.k[sk_i<K>(i)], xf);
-    }
+    s.k[sk_i<K>(i)] = (i < cnt) ? enc_key(g[i], xf) : key_max<K>();
+    if (HV) s.v[sv_i(i)] = (i < cnt) ? gv[i] : 0xffffffffu;
   }
 }
 
@@ -406,7 +391,7 @@ struct MergeGeom {
   __device__ __forceinline__ MergeGeom(uint64_t m, uint64_t L, uint64_t t) {
     const uint64_t o0 = t * TILE;
     const uint64_t o1 = (o0 + TILE < m) ? o0 + TILE : m;
-    pbase = (o0 / (2 * L)) * (2 * L);
+    pbase = o0 & ~(2 * L - 1);  // run lengths are powers of two
     la = (m - pbase < L) ? m - pbase : L;
     const uint64_t rem = m - pbase - la;
     lb = rem < L ? rem : L;

@@ -20,6 +20,7 @@
 
 #include "../../include/qms.h"
 #include "qms_cta.cuh"
+#include "qms_merge.cuh"
 
 namespace qms {
 namespace {
@@ -62,9 +63,12 @@ struct Workspace {
   uint64_t* splits = nullptr;
   cudaStream_t st = nullptr;
 
+  static constexpr uint64_t kMinMergeTile = 1024;  // smallest MergeCfg<K, HV>::MT
   static size_t size_for(uint64_t n) {
     const uint64_t nt = n / TILE + 2;
-    return ((sizeof(Desc) + 255) / 256) * 256 + ((nt * 4 + 255) / 256) * 256 + 3 * (nt + 1) * 8;
+    const uint64_t ns = n / kMinMergeTile + 3;
+    return ((sizeof(Desc) + 255) / 256) * 256 + ((nt * 4 + 255) / 256) * 256 + 2 * (nt + 1) * 8 +
+           ns * 8;
   }
   void alloc(uint64_t n, cudaStream_t s) {
     st = s;
@@ -151,18 +155,8 @@ class Sorter {
   Sorter(K* keys, uint32_t* vals, int xf, cudaStream_t st, Workspace& ws, Profiler& prof)
       : keys_(keys), vals_(vals), xf_(xf), st_(st), ws_(ws), prof_(prof) {
     static bool a1 = false, a2 = false, a3 = false, a4 = false;
-    static int merge_grid = 0;
     allow_smem(k_leaf_sort<K, HV, CNT>, tile_smem_bytes<K, HV>(), a1);
-    allow_smem(k_merge_level<K, HV, CNT>, 2 * tile_smem_bytes<K, HV>(), a2);
-    if (merge_grid == 0) {
-      int dev = 0, sms = 0, occ = 0;
-      ck(cudaGetDevice(&dev));
-      ck(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-      ck(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_merge_level<K, HV, CNT>, NT,
-                                                       2 * tile_smem_bytes<K, HV>()));
-      merge_grid = sms * std::max(occ, 1);
-    }
-    merge_grid_ = merge_grid;
+    (void)a2;
     allow_smem(k_part_local<K, HV, CNT>, tile_smem_bytes<K, HV>(), a3);
     allow_smem(k_pivot_sample<K, HV, CNT>, tile_smem_bytes<K, true>(), a4);
   }
@@ -198,16 +192,17 @@ class Sorter {
     const bool to_buf = (levels & 1) != 0;
     leaf(P, m, to_buf, Bb);
     uint64_t X = to_buf ? Bb : P, Y = to_buf ? P : Bb;
+    constexpr uint64_t MT = MergeCfg<K, HV>::MT;
+    const uint64_t mtiles = (m + MT - 1) / MT;
     for (int l = 0; l < levels; ++l) {
       const uint64_t L = static_cast<uint64_t>(TILE) << l;
       prof_.begin(st_);
-      k_merge_split<K, CNT><<<grid_of((leaves + 7) / 8), 256, 0, st_>>>(keys_, X, m, L, xf_,
-                                                                          ws_.splits, ws_.desc);
+      k_merge_split2<K, HV, CNT><<<grid_of((mtiles + 7) / 8), 256, 0, st_>>>(keys_, X, m, L, xf_,
+                                                                              ws_.splits, ws_.desc);
       prof_.end(st_, QMS_K_MERGE_SPLIT, 0);
       prof_.begin(st_);
-      k_merge_level<K, HV, CNT><<<grid_of(std::min<uint64_t>(leaves, merge_grid_)), NT,
-                                  2 * tile_smem_bytes<K, HV>(), st_>>>(
-          keys_, vals_, X, Y, m, L, ws_.splits, xf_, ws_.desc);
+      k_merge_level3<K, HV, CNT><<<grid_of(mtiles), MBT, 0, st_>>>(keys_, vals_, X, Y, m, L,
+                                                                    ws_.splits, xf_, ws_.desc);
       prof_.end(st_, QMS_K_MERGE, 4 * m * ES);
       launched(2);
       std::swap(X, Y);
@@ -351,7 +346,6 @@ class Sorter {
 
   K* keys_;
   uint32_t* vals_;
-  int merge_grid_ = 1;
   int xf_;
   cudaStream_t st_;
   Workspace& ws_;
@@ -554,13 +548,14 @@ int run_batched(void* keys, uint32_t* vals, const uint64_t* d_off, size_t nseg, 
 constexpr size_t round256(size_t x) { return (x + 255) / 256 * 256; }
 constexpr uint64_t kNoallocMaxN = QMS_NOALLOC_MAX_N;
 constexpr size_t kNoallocTiles = kNoallocMaxN / TILE + 2;
-constexpr size_t kNoallocBytes =
-    round256(sizeof(Desc)) + round256(kNoallocTiles * 4) + 3 * (kNoallocTiles + 1) * 8;
+constexpr size_t kNoallocSplits = kNoallocMaxN / 1024 + 3;
+constexpr size_t kNoallocBytes = round256(sizeof(Desc)) + round256(kNoallocTiles * 4) +
+                                 2 * (kNoallocTiles + 1) * 8 + kNoallocSplits * 8;
 
 }  // namespace
 }  // namespace qms
 
-// Scratch of qms_sort_noalloc (about 60 KB).  Every GPU that loads this
+// Scratch of qms_sort_noalloc (about 170 KB).  Every GPU that loads this
 // library holds it until the process exits.  All calls share it.
 static __device__ __align__(256) unsigned char qms_noalloc_scratch[qms::kNoallocBytes];
 

@@ -1,0 +1,162 @@
+// Grid-wide swap-merge level (Fig. 3 "merge" of arXiv 1804.10062, in its
+// full-buffer form): runs of length L in region X are merged pairwise into
+// region Y while Y's buffer elements move into exactly the X slots each
+// output tile consumed.
+//
+// Small blocks (128 threads, one output tile of 128 x VM elements each) and
+// many of them per SM: every thread first issues all of its global loads
+// (its share of the tile's A/B slices and of the buffer tile) into
+// registers, so a block has a whole tile in flight and eight blocks per SM
+// keep enough bytes in flight to stream at HBM speed.  The merge runs in
+// shared memory (padded layout, no bank conflicts on the merge-path probes).
+#pragma once
+
+#include "qms_device.cuh"
+
+namespace qms {
+
+constexpr int MBT = 128;  // threads per merge block
+
+template <class K, bool HV>
+struct MergeCfg {
+  static constexpr int VM = sizeof(K) == 4 ? 16 : 8;  // outputs per thread
+  static constexpr int MT = MBT * VM;                 // outputs per tile
+  static constexpr int IN_K = MT + MT / (128 / static_cast<int>(sizeof(K))) + 4;  // padded
+  static constexpr int IN_V = MT + MT / 32 + 4;
+};
+
+template <int MT>
+struct MGeom {
+  uint64_t pbase, la, lb, d0, d1;
+  __device__ __forceinline__ MGeom(uint64_t m, uint64_t L, uint64_t t) {
+    const uint64_t o0 = t * MT;
+    const uint64_t o1 = (o0 + MT < m) ? o0 + MT : m;
+    pbase = o0 & ~(2 * L - 1);  // run lengths are powers of two
+    la = (m - pbase < L) ? m - pbase : L;
+    const uint64_t rem = m - pbase - la;
+    lb = rem < L ? rem : L;
+    d0 = o0 - pbase;
+    d1 = o1 - pbase;
+  }
+};
+
+// One output tile per block.  Element i of the tile (i = j*MBT + thread) is
+// loaded from the A/B slices and from the buffer tile by the same thread,
+// which then stores its buffer value into that X slot: the tile's consumed
+// slots receive exactly its buffer elements.
+template <class K, bool HV, bool CNT>
+__global__ void __launch_bounds__(MBT) k_merge_level3(K* keys, uint32_t* vals, uint64_t X,
+                                                      uint64_t Y, uint64_t m, uint64_t L,
+                                                      const uint64_t* splits, int xf, Desc* desc) {
+  using C = MergeCfg<K, HV>;
+  constexpr int VM = C::VM, MT = C::MT;
+  __shared__ K sin[C::IN_K];
+  __shared__ K sout[C::IN_K];
+  __shared__ uint32_t svin[HV ? C::IN_V : 1];
+  __shared__ uint32_t svout[HV ? C::IN_V : 1];
+  uint64_t cmp = 0;
+  const uint64_t t = blockIdx.x;
+  const MGeom<MT> gm(m, L, t);
+  const uint64_t a_lo = splits[t];
+  const uint64_t a_hi = (gm.d1 == gm.la + gm.lb) ? gm.la : splits[t + 1];
+  const uint64_t b_lo = gm.d0 - a_lo;
+  K* ga = keys + X + gm.pbase + a_lo;
+  K* gb = keys + X + gm.pbase + gm.la + b_lo;
+  K* gy = keys + Y + t * MT;
+  uint32_t* gav = HV ? vals + X + gm.pbase + a_lo : nullptr;
+  uint32_t* gbv = HV ? vals + X + gm.pbase + gm.la + b_lo : nullptr;
+  uint32_t* gyv = HV ? vals + Y + t * MT : nullptr;
+  const int cnt = static_cast<int>(gm.d1 - gm.d0);
+  const int na = static_cast<int>(a_hi - a_lo), nb = cnt - na;
+  K x[VM], y[VM];
+  uint32_t xv[VM], yv[VM];
+#pragma unroll
+  for (int j = 0; j < VM; ++j) {
+    const int i = j * MBT + threadIdx.x;
+    if (i < cnt) {
+      x[j] = (i < na) ? ga[i] : gb[i - na];
+      y[j] = gy[i];
+      if (HV) {
+        xv[j] = (i < na) ? gav[i] : gbv[i - na];
+        yv[j] = gyv[i];
+      }
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < VM; ++j) {
+    const int i = j * MBT + threadIdx.x;
+    if (i < cnt) {
+      sin[sk_i<K>(i)] = enc_key(x[j], xf);
+      *((i < na) ? ga + i : gb + (i - na)) = y[j];
+      if (HV) {
+        svin[sv_i(i)] = xv[j];
+        *((i < na) ? gav + i : gbv + (i - na)) = yv[j];
+      }
+    }
+  }
+  __syncthreads();
+  // Staged layout: A at logical [0, na), B at [na, cnt).  Thread produces
+  // outputs [d, d + VM).
+  const int d = threadIdx.x * VM;
+  if (d < cnt) {
+    int lo = d > nb ? d - nb : 0, hi = d < na ? d : na;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (CNT) ++cmp;
+      if (!(sin[sk_i<K>(na + d - 1 - mid)] < sin[sk_i<K>(mid)])) lo = mid + 1; else hi = mid;
+    }
+    int ai = lo, bi = na + d - lo;
+    K ka = ai < na ? sin[sk_i<K>(ai)] : key_max<K>();
+    K kb = bi < cnt ? sin[sk_i<K>(bi)] : key_max<K>();
+#pragma unroll
+    for (int j = 0; j < VM; ++j) {
+      const bool a_ok = ai < na, b_ok = bi < cnt;
+      if (CNT && a_ok && b_ok) ++cmp;
+      const bool tb = b_ok && (!a_ok || kb < ka);
+      if (d + j < cnt) {
+        sout[sk_i<K>(d + j)] = tb ? kb : ka;
+        if (HV) svout[sv_i(d + j)] = svin[sv_i(tb ? bi : ai)];
+      }
+      if (tb) {
+        ++bi;
+        if (bi < cnt) kb = sin[sk_i<K>(bi)];
+      } else {
+        ++ai;
+        if (ai < na) ka = sin[sk_i<K>(ai)];
+      }
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < VM; ++j) {
+    const int i = j * MBT + threadIdx.x;
+    if (i < cnt) {
+      gy[i] = dec_key(sout[sk_i<K>(i)], xf);
+      if (HV) gyv[i] = svout[sv_i(i)];
+    }
+  }
+  if (CNT) flush_count(cmp, &desc->cmp);
+}
+
+// Split step for tiles of MT outputs: for every tile, the number of A
+// elements of its run pair preceding its first output.  One warp per tile;
+// runs before any tile of the level moves a buffer element.
+template <class K, bool HV, bool CNT>
+__global__ void __launch_bounds__(256) k_merge_split2(const K* keys, uint64_t X, uint64_t m,
+                                                      uint64_t L, int xf, uint64_t* splits,
+                                                      Desc* desc) {
+  using C = MergeCfg<K, HV>;
+  uint64_t cmp = 0;
+  const uint64_t ntiles = (m + C::MT - 1) / C::MT;
+  const uint64_t w0 = (blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x) >> 5;
+  const uint64_t nw = (static_cast<uint64_t>(gridDim.x) * blockDim.x) >> 5;
+  for (uint64_t t = w0; t < ntiles; t += nw) {
+    const MGeom<C::MT> g(m, L, t);
+    const K* A = keys + X + g.pbase;
+    const uint64_t a = (g.d0 == 0) ? 0 : merge_path_warp<K, CNT>(A, g.la, A + g.la, g.lb, g.d0, xf, cmp);
+    if ((threadIdx.x & 31u) == 0) splits[t] = a;
+  }
+  if (CNT) flush_count(cmp, &desc->cmp);
+}
+
+}  // namespace qms
