@@ -197,8 +197,8 @@ class Sorter {
     for (int l = 0; l < levels; ++l) {
       const uint64_t L = static_cast<uint64_t>(TILE) << l;
       prof_.begin(st_);
-      k_merge_split2<K, HV, CNT><<<grid_of((mtiles + 7) / 8), 256, 0, st_>>>(keys_, X, m, L, xf_,
-                                                                              ws_.splits, ws_.desc);
+      k_merge_split3<K, HV, CNT><<<grid_of((mtiles + 255) / 256), 256, 0, st_>>>(
+          keys_, X, m, L, xf_, ws_.splits, ws_.desc);
       prof_.end(st_, QMS_K_MERGE_SPLIT, 0);
       prof_.begin(st_);
       k_merge_level3<K, HV, CNT><<<grid_of(mtiles), MBT, 0, st_>>>(keys_, vals_, X, Y, m, L,
