@@ -81,13 +81,21 @@ typedef struct {
   uint64_t launches[QMS_NKINDS];
 } qms_profile;
 
+/* qms_options.flags */
+#define QMS_FLAG_ASYNC 1       /* qms_sort / qms_sort_pairs without stats: return once
+                                  the sort is enqueued on the stream (no host wait)  */
+#define QMS_FLAG_HOST_DRIVEN 2 /* run the rounds from the host (one launch per step,
+                                  one device-to-host read per round) instead of the
+                                  device-driven CUDA graph; implied by `profile`     */
+
 typedef struct {
   int pivot;       /* QMS_PIVOT_*                                              */
   int count_cmps;  /* nonzero: use the counting kernels and report
                       qms_stats.comparisons (element comparisons, Sec. 5)      */
-  int reserved0;
+  int flags;       /* QMS_FLAG_*                                               */
   int reserved1;
-  qms_profile* profile; /* NULL, or accumulates per-kernel device times      */
+  qms_profile* profile; /* NULL, or accumulates per-kernel device times (host-
+                           driven rounds, CUDA events around every launch)    */
 } qms_options;
 
 typedef struct {
@@ -107,8 +115,12 @@ const char* qms_error_string(int code);
 /* Sorts d_keys[0, n) in place, ascending (the QuickMergesort driver loop of
  * Fig. 3: partition, Mergesort the side left of the midpoint test, continue
  * on the other side; ranges of at most 8192 keys are finished by the base
- * case).  Errors: QMS_EINVAL (d_keys NULL with n > 1, bad dtype or pivot),
- * QMS_ENOMEM, QMS_ECUDA, QMS_EINTERNAL. */
+ * case).  By default the whole round loop runs on the device as one CUDA
+ * graph with conditional nodes (instances are cached per key type, pivot
+ * rule and device; the first call of a kind builds one) and the call returns
+ * after the sort finished; with QMS_FLAG_ASYNC and stats == NULL it returns
+ * once the sort is enqueued on `stream`.  Errors: QMS_EINVAL (d_keys NULL
+ * with n > 1, bad dtype or pivot), QMS_ENOMEM, QMS_ECUDA, QMS_EINTERNAL. */
 int qms_sort(void* d_keys, size_t n, int dtype, const qms_options* opt, void* stream,
              qms_stats* stats);
 

@@ -1,0 +1,492 @@
+// Device-driven QuickMergesort: the whole round loop of Fig. 3 (arXiv
+// 1804.10062, "sort") runs inside one CUDA graph with conditional nodes, so
+// the host never waits between rounds.
+//
+//   WHILE (range longer than one tile):
+//     begin   - pivot rule of the round; median-of-3 done here
+//     [sample / median-of-medians pivot kernels, present for those rules]
+//     partition pass 1 (local, scan, exchange) around the pivot
+//     mid     - place the pivot; IF a sample tie: partition pass 2 ("<=")
+//     side    - Fig. 3 side choice, Mergesort part and buffer, level count
+//     leaves  - base case X on the part (in place or swapped into the buffer)
+//     WHILE (levels left): split, swap-merge, level end
+//     end     - continue on the other side
+//   final leaf sort of the last range.
+//
+// All round state lives in DState (device memory); work kernels run a fixed
+// grid and stride over the counts they read from it, control kernels are a
+// single thread and set the conditions with cudaGraphSetConditional.
+#pragma once
+
+#include "qms_kernels.cuh"
+#include "qms_merge.cuh"
+
+namespace qms {
+
+struct DState {
+  // written by the host for every launch
+  void* keys;
+  uint32_t* vals;
+  unsigned long long n;
+  int xf;
+  int pivot;  // QMS_PIVOT_* of the call
+  Desc* desc;
+  uint32_t* counts;
+  unsigned long long* pml;
+  unsigned long long* pmr;
+  unsigned long long* splits;
+  // driver state
+  unsigned long long b, e;          // remaining range
+  unsigned long long lo, hi, parked;  // current partition pass
+  unsigned long long k, eq;         // pivot block of the round
+  unsigned long long P, Bb, m;      // Mergesort part and buffer
+  unsigned long long X, Y, L;       // current merge level
+  unsigned long long rounds, mom_rounds;
+  unsigned long long launches;  // kernels of the graph that ran (all nodes count)
+  unsigned int le, levels, to_buf, mom_next, rule, active, pass2, pad;
+};
+
+constexpr int RULE_M3 = 0, RULE_SQRTN = 1, RULE_MOM = 2, RULE_HYBRID = 3;
+
+__device__ __forceinline__ void count_launch(DState* S) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&S->launches, 1ull);
+}
+
+template <class K, bool HV>
+__device__ __forceinline__ void swap_at(DState& s, uint64_t a, uint64_t b) {
+  if (a == b) return;
+  K* keys = static_cast<K*>(s.keys);
+  const K x = keys[a];
+  keys[a] = keys[b];
+  keys[b] = x;
+  if (HV) {
+    const uint32_t y = s.vals[a];
+    s.vals[a] = s.vals[b];
+    s.vals[b] = y;
+  }
+}
+
+template <class K, bool HV, bool CNT>
+__global__ void k_g_begin(DState* S, cudaGraphConditionalHandle h_round) {
+  count_launch(S);
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  DState& s = *S;
+  if (s.e - s.b <= static_cast<unsigned long long>(TILE)) {
+    s.active = 0;
+    cudaGraphSetConditional(h_round, 0);
+    return;
+  }
+  s.active = 1;
+  ++s.rounds;
+  const uint64_t b = s.b, e = s.e, n = e - b;
+  const int rule = (s.pivot == RULE_MOM || (s.pivot == RULE_HYBRID && s.mom_next))
+                       ? RULE_MOM
+                       : (s.pivot == RULE_SQRTN ? RULE_SQRTN : RULE_M3);
+  s.rule = rule;
+  s.lo = b;
+  s.hi = e - 1;
+  s.parked = e - 1;
+  s.le = 0;
+  Desc* d = s.desc;
+  if (rule == RULE_MOM) {
+    ++s.mom_rounds;
+    d->sel_prefix = 0;
+    d->sel_mask = 0;
+    d->sel_rank = (n / 3) / 2;
+    d->pos = ~0ull;
+  } else if (rule == RULE_M3) {
+    K* keys = static_cast<K*>(s.keys);
+    uint64_t p0 = b, p1 = b + n / 2, p2 = e - 1;
+    K u0 = enc_key(keys[p0], s.xf), u1 = enc_key(keys[p1], s.xf), u2 = enc_key(keys[p2], s.xf);
+    if (u1 < u0) { K t = u0; u0 = u1; u1 = t; uint64_t q = p0; p0 = p1; p1 = q; }
+    unsigned c = 2;
+    if (u2 < u1) {
+      K t = u1; u1 = u2; u2 = t; uint64_t q = p1; p1 = p2; p2 = q;
+      ++c;
+      if (u1 < u0) { t = u0; u0 = u1; u1 = t; q = p0; p0 = p1; p1 = q; }
+    }
+    d->tie = (!(u0 < u1) || !(u1 < u2)) ? 1u : 0u;
+    d->pivot = static_cast<unsigned long long>(u1);
+    if (CNT) d->cmp += c + 2;
+    swap_at<K, HV>(s, p1, e - 1);
+  }
+}
+
+// Median-of-sqrt(n) sample pivot (one block).
+template <class K, bool HV, bool CNT>
+__global__ void __launch_bounds__(NT) k_g_pivot_sample(DState* S) {
+  count_launch(S);
+  DState& s = *S;
+  if (!s.active || s.rule != RULE_SQRTN) return;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const auto sm = TileSmem<K, true>::carve(smem);
+  uint64_t cmp = 0;
+  const uint64_t b = s.b, e = s.e, n = e - b;
+  uint64_t c = 1;
+  while (c * c < n) ++c;
+  uint64_t kk = (c & 1) ? c : c - 1;
+  if (kk > static_cast<uint64_t>(TILE - 1)) kk = TILE - 1;
+  const int ks = static_cast<int>(kk);
+  const uint64_t step = n / kk;
+  K* keys = static_cast<K*>(s.keys);
+  for (int i = threadIdx.x; i < TILE; i += NT) {
+    sm.k[sk_i<K>(i)] = (i < ks) ? enc_key(keys[b + static_cast<uint64_t>(i) * step], s.xf) : key_max<K>();
+    sm.v[sv_i(i)] = static_cast<uint32_t>(i);
+  }
+  block_sort_tile<K, true, CNT>(sm, cmp);
+  if (CNT) flush_count(cmp, &s.desc->cmp);
+  if (threadIdx.x == 0) {
+    const int h = ks / 2;
+    const K med = sm.k[sk_i<K>(h)];
+    const uint64_t pm = b + static_cast<uint64_t>(sm.v[sv_i(h)]) * step;
+    bool tie = false;
+    if (ks >= 3) tie = !(sm.k[sk_i<K>(h - 1)] < med) || !(med < sm.k[sk_i<K>(h + 1)]);
+    swap_at<K, HV>(s, pm, e - 1);
+    s.desc->pivot = static_cast<unsigned long long>(med);
+    s.desc->tie = tie ? 1u : 0u;
+    if (CNT) s.desc->cmp += 2;
+  }
+}
+
+// Median-of-medians pivot (Sec. 4): triple medians, radix select, place.
+template <class K, bool HV, bool CNT>
+__global__ void k_g_mom_triples(DState* S) {
+  count_launch(S);
+  DState& s = *S;
+  if (!s.active || s.rule != RULE_MOM) return;
+  uint64_t cmp = 0;
+  const uint64_t b = s.b, t = (s.e - s.b) / 3;
+  K* keys = static_cast<K*>(s.keys);
+  const int xf = s.xf;
+  for (uint64_t i = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; i < t;
+       i += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
+    const uint64_t q = b + 3 * i;
+    const K x0 = keys[q], x1 = keys[q + 1], x2 = keys[q + 2];
+    const K u0 = enc_key(x0, xf), u1 = enc_key(x1, xf), u2 = enc_key(x2, xf);
+    int mi;
+    if (u1 < u0) {
+      mi = (u2 < u1) ? 1 : ((u2 < u0) ? 2 : 0);
+    } else {
+      mi = (u2 < u1) ? ((u2 < u0) ? 0 : 2) : 1;
+    }
+    if (CNT) cmp += 3;
+    if (mi != 1) {
+      const uint64_t p = q + mi;
+      keys[q + 1] = (mi == 0) ? x0 : x2;
+      keys[p] = x1;
+      if (HV) { const uint32_t a = s.vals[p]; s.vals[p] = s.vals[q + 1]; s.vals[q + 1] = a; }
+    }
+  }
+  if (CNT) flush_count(cmp, &s.desc->cmp);
+}
+
+template <class K>
+__global__ void k_g_sel_hist(DState* S, int shift) {
+  count_launch(S);
+  DState& s = *S;
+  if (!s.active || s.rule != RULE_MOM) return;
+  __shared__ unsigned int h[256];
+  for (int i = threadIdx.x; i < 256; i += blockDim.x) h[i] = 0;
+  __syncthreads();
+  Desc* d = s.desc;
+  const K pre = static_cast<K>(d->sel_prefix), msk = static_cast<K>(d->sel_mask);
+  const uint64_t b = s.b, t = (s.e - s.b) / 3;
+  const K* keys = static_cast<const K*>(s.keys);
+  for (uint64_t i = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; i < t;
+       i += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
+    const K u = enc_key(keys[b + 3 * i + 1], s.xf);
+    if (((u ^ pre) & msk) == 0) atomicAdd(&h[static_cast<unsigned>(u >> shift) & 255u], 1u);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 256; i += blockDim.x)
+    if (h[i]) atomicAdd(&d->hist[i], h[i]);
+}
+
+__global__ static void k_g_sel_pick(DState* S, int shift) {
+  count_launch(S);
+  DState& s = *S;
+  if (threadIdx.x != 0 || !s.active || s.rule != RULE_MOM) return;
+  Desc* d = s.desc;
+  unsigned long long r = d->sel_rank, acc = 0;
+  int bin = 255;
+  for (int i = 0; i < 256; ++i) {
+    const unsigned long long c = d->hist[i];
+    if (r < acc + c) { bin = i; break; }
+    acc += c;
+  }
+  d->sel_eq = d->hist[bin];
+  d->sel_prefix |= static_cast<unsigned long long>(bin) << shift;
+  d->sel_mask |= 255ull << shift;
+  d->sel_rank = r - acc;
+  for (int i = 0; i < 256; ++i) d->hist[i] = 0;
+}
+
+template <class K>
+__global__ void k_g_mom_locate(DState* S) {
+  count_launch(S);
+  DState& s = *S;
+  if (!s.active || s.rule != RULE_MOM) return;
+  const K v = static_cast<K>(s.desc->sel_prefix);
+  const uint64_t b = s.b, t = (s.e - s.b) / 3;
+  const K* keys = static_cast<const K*>(s.keys);
+  for (uint64_t i = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; i < t;
+       i += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
+    if (enc_key(keys[b + 3 * i + 1], s.xf) == v) atomicMin(&s.desc->pos, static_cast<unsigned long long>(i));
+  }
+}
+
+template <class K, bool HV>
+__global__ void k_g_mom_place(DState* S) {
+  count_launch(S);
+  DState& s = *S;
+  if (threadIdx.x != 0 || !s.active || s.rule != RULE_MOM) return;
+  Desc* d = s.desc;
+  const uint64_t t = (s.e - s.b) / 3;
+  if (d->pos >= t) {
+    d->err |= 2u;
+    s.active = 0;
+    return;
+  }
+  swap_at<K, HV>(s, s.b + 3 * d->pos + 1, s.e - 1);
+  d->pivot = d->sel_prefix;
+  d->tie = d->sel_eq > 1 ? 1u : 0u;
+}
+
+// Partition pass over [lo, hi) (mode le), fixed grid striding over tiles.
+template <class K, bool HV, bool CNT>
+__global__ void __launch_bounds__(NT) k_g_part_local(DState* S) {
+  count_launch(S);
+  DState& s = *S;
+  if (!s.active) return;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const auto sm = TileSmem<K, HV>::carve(smem);
+  uint64_t cmp = 0;
+  const K piv = static_cast<K>(s.desc->pivot);
+  const uint64_t lo = s.lo, n = s.hi - s.lo, ntiles = (n + TILE - 1) / TILE;
+  K* keys = static_cast<K*>(s.keys);
+  for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const uint64_t off = t * TILE;
+    const int cnt = static_cast<int>((n - off) < static_cast<uint64_t>(TILE) ? (n - off) : TILE);
+    const uint32_t c = part_local_tile<K, HV, CNT>(sm, keys + lo + off, HV ? s.vals + lo + off : nullptr,
+                                                   cnt, piv, s.le != 0, s.xf, cmp);
+    if (threadIdx.x == 0) s.counts[t] = c;
+  }
+  if (CNT) flush_count(cmp, &s.desc->cmp);
+}
+
+__global__ static void __launch_bounds__(NT) k_g_part_scan(DState* S) {
+  count_launch(S);
+  DState& s = *S;
+  if (!s.active) return;
+  __shared__ uint64_t scr[NWARP + 1];
+  const uint64_t lo = s.lo, hi = s.hi;
+  const uint32_t ntiles = static_cast<uint32_t>((hi - lo + TILE - 1) / TILE);
+  const uint32_t* counts = s.counts;
+  uint64_t sum = 0;
+  for (uint32_t t = threadIdx.x; t < ntiles; t += NT) sum += counts[t];
+  uint64_t L;
+  (void)block_excl_scan_u64(sum, scr, &L);
+  const uint64_t sb = lo + L;
+  const uint32_t chunk = (ntiles + NT - 1) / NT;
+  const uint32_t t0 = threadIdx.x * chunk;
+  const uint32_t t1 = (t0 + chunk < ntiles) ? t0 + chunk : ntiles;
+  uint64_t sl = 0, sr = 0;
+  for (uint32_t t = t0; t < t1; ++t) {
+    const uint64_t ts = lo + static_cast<uint64_t>(t) * TILE;
+    const uint64_t te = (ts + TILE < hi) ? ts + TILE : hi;
+    const uint64_t cs = ts + counts[t];
+    const uint64_t lend = te < sb ? te : sb;
+    const uint64_t rbeg = ts > sb ? ts : sb;
+    sl += lend > cs ? lend - cs : 0;
+    sr += cs > rbeg ? cs - rbeg : 0;
+  }
+  uint64_t totl, totr;
+  uint64_t bl = block_excl_scan_u64(sl, scr, &totl);
+  uint64_t br = block_excl_scan_u64(sr, scr, &totr);
+  for (uint32_t t = t0; t < t1; ++t) {
+    s.pml[t] = bl;
+    s.pmr[t] = br;
+    const uint64_t ts = lo + static_cast<uint64_t>(t) * TILE;
+    const uint64_t te = (ts + TILE < hi) ? ts + TILE : hi;
+    const uint64_t cs = ts + counts[t];
+    const uint64_t lend = te < sb ? te : sb;
+    const uint64_t rbeg = ts > sb ? ts : sb;
+    bl += lend > cs ? lend - cs : 0;
+    br += cs > rbeg ? cs - rbeg : 0;
+  }
+  if (threadIdx.x == 0) {
+    s.pml[ntiles] = totl;
+    s.pmr[ntiles] = totr;
+    s.desc->L = L;
+    s.desc->mis = totl;
+    if (totl != totr) {
+      s.desc->err |= 1u;
+      s.active = 0;
+    }
+  }
+}
+
+template <class K, bool HV>
+__global__ void __launch_bounds__(NT) k_g_part_exchange(DState* S) {
+  count_launch(S);
+  DState& s = *S;
+  if (!s.active) return;
+  const uint64_t mis = s.desc->mis, lo = s.lo;
+  const uint64_t sb = lo + s.desc->L;
+  const uint32_t ntiles = static_cast<uint32_t>((s.hi - lo + TILE - 1) / TILE);
+  for (uint64_t j0 = (blockIdx.x * static_cast<uint64_t>(NT) + threadIdx.x) * EXV; j0 < mis;
+       j0 += static_cast<uint64_t>(gridDim.x) * NT * EXV) {
+    exchange_ranks<K, HV>(static_cast<K*>(s.keys), s.vals, lo, sb, s.counts,
+                          reinterpret_cast<const uint64_t*>(s.pml), reinterpret_cast<const uint64_t*>(s.pmr),
+                          ntiles, j0, mis);
+  }
+}
+
+template <class K, bool HV>
+__global__ void k_g_mid(DState* S, cudaGraphConditionalHandle h_pass2) {
+  count_launch(S);
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  DState& s = *S;
+  s.pass2 = 0;
+  if (s.active) {
+    const uint64_t k = s.lo + s.desc->L;
+    swap_at<K, HV>(s, k, s.parked);
+    s.k = k;
+    if (s.desc->tie && k + 1 < s.e) {
+      s.lo = k + 1;
+      s.hi = s.e;
+      s.le = 1;
+      s.parked = ~0ull;
+      s.pass2 = 1;
+    }
+  }
+  cudaGraphSetConditional(h_pass2, s.pass2);
+}
+
+template <class K, bool HV>
+__global__ void k_g_side(DState* S, cudaGraphConditionalHandle h_level) {
+  count_launch(S);
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  DState& s = *S;
+  s.levels = 0;
+  s.m = 0;
+  if (s.active) {
+    const uint64_t b = s.b, e = s.e, nn = e - b, k = s.k;
+    const uint64_t eq = s.pass2 ? s.desc->L : 0;
+    s.eq = eq;
+    if (s.pivot == RULE_HYBRID) {
+      const uint64_t d = nn / 16, rlo = k - b, rhi = k + eq - b;
+      s.mom_next = (s.rule != RULE_MOM && (rhi < d || rlo > nn - 1 - d)) ? 1u : 0u;
+    }
+    const uint64_t rb = k + 1 + eq;
+    const uint64_t nl = k - b, nr = e - rb;
+    const bool left = (eq == 0) ? (k < b + nn / 2) : (nl <= nr);
+    if (left) {
+      s.P = b;
+      s.m = nl;
+      s.Bb = rb;
+      s.b = rb;
+    } else {
+      s.P = rb;
+      s.m = nr;
+      s.Bb = b;
+      s.e = k;
+    }
+    const uint64_t leaves = (s.m + TILE - 1) / TILE;
+    unsigned levels = 0;
+    while ((1ull << levels) < leaves) ++levels;
+    s.levels = levels;
+    s.to_buf = levels & 1u;
+    s.X = s.to_buf ? s.Bb : s.P;
+    s.Y = s.to_buf ? s.P : s.Bb;
+    s.L = TILE;
+  }
+  cudaGraphSetConditional(h_level, s.levels > 0 ? 1u : 0u);
+}
+
+template <class K, bool HV, bool CNT>
+__global__ void __launch_bounds__(NT) k_g_leaf(DState* S) {
+  count_launch(S);
+  DState& s = *S;
+  if (!s.active || s.m <= 1) return;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const auto sm = TileSmem<K, HV>::carve(smem);
+  uint64_t cmp = 0;
+  const uint64_t m = s.m, P = s.P, Bb = s.Bb;
+  const bool to_buf = s.to_buf != 0;
+  K* keys = static_cast<K*>(s.keys);
+  const uint64_t ntiles = (m + TILE - 1) / TILE;
+  for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const uint64_t off = t * TILE;
+    const int cnt = static_cast<int>((m - off) < static_cast<uint64_t>(TILE) ? (m - off) : TILE);
+    leaf_sort_tile<K, HV, CNT>(sm, keys + P + off, HV ? s.vals + P + off : nullptr,
+                               to_buf ? keys + Bb + off : nullptr,
+                               (HV && to_buf) ? s.vals + Bb + off : nullptr, cnt, s.xf, cmp);
+  }
+  if (CNT) flush_count(cmp, &s.desc->cmp);
+}
+
+template <class K, bool HV, bool CNT>
+__global__ void __launch_bounds__(256) k_g_split(DState* S) {
+  count_launch(S);
+  const DState& s = *S;
+  uint64_t cmp = 0;
+  const uint64_t ngroups = (s.m + MergeCfg<K, HV>::MT * 32ull - 1) / (MergeCfg<K, HV>::MT * 32ull);
+  const uint64_t nw = (static_cast<uint64_t>(gridDim.x) * blockDim.x) >> 5;
+  for (uint64_t w = (blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x) >> 5; w < ngroups;
+       w += nw)
+    split_group<K, HV, CNT>(static_cast<const K*>(s.keys), s.X, s.m, s.L, s.xf,
+                            reinterpret_cast<uint64_t*>(s.splits), w, cmp);
+  if (CNT) flush_count(cmp, &s.desc->cmp);
+}
+
+template <class K, bool HV, bool CNT>
+__global__ void __launch_bounds__(MBT, MergeCfg<K, HV>::MINB) k_g_merge(DState* S) {
+  count_launch(S);
+  const DState& s = *S;
+  using C = MergeCfg<K, HV>;
+  const uint64_t m = s.m, L = s.L, X = s.X, Y = s.Y;
+  const uint64_t ntiles = (m + C::MT - 1) / C::MT;
+  for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    __syncthreads();
+    merge_level_tile<K, HV, CNT>(static_cast<K*>(s.keys), s.vals, X, Y, m, L,
+                                 reinterpret_cast<const uint64_t*>(s.splits), s.xf, s.desc, t);
+  }
+}
+
+__global__ static void k_g_level_end(DState* S, cudaGraphConditionalHandle h_level) {
+  count_launch(S);
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  DState& s = *S;
+  s.L *= 2;
+  const unsigned long long x = s.X;
+  s.X = s.Y;
+  s.Y = x;
+  --s.levels;
+  cudaGraphSetConditional(h_level, s.levels > 0 ? 1u : 0u);
+}
+
+__global__ static void k_g_end(DState* S, cudaGraphConditionalHandle h_round) {
+  count_launch(S);
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  DState& s = *S;
+  const bool more = s.active && s.e - s.b > static_cast<unsigned long long>(TILE) && !s.desc->err;
+  cudaGraphSetConditional(h_round, more ? 1u : 0u);
+}
+
+template <class K, bool HV, bool CNT>
+__global__ void __launch_bounds__(NT) k_g_final(DState* S) {
+  count_launch(S);
+  DState& s = *S;
+  if (s.desc->err || s.e - s.b <= 1) return;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const auto sm = TileSmem<K, HV>::carve(smem);
+  uint64_t cmp = 0;
+  const uint64_t b = s.b;
+  K* keys = static_cast<K*>(s.keys);
+  leaf_sort_tile<K, HV, CNT>(sm, keys + b, HV ? s.vals + b : nullptr, nullptr, nullptr,
+                             static_cast<int>(s.e - b), s.xf, cmp);
+  if (CNT) flush_count(cmp, &s.desc->cmp);
+}
+
+}  // namespace qms

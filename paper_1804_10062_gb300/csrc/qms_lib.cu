@@ -15,12 +15,15 @@
 #include <chrono>
 #include <cstdint>
 #include <cstring>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "../../include/qms.h"
 #include "qms_cta.cuh"
 #include "qms_merge.cuh"
+#include "qms_graph.cuh"
 
 namespace qms {
 namespace {
@@ -352,6 +355,259 @@ class Sorter {
   Profiler& prof_;
 };
 
+// ---------------------------------------------------------------------------
+// Device-driven sort: one instantiated CUDA graph per (key type, payload,
+// counting, pivot rule, device) instance, holding the whole round loop
+// (qms_graph.cuh).  A call writes the keys' address and size into the
+// instance's device state and launches the graph; the host does not wait
+// between rounds.  Graphs with conditional nodes allow one instantiation
+// each, so concurrent calls use separate instances from a pool.
+
+struct GraphInst {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  DState* d_state = nullptr;
+  DState* h_state = nullptr;  // pinned staging copy
+  unsigned char* ws = nullptr;
+  uint64_t cap = 0;
+  size_t ws_bytes = 0;
+  cudaEvent_t done = nullptr;
+  bool busy = false;
+};
+
+inline size_t graph_ws_bytes(uint64_t cap) {
+  const uint64_t nt = cap / TILE + 2;
+  const uint64_t ns = cap / 1024 + 3;  // merge tiles of at least 1024 outputs
+  return ((sizeof(Desc) + 255) / 256) * 256 + ((nt * 4 + 255) / 256) * 256 + 2 * (nt + 1) * 8 +
+         ns * 8;
+}
+
+std::mutex g_graph_mu;
+std::map<std::tuple<int, int, int, int, int>, std::vector<GraphInst*>> g_graphs;
+
+cudaGraphNode_t add_kernel(cudaGraph_t g, cudaGraphNode_t dep, const void* func, unsigned grid,
+                           unsigned block, size_t smem, void** args) {
+  cudaKernelNodeParams p{};
+  p.func = const_cast<void*>(func);
+  p.gridDim = dim3(grid);
+  p.blockDim = dim3(block);
+  p.sharedMemBytes = static_cast<unsigned>(smem);
+  p.kernelParams = args;
+  p.extra = nullptr;
+  cudaGraphNode_t n = nullptr;
+  ck(cudaGraphAddKernelNode(&n, g, dep ? &dep : nullptr, dep ? 1 : 0, &p));
+  return n;
+}
+
+cudaGraphNode_t add_cond(cudaGraph_t g, cudaGraphNode_t dep, cudaGraphConditionalHandle h,
+                         cudaGraphConditionalNodeType type, cudaGraph_t* body) {
+  cudaGraphNodeParams cp{};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = type;
+  cp.conditional.size = 1;
+  cudaGraphNode_t n = nullptr;
+  ck(cudaGraphAddNode(&n, g, dep ? &dep : nullptr, nullptr, dep ? 1 : 0, &cp));
+  *body = cp.conditional.phGraph_out[0];
+  return n;
+}
+
+template <class K, bool HV, bool CNT>
+class GraphRunner {
+ public:
+  // Builds the graph of one instance (kernel arguments: the instance's
+  // device state and the three condition handles).
+  static void build(GraphInst* gi, int pivot) {
+    int dev = 0, sms = 0;
+    ck(cudaGetDevice(&dev));
+    ck(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const size_t tsm = tile_smem_bytes<K, HV>(), tsm_s = tile_smem_bytes<K, true>();
+    static std::once_flag once;
+    std::call_once(once, [&] {
+      cudaFuncSetAttribute(reinterpret_cast<const void*>(k_g_part_local<K, HV, CNT>),
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(tsm));
+      cudaFuncSetAttribute(reinterpret_cast<const void*>(k_g_leaf<K, HV, CNT>),
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(tsm));
+      cudaFuncSetAttribute(reinterpret_cast<const void*>(k_g_final<K, HV, CNT>),
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(tsm));
+      cudaFuncSetAttribute(reinterpret_cast<const void*>(k_g_pivot_sample<K, HV, CNT>),
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(tsm_s));
+    });
+    auto occ = [&](const void* f, int block, size_t smem) {
+      int o = 0;
+      ck(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, f, block, smem));
+      return static_cast<unsigned>(sms * std::max(o, 1));
+    };
+    const unsigned g_part = occ(reinterpret_cast<const void*>(k_g_part_local<K, HV, CNT>), NT, tsm) * 2;
+    const unsigned g_leaf = occ(reinterpret_cast<const void*>(k_g_leaf<K, HV, CNT>), NT, tsm) * 2;
+    const unsigned g_exch = static_cast<unsigned>(sms) * 4;
+    const unsigned g_split = static_cast<unsigned>(sms) * 4;
+    const unsigned g_merge = occ(reinterpret_cast<const void*>(k_g_merge<K, HV, CNT>), MBT, 0) * 2;
+    const unsigned g_mom = static_cast<unsigned>(sms) * 8;
+
+    cudaGraph_t g = nullptr;
+    ck(cudaGraphCreate(&g, 0));
+    cudaGraphConditionalHandle h_round, h_pass2, h_level;
+    ck(cudaGraphConditionalHandleCreate(&h_round, g, 1, cudaGraphCondAssignDefault));
+    ck(cudaGraphConditionalHandleCreate(&h_pass2, g, 0, cudaGraphCondAssignDefault));
+    ck(cudaGraphConditionalHandleCreate(&h_level, g, 0, cudaGraphCondAssignDefault));
+    DState* S = gi->d_state;
+    void* a_s[] = {&S};
+    void* a_round[] = {&S, &h_round};
+    void* a_pass2[] = {&S, &h_pass2};
+    void* a_level[] = {&S, &h_level};
+    cudaGraph_t body = nullptr;
+    cudaGraphNode_t w_round = add_cond(g, nullptr, h_round, cudaGraphCondTypeWhile, &body);
+    cudaGraphNode_t n = add_kernel(body, nullptr, reinterpret_cast<const void*>(k_g_begin<K, HV, CNT>),
+                                   1, 32, 0, a_round);
+    if (pivot == QMS_PIVOT_SQRTN) {
+      n = add_kernel(body, n, reinterpret_cast<const void*>(k_g_pivot_sample<K, HV, CNT>), 1, NT,
+                     tsm_s, a_s);
+    }
+    if (pivot == QMS_PIVOT_MOM || pivot == QMS_PIVOT_HYBRID) {
+      n = add_kernel(body, n, reinterpret_cast<const void*>(k_g_mom_triples<K, HV, CNT>), g_mom, 256,
+                     0, a_s);
+      for (int shift = static_cast<int>(sizeof(K) * 8) - 8; shift >= 0; shift -= 8) {
+        int sh = shift;
+        void* a_sh[] = {&S, &sh};
+        n = add_kernel(body, n, reinterpret_cast<const void*>(k_g_sel_hist<K>), g_mom, 256, 0, a_sh);
+        n = add_kernel(body, n, reinterpret_cast<const void*>(k_g_sel_pick), 1, 32, 0, a_sh);
+      }
+      n = add_kernel(body, n, reinterpret_cast<const void*>(k_g_mom_locate<K>), g_mom, 256, 0, a_s);
+      n = add_kernel(body, n, reinterpret_cast<const void*>(k_g_mom_place<K, HV>), 1, 32, 0, a_s);
+    }
+    auto add_pass = [&](cudaGraph_t gr, cudaGraphNode_t d) {
+      d = add_kernel(gr, d, reinterpret_cast<const void*>(k_g_part_local<K, HV, CNT>), g_part, NT, tsm,
+                     a_s);
+      d = add_kernel(gr, d, reinterpret_cast<const void*>(k_g_part_scan), 1, NT, 0, a_s);
+      d = add_kernel(gr, d, reinterpret_cast<const void*>(k_g_part_exchange<K, HV>), g_exch, NT, 0, a_s);
+      return d;
+    };
+    n = add_pass(body, n);
+    n = add_kernel(body, n, reinterpret_cast<const void*>(k_g_mid<K, HV>), 1, 32, 0, a_pass2);
+    cudaGraph_t p2 = nullptr;
+    n = add_cond(body, n, h_pass2, cudaGraphCondTypeIf, &p2);
+    add_pass(p2, nullptr);
+    n = add_kernel(body, n, reinterpret_cast<const void*>(k_g_side<K, HV>), 1, 32, 0, a_level);
+    n = add_kernel(body, n, reinterpret_cast<const void*>(k_g_leaf<K, HV, CNT>), g_leaf, NT, tsm, a_s);
+    cudaGraph_t lv = nullptr;
+    n = add_cond(body, n, h_level, cudaGraphCondTypeWhile, &lv);
+    {
+      cudaGraphNode_t q = add_kernel(lv, nullptr, reinterpret_cast<const void*>(k_g_split<K, HV, CNT>),
+                                     g_split, 256, 0, a_s);
+      q = add_kernel(lv, q, reinterpret_cast<const void*>(k_g_merge<K, HV, CNT>), g_merge, MBT, 0, a_s);
+      add_kernel(lv, q, reinterpret_cast<const void*>(k_g_level_end), 1, 32, 0, a_level);
+    }
+    add_kernel(body, n, reinterpret_cast<const void*>(k_g_end), 1, 32, 0, a_round);
+    add_kernel(g, w_round, reinterpret_cast<const void*>(k_g_final<K, HV, CNT>), 1, NT, tsm, a_s);
+    ck(cudaGraphInstantiate(&gi->exec, g, 0));
+    gi->graph = g;
+  }
+
+  // Takes a free instance able to hold n keys (creating or growing one).
+  static GraphInst* acquire(uint64_t n, int pivot) {
+    int dev = 0;
+    ck(cudaGetDevice(&dev));
+    const auto key = std::make_tuple(static_cast<int>(sizeof(K)), HV ? 1 : 0, CNT ? 1 : 0, pivot, dev);
+    std::lock_guard<std::mutex> lk(g_graph_mu);
+    auto& pool = g_graphs[key];
+    GraphInst* gi = nullptr;
+    for (GraphInst* c : pool) {
+      if (c->busy) continue;
+      if (cudaEventQuery(c->done) != cudaSuccess) {
+        (void)cudaGetLastError();
+        continue;
+      }
+      gi = c;
+      break;
+    }
+    if (gi == nullptr) {
+      gi = new GraphInst();
+      ck(cudaMalloc(reinterpret_cast<void**>(&gi->d_state), sizeof(DState)));
+      ck(cudaMallocHost(reinterpret_cast<void**>(&gi->h_state), sizeof(DState)));
+      ck(cudaEventCreateWithFlags(&gi->done, cudaEventDisableTiming));
+      build(gi, pivot);
+      pool.push_back(gi);
+    }
+    if (gi->cap < n) {
+      if (gi->ws) ck(cudaFree(gi->ws));
+      gi->ws = nullptr;
+      const uint64_t cap = std::max<uint64_t>(n, 1ull << 20);
+      gi->ws_bytes = graph_ws_bytes(cap);
+      if (cudaMalloc(reinterpret_cast<void**>(&gi->ws), gi->ws_bytes) != cudaSuccess) {
+        (void)cudaGetLastError();
+        gi->cap = 0;
+        throw Err{QMS_ENOMEM};
+      }
+      gi->cap = cap;
+    }
+    gi->busy = true;
+    return gi;
+  }
+
+  static void release(GraphInst* gi) {
+    std::lock_guard<std::mutex> lk(g_graph_mu);
+    gi->busy = false;
+  }
+
+  // Enqueues the sort of keys[0, n) on st; with stats, waits and fills them.
+  static int run(K* keys, uint32_t* vals, uint64_t n, int dtype, int pivot, cudaStream_t st,
+                 qms_stats* stats) {
+    const auto t0 = std::chrono::steady_clock::now();
+    GraphInst* gi = acquire(n, pivot);
+    struct Rel {
+      GraphInst* g;
+      ~Rel() { release(g); }
+    } rel{gi};
+    const uint64_t cap = gi->cap;
+    const uint64_t nt = cap / TILE + 2;
+    unsigned char* w = gi->ws;
+    DState& h = *gi->h_state;
+    std::memset(&h, 0, sizeof(DState));
+    h.keys = keys;
+    h.vals = vals;
+    h.n = n;
+    h.xf = xform_of(dtype);
+    h.pivot = pivot;
+    size_t off = 0;
+    h.desc = reinterpret_cast<Desc*>(w);
+    off += ((sizeof(Desc) + 255) / 256) * 256;
+    h.counts = reinterpret_cast<uint32_t*>(w + off);
+    off += ((nt * 4 + 255) / 256) * 256;
+    h.pml = reinterpret_cast<unsigned long long*>(w + off);
+    off += (nt + 1) * 8;
+    h.pmr = reinterpret_cast<unsigned long long*>(w + off);
+    off += (nt + 1) * 8;
+    h.splits = reinterpret_cast<unsigned long long*>(w + off);
+    h.b = 0;
+    h.e = n;
+    ck(cudaMemcpyAsync(gi->d_state, &h, sizeof(DState), cudaMemcpyHostToDevice, st));
+    ck(cudaMemsetAsync(h.desc, 0, sizeof(Desc), st));
+    ck(cudaGraphLaunch(gi->exec, st));
+    if (stats) {
+      unsigned long long cmp = 0;
+      unsigned err = 0;
+      ck(cudaMemcpyAsync(&cmp, &h.desc->cmp, sizeof(cmp), cudaMemcpyDeviceToHost, st));
+      ck(cudaMemcpyAsync(&err, &h.desc->err, sizeof(err), cudaMemcpyDeviceToHost, st));
+      ck(cudaMemcpyAsync(gi->h_state, gi->d_state, sizeof(DState), cudaMemcpyDeviceToHost, st));
+      ck(cudaEventRecord(gi->done, st));
+      ck(cudaStreamSynchronize(st));
+      ck(cudaGetLastError());
+      if (err) throw Err{QMS_EINTERNAL};
+      stats->comparisons = cmp;
+      stats->aux_bytes = gi->ws_bytes;
+      stats->rounds = gi->h_state->rounds;
+      stats->mom_rounds = gi->h_state->mom_rounds;
+      stats->launches = gi->h_state->launches;
+      stats->ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    } else {
+      ck(cudaEventRecord(gi->done, st));
+      ck(cudaGetLastError());
+    }
+    return QMS_OK;
+  }
+};
+
 struct Args {
   void* keys;
   uint32_t* vals;
@@ -660,7 +916,27 @@ static int sort_common(void* d_keys, uint32_t* d_vals, size_t n, int dtype, cons
   if (d_vals != nullptr && n >= (1ull << 32)) return QMS_EINVAL;
   Args a{d_keys, d_vals, n, dtype, pivot, opt && opt->count_cmps, static_cast<cudaStream_t>(stream),
          opt ? opt->profile : nullptr};
-  return dispatch(a, stats, [&](auto& s) { s.sort(n, pivot); });
+  const bool host_driven = (opt && (opt->profile || (opt->flags & QMS_FLAG_HOST_DRIVEN)));
+  if (host_driven) return dispatch(a, stats, [&](auto& s) { s.sort(n, pivot); });
+  qms_stats local{};
+  qms_stats* st = stats ? stats : ((opt && (opt->flags & QMS_FLAG_ASYNC)) ? nullptr : &local);
+  try {
+    const bool u64 = (dtype == QMS_U64 || dtype == QMS_I64);
+    const bool hv = d_vals != nullptr, cnt = a.count;
+    const cudaStream_t s = a.st;
+#define QMS_G(K, H, C) GraphRunner<K, H, C>::run(static_cast<K*>(d_keys), d_vals, n, dtype, pivot, s, st)
+    if (u64) {
+      if (hv) return cnt ? QMS_G(uint64_t, true, true) : QMS_G(uint64_t, true, false);
+      return cnt ? QMS_G(uint64_t, false, true) : QMS_G(uint64_t, false, false);
+    }
+    if (hv) return cnt ? QMS_G(uint32_t, true, true) : QMS_G(uint32_t, true, false);
+    return cnt ? QMS_G(uint32_t, false, true) : QMS_G(uint32_t, false, false);
+#undef QMS_G
+  } catch (const Err& e) {
+    return e.code;
+  } catch (...) {
+    return QMS_EINTERNAL;
+  }
 }
 
 int qms_sort(void* d_keys, size_t n, int dtype, const qms_options* opt, void* stream,

@@ -23,6 +23,7 @@ struct MergeCfg {
   static constexpr int MT = MBT * VM;                 // outputs per tile
   static constexpr int IN_K = MT + MT / (128 / static_cast<int>(sizeof(K))) + 4;  // padded
   static constexpr int IN_V = MT + MT / 32 + 4;
+  static constexpr int MINB = HV ? 4 : 8;  // resident blocks per SM the kernel is built for
 };
 
 template <int MT>
@@ -45,9 +46,9 @@ struct MGeom {
 // which then stores its buffer value into that X slot: the tile's consumed
 // slots receive exactly its buffer elements.
 template <class K, bool HV, bool CNT>
-__global__ void __launch_bounds__(MBT) k_merge_level3(K* keys, uint32_t* vals, uint64_t X,
-                                                      uint64_t Y, uint64_t m, uint64_t L,
-                                                      const uint64_t* splits, int xf, Desc* desc) {
+__device__ __forceinline__ void merge_level_tile(K* keys, uint32_t* vals, uint64_t X, uint64_t Y,
+                                                 uint64_t m, uint64_t L, const uint64_t* splits,
+                                                 int xf, Desc* desc, uint64_t t) {
   using C = MergeCfg<K, HV>;
   constexpr int VM = C::VM, MT = C::MT;
   __shared__ K sin[C::IN_K];
@@ -55,7 +56,6 @@ __global__ void __launch_bounds__(MBT) k_merge_level3(K* keys, uint32_t* vals, u
   __shared__ uint32_t svin[HV ? C::IN_V : 1];
   __shared__ uint32_t svout[HV ? C::IN_V : 1];
   uint64_t cmp = 0;
-  const uint64_t t = blockIdx.x;
   const MGeom<MT> gm(m, L, t);
   const uint64_t a_lo = splits[t];
   const uint64_t a_hi = (gm.d1 == gm.la + gm.lb) ? gm.la : splits[t + 1];
@@ -138,6 +138,13 @@ __global__ void __launch_bounds__(MBT) k_merge_level3(K* keys, uint32_t* vals, u
   if (CNT) flush_count(cmp, &desc->cmp);
 }
 
+template <class K, bool HV, bool CNT>
+__global__ void __launch_bounds__(MBT, MergeCfg<K, HV>::MINB)
+    k_merge_level3(K* keys, uint32_t* vals, uint64_t X, uint64_t Y, uint64_t m, uint64_t L,
+                   const uint64_t* splits, int xf, Desc* desc) {
+  merge_level_tile<K, HV, CNT>(keys, vals, X, Y, m, L, splits, xf, desc, blockIdx.x);
+}
+
 // Split step for tiles of MT outputs: for every tile, the number of A
 // elements of its run pair preceding its first output.  Runs before any tile
 // of the level moves a buffer element.  A warp serves 32 consecutive tiles:
@@ -147,51 +154,56 @@ __global__ void __launch_bounds__(MBT) k_merge_level3(K* keys, uint32_t* vals, u
 // most the diagonal's advance); otherwise each lane searches its tile's full
 // window.
 template <class K, bool HV, bool CNT>
+__device__ __forceinline__ void split_group(const K* keys, uint64_t X, uint64_t m, uint64_t L,
+                                            int xf, uint64_t* splits, uint64_t w, uint64_t& cmp) {
+  using C = MergeCfg<K, HV>;
+  constexpr int MT = C::MT;
+  const uint64_t ntiles = (m + MT - 1) / MT;
+  const unsigned lane = threadIdx.x & 31u;
+  const uint64_t t0 = w * 32;
+  if (t0 >= ntiles) return;
+  const bool grouped = 2 * L >= 32ull * MT;  // pairs hold whole groups
+  uint64_t a0 = 0, a1 = 0, d0 = 0, d1 = 0;
+  if (grouped) {
+    const MGeom<MT> g0(m, L, t0);
+    const K* A = keys + X + g0.pbase;
+    d0 = g0.d0;
+    a0 = (d0 == 0) ? 0 : merge_path_warp<K, CNT>(A, g0.la, A + g0.la, g0.lb, d0, xf, cmp);
+    const uint64_t te = (t0 + 32 < ntiles) ? t0 + 32 : ntiles;
+    const uint64_t oe = (te * MT < m) ? te * MT : m;
+    d1 = oe - g0.pbase;
+    a1 = (d1 >= g0.la + g0.lb) ? g0.la : merge_path_warp<K, CNT>(A, g0.la, A + g0.la, g0.lb, d1, xf, cmp);
+  }
+  const uint64_t t = t0 + lane;
+  if (t < ntiles) {
+    const MGeom<MT> g(m, L, t);
+    const K* A = keys + X + g.pbase;
+    const K* B = A + g.la;
+    const uint64_t d = g.d0;
+    uint64_t lo = d > g.lb ? d - g.lb : 0, hi = d < g.la ? d : g.la;
+    if (grouped) {
+      const uint64_t lo2 = (a1 > d1 - d) ? a1 - (d1 - d) : 0;
+      const uint64_t hi2 = a0 + (d - d0);
+      const uint64_t l3 = a0 > lo2 ? a0 : lo2, h3 = a1 < hi2 ? a1 : hi2;
+      lo = lo > l3 ? lo : l3;
+      hi = hi < h3 ? hi : h3;
+    }
+    while (lo < hi) {
+      const uint64_t mid = (lo + hi) >> 1;
+      if (CNT) ++cmp;
+      if (!(enc_key(B[d - 1 - mid], xf) < enc_key(A[mid], xf))) lo = mid + 1; else hi = mid;
+    }
+    splits[t] = lo;
+  }
+}
+
+template <class K, bool HV, bool CNT>
 __global__ void __launch_bounds__(256) k_merge_split3(const K* keys, uint64_t X, uint64_t m,
                                                       uint64_t L, int xf, uint64_t* splits,
                                                       Desc* desc) {
-  using C = MergeCfg<K, HV>;
-  constexpr int MT = C::MT;
   uint64_t cmp = 0;
-  const uint64_t ntiles = (m + MT - 1) / MT;
-  const uint64_t w = (blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x) >> 5;
-  const unsigned lane = threadIdx.x & 31u;
-  const uint64_t t0 = w * 32;
-  if (t0 < ntiles) {
-    const bool grouped = 2 * L >= 32ull * MT;  // pairs hold whole groups
-    uint64_t a0 = 0, a1 = 0, d0 = 0, d1 = 0;
-    if (grouped) {
-      const MGeom<MT> g0(m, L, t0);
-      const K* A = keys + X + g0.pbase;
-      d0 = g0.d0;
-      a0 = (d0 == 0) ? 0 : merge_path_warp<K, CNT>(A, g0.la, A + g0.la, g0.lb, d0, xf, cmp);
-      const uint64_t te = (t0 + 32 < ntiles) ? t0 + 32 : ntiles;
-      const uint64_t oe = (te * MT < m) ? te * MT : m;
-      d1 = oe - g0.pbase;
-      a1 = (d1 >= g0.la + g0.lb) ? g0.la : merge_path_warp<K, CNT>(A, g0.la, A + g0.la, g0.lb, d1, xf, cmp);
-    }
-    const uint64_t t = t0 + lane;
-    if (t < ntiles) {
-      const MGeom<MT> g(m, L, t);
-      const K* A = keys + X + g.pbase;
-      const K* B = A + g.la;
-      const uint64_t d = g.d0;
-      uint64_t lo = d > g.lb ? d - g.lb : 0, hi = d < g.la ? d : g.la;
-      if (grouped) {
-        const uint64_t lo2 = (a1 > d1 - d) ? a1 - (d1 - d) : 0;
-        const uint64_t hi2 = a0 + (d - d0);
-        const uint64_t l3 = a0 > lo2 ? a0 : lo2, h3 = a1 < hi2 ? a1 : hi2;
-        lo = lo > l3 ? lo : l3;
-        hi = hi < h3 ? hi : h3;
-      }
-      while (lo < hi) {
-        const uint64_t mid = (lo + hi) >> 1;
-        if (CNT) ++cmp;
-        if (!(enc_key(B[d - 1 - mid], xf) < enc_key(A[mid], xf))) lo = mid + 1; else hi = mid;
-      }
-      splits[t] = lo;
-    }
-  }
+  split_group<K, HV, CNT>(keys, X, m, L, xf, splits,
+                          (blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x) >> 5, cmp);
   if (CNT) flush_count(cmp, &desc->cmp);
 }
 

@@ -44,7 +44,7 @@ class qms_profile(ctypes.Structure):
 
 class qms_options(ctypes.Structure):
     _fields_ = [("pivot", ctypes.c_int), ("count_cmps", ctypes.c_int),
-                ("reserved0", ctypes.c_int), ("reserved1", ctypes.c_int),
+                ("flags", ctypes.c_int), ("reserved1", ctypes.c_int),
                 ("profile", ctypes.POINTER(qms_profile))]
 
 
@@ -160,33 +160,41 @@ def _raise(rc, what):
         raise QmsError(rc, what)
 
 
-def _options(pivot, count_cmps, profile):
-    opt = qms_options(PIVOTS[pivot], 1 if count_cmps else 0, 0, 0, None)
+QMS_FLAG_ASYNC = 1
+QMS_FLAG_HOST_DRIVEN = 2
+
+
+def _options(pivot, count_cmps, profile, flags=0):
+    opt = qms_options(PIVOTS[pivot], 1 if count_cmps else 0, flags, 0, None)
     if profile is not None:
         opt.profile = ctypes.pointer(profile)
     return opt
 
 
 def qms_sort(keys, pivot: str = "m3", count_cmps: bool = False, stream=None, dtype=None,
-             profile: qms_profile | None = None):
-    """Sorts ``keys`` in place; returns the qms_stats fields as a dict.
+             profile: qms_profile | None = None, host_driven: bool = False, wait: bool = True):
+    """Sorts ``keys`` in place; returns the qms_stats fields as a dict (or
+    None with ``wait=False``: the sort is only enqueued on the stream).
 
-    ``profile`` (a qms_profile) accumulates per-kernel device times."""
+    ``profile`` (a qms_profile) accumulates per-kernel device times (this
+    runs the rounds from the host); ``host_driven`` selects that driver
+    without profiling."""
     code = _check_keys(keys, dtype)
-    opt = _options(pivot, count_cmps, profile)
+    flags = (QMS_FLAG_HOST_DRIVEN if host_driven else 0) | (0 if wait else QMS_FLAG_ASYNC)
+    opt = _options(pivot, count_cmps, profile, flags)
     st = qms_stats()
     rc = lib().qms_sort(ctypes.c_void_p(keys.data_ptr()), keys.numel(), code, ctypes.byref(opt),
-                        _stream(stream), ctypes.byref(st))
+                        _stream(stream), ctypes.byref(st) if wait else None)
     _raise(rc, "qms_sort")
-    return st.as_dict()
+    return st.as_dict() if wait else None
 
 
 def qms_sort_pairs(keys, vals, pivot: str = "m3", count_cmps: bool = False, stream=None, dtype=None,
-                   profile: qms_profile | None = None):
+                   profile: qms_profile | None = None, host_driven: bool = False):
     """Sorts ``keys`` in place, moving ``vals`` with them; returns stats."""
     code = _check_keys(keys, dtype)
     vp = _check_vals(vals, keys.numel())
-    opt = _options(pivot, count_cmps, profile)
+    opt = _options(pivot, count_cmps, profile, QMS_FLAG_HOST_DRIVEN if host_driven else 0)
     st = qms_stats()
     rc = lib().qms_sort_pairs(ctypes.c_void_p(keys.data_ptr()), vp, keys.numel(), code,
                               ctypes.byref(opt), _stream(stream), ctypes.byref(st))

@@ -238,3 +238,30 @@ def test_full_size_2_24_sampled(q):
         d = _dev(k)
         q.qms_sort(d, pivot=pivot, dtype=dtype)
         assert _host(d, dtype).tobytes() == oracle.reference_sorted(k).tobytes(), (dtype, pivot)
+
+
+@pytest.mark.parametrize("pivot", ["m3", "sqrtn", "mom", "hybrid"])
+@pytest.mark.parametrize("dtype", ["u32", "i64"])
+def test_host_driven_driver_matches_oracle(q, pivot, dtype):
+    # The rounds can also run from the host (one launch per step; the
+    # profiling path): same kernels, same result.
+    n = (1 << 17) + 999
+    k = _dist_keys("uniform", dtype, n, 44)
+    ref = oracle.reference_sorted(k)
+    d = _dev(k)
+    st = q.qms_sort(d, pivot=pivot, dtype=dtype, host_driven=True)
+    assert _host(d, dtype).tobytes() == ref.tobytes()
+    d2 = _dev(k)
+    st2 = q.qms_sort(d2, pivot=pivot, dtype=dtype)
+    assert _host(d2, dtype).tobytes() == ref.tobytes()
+    assert st2["rounds"] >= 1 and st2["launches"] > 0
+
+
+def test_async_sorts_back_to_back(q):
+    # Several device-driven sorts enqueued without host waits on one stream.
+    arrays = [gen.keys("uniform", "u32", (1 << 19) + i * 1001, 60 + i) for i in range(4)]
+    ds = [_dev(a) for a in arrays]
+    for d in ds:
+        assert q.qms_sort(d, dtype="u32", wait=False) is None
+    for a, d in zip(arrays, ds):
+        assert _host(d, "u32").tobytes() == np.sort(a).tobytes()
