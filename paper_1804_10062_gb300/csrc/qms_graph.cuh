@@ -44,7 +44,25 @@ struct DState {
   unsigned long long rounds, mom_rounds;
   unsigned long long launches;  // kernels of the graph that ran (all nodes count)
   unsigned int le, levels, to_buf, mom_next, rule, active, pass2, pad;
+  // Work nodes whose grid the control kernels size to the round's work
+  // (device-updatable kernel nodes); null when the graph was built with
+  // fixed grids.  cap: the fixed grid the node was built with.
+  cudaGraphDeviceNode_t dn[7];
+  unsigned int cap[7];
+  unsigned int dyn;
 };
+
+enum : int { DN_PART1 = 0, DN_EXCH1 = 1, DN_PART2 = 2, DN_EXCH2 = 3, DN_LEAF = 4, DN_SPLIT = 5,
+             DN_MERGE = 6 };
+
+// Sets a work node's grid to cover `units` blocks (at least 1, at most its
+// built-in grid).
+__device__ __forceinline__ void size_node(DState& s, int i, unsigned long long units) {
+  if (!s.dyn) return;
+  unsigned long long g = units < 1 ? 1 : units;
+  if (g > s.cap[i]) g = s.cap[i];
+  cudaGraphKernelNodeSetGridDim(s.dn[i], dim3(static_cast<unsigned>(g)));
+}
 
 constexpr int RULE_M3 = 0, RULE_SQRTN = 1, RULE_MOM = 2, RULE_HYBRID = 3;
 
@@ -87,6 +105,8 @@ __global__ void k_g_begin(DState* S, cudaGraphConditionalHandle h_round) {
   s.hi = e - 1;
   s.parked = e - 1;
   s.le = 0;
+  s.pass2 = 0;
+  size_node(s, DN_PART1, (n - 1 + TILE - 1) / TILE);
   Desc* d = s.desc;
   if (rule == RULE_MOM) {
     ++s.mom_rounds;
@@ -323,6 +343,8 @@ __global__ static void __launch_bounds__(NT) k_g_part_scan(DState* S) {
       s.desc->err |= 1u;
       s.active = 0;
     }
+    size_node(s, s.pass2 ? DN_EXCH2 : DN_EXCH1,
+              (totl + static_cast<unsigned long long>(NT) * EXV - 1) / (static_cast<unsigned long long>(NT) * EXV));
   }
 }
 
@@ -358,6 +380,7 @@ __global__ void k_g_mid(DState* S, cudaGraphConditionalHandle h_pass2) {
       s.le = 1;
       s.parked = ~0ull;
       s.pass2 = 1;
+      size_node(s, DN_PART2, (s.hi - s.lo + TILE - 1) / TILE);
     }
   }
   cudaGraphSetConditional(h_pass2, s.pass2);
@@ -400,6 +423,11 @@ __global__ void k_g_side(DState* S, cudaGraphConditionalHandle h_level) {
     s.X = s.to_buf ? s.Bb : s.P;
     s.Y = s.to_buf ? s.P : s.Bb;
     s.L = TILE;
+    size_node(s, DN_LEAF, leaves);
+    const unsigned long long mt = MergeCfg<K, HV>::MT;
+    const unsigned long long mtiles = (s.m + mt - 1) / mt;
+    size_node(s, DN_SPLIT, (mtiles + 255) / 256);
+    size_node(s, DN_MERGE, mtiles);
   }
   cudaGraphSetConditional(h_level, s.levels > 0 ? 1u : 0u);
 }

@@ -14,6 +14,8 @@
 #include <algorithm>
 #include <chrono>
 #include <cstdint>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -364,6 +366,9 @@ class Sorter {
 // each, so concurrent calls use separate instances from a pool.
 
 struct GraphInst {
+  cudaGraphDeviceNode_t dn[7] = {};
+  unsigned int gcap[7] = {};  // built-in grid of each work node
+  unsigned int dyn = 0;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   DState* d_state = nullptr;
@@ -386,7 +391,8 @@ std::mutex g_graph_mu;
 std::map<std::tuple<int, int, int, int, int>, std::vector<GraphInst*>> g_graphs;
 
 cudaGraphNode_t add_kernel(cudaGraph_t g, cudaGraphNode_t dep, const void* func, unsigned grid,
-                           unsigned block, size_t smem, void** args) {
+                           unsigned block, size_t smem, void** args,
+                           cudaGraphDeviceNode_t* devnode = nullptr) {
   cudaKernelNodeParams p{};
   p.func = const_cast<void*>(func);
   p.gridDim = dim3(grid);
@@ -396,6 +402,20 @@ cudaGraphNode_t add_kernel(cudaGraph_t g, cudaGraphNode_t dep, const void* func,
   p.extra = nullptr;
   cudaGraphNode_t n = nullptr;
   ck(cudaGraphAddKernelNode(&n, g, dep ? &dep : nullptr, dep ? 1 : 0, &p));
+  if (devnode) {
+    // Device-updatable: the control kernels size its grid to the work.
+    cudaKernelNodeAttrValue v{};
+    v.deviceUpdatableKernelNode.deviceUpdatable = 1;
+    *devnode = nullptr;
+    if (cudaGraphKernelNodeSetAttribute(n, cudaLaunchAttributeDeviceUpdatableKernelNode, &v) ==
+        cudaSuccess) {
+      cudaKernelNodeAttrValue o{};
+      if (cudaGraphKernelNodeGetAttribute(n, cudaLaunchAttributeDeviceUpdatableKernelNode, &o) ==
+          cudaSuccess)
+        *devnode = o.deviceUpdatableKernelNode.devNode;
+    }
+    (void)cudaGetLastError();
+  }
   return n;
 }
 
@@ -418,6 +438,10 @@ class GraphRunner {
   // Builds the graph of one instance (kernel arguments: the instance's
   // device state and the three condition handles).
   static void build(GraphInst* gi, int pivot) {
+    build_impl(gi, pivot, true);
+  }
+
+  static void build_impl(GraphInst* gi, int pivot, bool dyn) {
     int dev = 0, sms = 0;
     ck(cudaGetDevice(&dev));
     ck(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -476,32 +500,64 @@ class GraphRunner {
       n = add_kernel(body, n, reinterpret_cast<const void*>(k_g_mom_locate<K>), g_mom, 256, 0, a_s);
       n = add_kernel(body, n, reinterpret_cast<const void*>(k_g_mom_place<K, HV>), 1, 32, 0, a_s);
     }
-    auto add_pass = [&](cudaGraph_t gr, cudaGraphNode_t d) {
+    cudaGraphDeviceNode_t* dn = dyn ? gi->dn : nullptr;
+    gi->gcap[DN_PART1] = gi->gcap[DN_PART2] = g_part;
+    gi->gcap[DN_EXCH1] = gi->gcap[DN_EXCH2] = g_exch;
+    gi->gcap[DN_LEAF] = g_leaf;
+    gi->gcap[DN_SPLIT] = g_split;
+    gi->gcap[DN_MERGE] = g_merge;
+    auto add_pass = [&](cudaGraph_t gr, cudaGraphNode_t d, int ip, int ie) {
       d = add_kernel(gr, d, reinterpret_cast<const void*>(k_g_part_local<K, HV, CNT>), g_part, NT, tsm,
-                     a_s);
+                     a_s, dn ? dn + ip : nullptr);
       d = add_kernel(gr, d, reinterpret_cast<const void*>(k_g_part_scan), 1, NT, 0, a_s);
-      d = add_kernel(gr, d, reinterpret_cast<const void*>(k_g_part_exchange<K, HV>), g_exch, NT, 0, a_s);
+      d = add_kernel(gr, d, reinterpret_cast<const void*>(k_g_part_exchange<K, HV>), g_exch, NT, 0, a_s,
+                     dn ? dn + ie : nullptr);
       return d;
     };
-    n = add_pass(body, n);
+    n = add_pass(body, n, DN_PART1, DN_EXCH1);
     n = add_kernel(body, n, reinterpret_cast<const void*>(k_g_mid<K, HV>), 1, 32, 0, a_pass2);
     cudaGraph_t p2 = nullptr;
     n = add_cond(body, n, h_pass2, cudaGraphCondTypeIf, &p2);
-    add_pass(p2, nullptr);
+    add_pass(p2, nullptr, DN_PART2, DN_EXCH2);
     n = add_kernel(body, n, reinterpret_cast<const void*>(k_g_side<K, HV>), 1, 32, 0, a_level);
-    n = add_kernel(body, n, reinterpret_cast<const void*>(k_g_leaf<K, HV, CNT>), g_leaf, NT, tsm, a_s);
+    n = add_kernel(body, n, reinterpret_cast<const void*>(k_g_leaf<K, HV, CNT>), g_leaf, NT, tsm, a_s,
+                   dn ? dn + DN_LEAF : nullptr);
     cudaGraph_t lv = nullptr;
     n = add_cond(body, n, h_level, cudaGraphCondTypeWhile, &lv);
     {
       cudaGraphNode_t q = add_kernel(lv, nullptr, reinterpret_cast<const void*>(k_g_split<K, HV, CNT>),
-                                     g_split, 256, 0, a_s);
-      q = add_kernel(lv, q, reinterpret_cast<const void*>(k_g_merge<K, HV, CNT>), g_merge, MBT, 0, a_s);
+                                     g_split, 256, 0, a_s, dn ? dn + DN_SPLIT : nullptr);
+      q = add_kernel(lv, q, reinterpret_cast<const void*>(k_g_merge<K, HV, CNT>), g_merge, MBT, 0, a_s,
+                     dn ? dn + DN_MERGE : nullptr);
       add_kernel(lv, q, reinterpret_cast<const void*>(k_g_level_end), 1, 32, 0, a_level);
     }
     add_kernel(body, n, reinterpret_cast<const void*>(k_g_end), 1, 32, 0, a_round);
     add_kernel(g, w_round, reinterpret_cast<const void*>(k_g_final<K, HV, CNT>), 1, NT, tsm, a_s);
-    ck(cudaGraphInstantiate(&gi->exec, g, 0));
+    bool all = dyn;
+    for (int i = 0; i < 7 && dyn; ++i) all = all && gi->dn[i] != nullptr;
+    gi->dyn = all ? 1u : 0u;
+    if (cudaGraphInstantiate(&gi->exec, g, 0) != cudaSuccess) {
+      (void)cudaGetLastError();
+      cudaGraphDestroy(g);
+      if (dyn) {  // device-updatable nodes not accepted here: fixed grids
+        for (int i = 0; i < 7; ++i) gi->dn[i] = nullptr;
+        build_impl(gi, pivot, false);
+        return;
+      }
+      throw Err{QMS_ECUDA};
+    }
+    if (gi->dyn && cudaGraphUpload(gi->exec, nullptr) != cudaSuccess) {
+      (void)cudaGetLastError();
+      cudaGraphExecDestroy(gi->exec);
+      cudaGraphDestroy(g);
+      for (int i = 0; i < 7; ++i) gi->dn[i] = nullptr;
+      build_impl(gi, pivot, false);
+      return;
+    }
     gi->graph = g;
+    if (std::getenv("QMS_VERBOSE"))
+      std::fprintf(stderr, "qms: graph built (K=%zu HV=%d CNT=%d pivot=%d): %s grids\n", sizeof(K),
+                   HV ? 1 : 0, CNT ? 1 : 0, pivot, gi->dyn ? "device-sized" : "fixed");
   }
 
   // Takes a free instance able to hold n keys (creating or growing one).
@@ -581,6 +637,11 @@ class GraphRunner {
     h.splits = reinterpret_cast<unsigned long long*>(w + off);
     h.b = 0;
     h.e = n;
+    for (int i = 0; i < 7; ++i) {
+      h.dn[i] = gi->dn[i];
+      h.cap[i] = gi->gcap[i];
+    }
+    h.dyn = gi->dyn;
     ck(cudaMemcpyAsync(gi->d_state, &h, sizeof(DState), cudaMemcpyHostToDevice, st));
     ck(cudaMemsetAsync(h.desc, 0, sizeof(Desc), st));
     ck(cudaGraphLaunch(gi->exec, st));
