@@ -100,7 +100,7 @@ typedef struct {
 
 typedef struct {
   uint64_t comparisons; /* element comparisons made (count_cmps only)          */
-  uint64_t aux_bytes;   /* device workspace used (O(n/8192 + 1) words)          */
+  uint64_t aux_bytes;   /* device workspace used (about n/20 bytes + 18 KB)    */
   uint64_t rounds;      /* partition rounds                                      */
   uint64_t mom_rounds;  /* rounds that used a median-of-medians pivot            */
   uint64_t launches;    /* kernels launched                                      */
@@ -237,7 +237,7 @@ int qms_mergesort(void* d_keys, uint32_t* d_vals, size_t m, size_t buf, int dtyp
  * allocator and forbids any other cudaMalloc, or a latency-critical loop in
  * which an allocation could synchronise the device or fail under memory
  * pressure.  The sort's round descriptor and per-tile counters live in one
- * fixed file-scope device array of about 170 KB, which every GPU that loads
+ * fixed file-scope device array of about 840 KB, which every GPU that loads
  * the library holds until the process exits.  The caller passes the keys as
  * with qms_sort (keys only; opt->profile must be NULL).
  *   - n > QMS_NOALLOC_MAX_N (2^24) returns QMS_EINVAL; nothing runs.

@@ -644,4 +644,164 @@ __device__ __forceinline__ void exchange_ranks(K* keys, uint32_t* vals, uint64_t
   }
 }
 
+// ---------------------------------------------------------------------------
+// Grid-wide partition with small blocks: partition tiles of PT = 2048 keys,
+// one per 128-thread block, so that many blocks per SM keep loads in flight.
+
+constexpr int PNT = 128;        // threads per partition block
+constexpr int PT = PNT * V;     // keys per partition tile
+constexpr int PNWARP = PNT / 32;
+
+template <class K>
+__host__ __device__ constexpr int pk_len() {
+  return PT + PT / (128 / static_cast<int>(sizeof(K))) + 4;
+}
+__host__ __device__ constexpr int pv_len() { return PT + PT / 32 + 4; }
+
+// Exclusive scan over the PNT threads of a partition block (scratch: PNWARP + 1).
+__device__ __forceinline__ uint32_t pblock_excl_scan(uint32_t x, uint32_t* scratch, uint32_t* total) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const uint32_t inc = warp_incl_scan(x);
+  if (lane == 31) scratch[w] = inc;
+  __syncthreads();
+  if (w == 0) {
+    const uint32_t s = lane < PNWARP ? scratch[lane] : 0u;
+    const uint32_t si = warp_incl_scan(s);
+    if (lane < PNWARP) scratch[lane] = si - s;
+    if (lane == 31) scratch[PNWARP] = si;
+  }
+  __syncthreads();
+  const uint32_t r = scratch[w] + inc - x;
+  *total = scratch[PNWARP];
+  __syncthreads();
+  return r;
+}
+
+// Local partition of one partition tile g[0, cnt) (cnt <= PT): left keys
+// (key < piv, or key <= piv when le) gathered at the front; returns their
+// number.  Shared: sk (pk_len), sv (pv_len), scratch (PNWARP + 1 words).
+template <class K, bool HV, bool CNT>
+__device__ __forceinline__ uint32_t part_local_small(K* g, uint32_t* gv, int cnt, K piv, bool le,
+                                                     int xf, K* sk, uint32_t* sv, uint32_t* scratch,
+                                                     uint64_t& cmp) {
+  K x[V];
+  uint32_t y[V];
+  uint32_t flags = 0, lc = 0, nc = 0;
+#pragma unroll
+  for (int j = 0; j < V; ++j) {
+    const int i = j * PNT + threadIdx.x;
+    if (i < cnt) {
+      x[j] = g[i];
+      if (HV) y[j] = gv[i];
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < V; ++j) {
+    const int i = j * PNT + threadIdx.x;
+    if (i < cnt) {
+      const K u = enc_key(x[j], xf);
+      const bool l = le ? !(piv < u) : (u < piv);
+      flags |= static_cast<uint32_t>(l) << j;
+      lc += l;
+      ++nc;
+    }
+  }
+  if (CNT) cmp += nc;
+  uint32_t tot;
+  const uint32_t ex = pblock_excl_scan(lc | ((nc - lc) << 16), scratch, &tot);
+  const uint32_t c = tot & 0xffffu;
+  if (c == 0 || c == static_cast<uint32_t>(cnt)) return c;  // already partitioned
+  uint32_t offL = ex & 0xffffu, offR = c + (ex >> 16);
+#pragma unroll
+  for (int j = 0; j < V; ++j) {
+    const int i = j * PNT + threadIdx.x;
+    if (i < cnt) {
+      const uint32_t dst = ((flags >> j) & 1u) ? offL++ : offR++;
+      sk[sk_i<K>(dst)] = x[j];
+      if (HV) sv[sv_i(dst)] = y[j];
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < V; ++j) {
+    const int i = j * PNT + threadIdx.x;
+    if (i < cnt) {
+      g[i] = sk[sk_i<K>(i)];
+      if (HV) gv[i] = sv[sv_i(i)];
+    }
+  }
+  return c;
+}
+
+// Exchange of misplaced keys (step 3 of the partition, tiles of PT keys):
+// warp w handles ranks [jw, jw + 32 * EXW); one lane finds the chunk's first
+// tile on each side, then lane l swaps ranks jw + l + 32k (consecutive lanes,
+// consecutive positions inside a run), walking its tiles forward.
+constexpr int EXW = 8;                 // ranks per lane
+constexpr uint64_t EXJ = 32ull * EXW;  // ranks per warp
+
+// Swaps the misplaced pairs of ranks [jw, jw + EXJ) (jw a multiple of EXJ).
+// wtl/wtr give, per warp, the tile holding its first left / right rank.
+template <class K, bool HV>
+__device__ __forceinline__ void exchange_warp(K* keys, uint32_t* vals, uint64_t lo, uint64_t s,
+                                              const uint32_t* counts, const uint64_t* pml,
+                                              const uint64_t* pmr, const uint32_t* wtl,
+                                              const uint32_t* wtr, uint64_t jw, uint64_t mis) {
+  const unsigned lane = threadIdx.x & 31u;
+  uint32_t tl = wtl[jw / EXJ], tr = wtr[jw / EXJ];
+  // Positions first (walking the tiles with their bounds kept in registers),
+  // then all loads, then all stores: a lane keeps 2 * EXW loads in flight.
+  uint64_t l_lo = pml[tl], l_hi = pml[tl + 1], l_base = lo + static_cast<uint64_t>(tl) * PT + counts[tl];
+  uint64_t r_lo = pmr[tr], r_hi = pmr[tr + 1];
+  uint64_t r_base = lo + static_cast<uint64_t>(tr) * PT;
+  if (r_base < s) r_base = s;
+  uint64_t lp[EXW], rp[EXW];
+#pragma unroll
+  for (int q = 0; q < EXW; ++q) {
+    const uint64_t j = jw + lane + 32u * q;
+    lp[q] = rp[q] = ~0ull;
+    if (j < mis) {
+      while (j >= l_hi) {
+        ++tl;
+        l_lo = l_hi;
+        l_hi = pml[tl + 1];
+        l_base = lo + static_cast<uint64_t>(tl) * PT + counts[tl];
+      }
+      while (j >= r_hi) {
+        ++tr;
+        r_lo = r_hi;
+        r_hi = pmr[tr + 1];
+        r_base = lo + static_cast<uint64_t>(tr) * PT;
+        if (r_base < s) r_base = s;
+      }
+      lp[q] = l_base + (j - l_lo);
+      rp[q] = r_base + (j - r_lo);
+    }
+  }
+  K a[EXW], b[EXW];
+  uint32_t va[EXW], vb[EXW];
+#pragma unroll
+  for (int q = 0; q < EXW; ++q) {
+    if (lp[q] != ~0ull) {
+      a[q] = keys[lp[q]];
+      b[q] = keys[rp[q]];
+      if (HV) {
+        va[q] = vals[lp[q]];
+        vb[q] = vals[rp[q]];
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < EXW; ++q) {
+    if (lp[q] != ~0ull) {
+      keys[lp[q]] = b[q];
+      keys[rp[q]] = a[q];
+      if (HV) {
+        vals[lp[q]] = vb[q];
+        vals[rp[q]] = va[q];
+      }
+    }
+  }
+}
+
 }  // namespace qms

@@ -35,6 +35,8 @@ struct DState {
   unsigned long long* pml;
   unsigned long long* pmr;
   unsigned long long* splits;
+  uint32_t* wtl;
+  uint32_t* wtr;
   // driver state
   unsigned long long b, e;          // remaining range
   unsigned long long lo, hi, parked;  // current partition pass
@@ -47,13 +49,13 @@ struct DState {
   // Work nodes whose grid the control kernels size to the round's work
   // (device-updatable kernel nodes); null when the graph was built with
   // fixed grids.  cap: the fixed grid the node was built with.
-  cudaGraphDeviceNode_t dn[7];
-  unsigned int cap[7];
+  cudaGraphDeviceNode_t dn[11];
+  unsigned int cap[11];
   unsigned int dyn;
 };
 
 enum : int { DN_PART1 = 0, DN_EXCH1 = 1, DN_PART2 = 2, DN_EXCH2 = 3, DN_LEAF = 4, DN_SPLIT = 5,
-             DN_MERGE = 6 };
+             DN_MERGE = 6, DN_CHUNK1 = 7, DN_PREF1 = 8, DN_CHUNK2 = 9, DN_PREF2 = 10, DN_COUNT = 11 };
 
 // Sets a work node's grid to cover `units` blocks (at least 1, at most its
 // built-in grid).
@@ -106,8 +108,15 @@ __global__ void k_g_begin(DState* S, cudaGraphConditionalHandle h_round) {
   s.parked = e - 1;
   s.le = 0;
   s.pass2 = 0;
-  size_node(s, DN_PART1, (n - 1 + TILE - 1) / TILE);
+  {
+    const uint64_t nt = (n - 1 + PT - 1) / PT;
+    const uint64_t ch = scan_chunk(nt);
+    size_node(s, DN_PART1, nt);
+    size_node(s, DN_CHUNK1, (nt + ch - 1) / ch);
+    size_node(s, DN_PREF1, (nt + ch - 1) / ch);
+  }
   Desc* d = s.desc;
+  d->L = 0;
   if (rule == RULE_MOM) {
     ++s.mom_rounds;
     d->sel_prefix = 0;
@@ -272,79 +281,50 @@ __global__ void k_g_mom_place(DState* S) {
   d->tie = d->sel_eq > 1 ? 1u : 0u;
 }
 
-// Partition pass over [lo, hi) (mode le), fixed grid striding over tiles.
+// Partition pass over [lo, hi) (mode le), grid striding over partition tiles.
 template <class K, bool HV, bool CNT>
-__global__ void __launch_bounds__(NT) k_g_part_local(DState* S) {
+__global__ void __launch_bounds__(PNT) k_g_part_local(DState* S) {
   count_launch(S);
   DState& s = *S;
   if (!s.active) return;
-  extern __shared__ __align__(16) unsigned char smem[];
-  const auto sm = TileSmem<K, HV>::carve(smem);
+  __shared__ K sk[pk_len<K>()];
+  __shared__ uint32_t sv[HV ? pv_len() : 1];
+  __shared__ uint32_t scr[PNWARP + 1];
   uint64_t cmp = 0;
   const K piv = static_cast<K>(s.desc->pivot);
-  const uint64_t lo = s.lo, n = s.hi - s.lo, ntiles = (n + TILE - 1) / TILE;
+  const uint64_t lo = s.lo, n = s.hi - s.lo, ntiles = (n + PT - 1) / PT;
   K* keys = static_cast<K*>(s.keys);
   for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const uint64_t off = t * TILE;
-    const int cnt = static_cast<int>((n - off) < static_cast<uint64_t>(TILE) ? (n - off) : TILE);
-    const uint32_t c = part_local_tile<K, HV, CNT>(sm, keys + lo + off, HV ? s.vals + lo + off : nullptr,
-                                                   cnt, piv, s.le != 0, s.xf, cmp);
-    if (threadIdx.x == 0) s.counts[t] = c;
+    const uint64_t off = t * PT;
+    const int cnt = static_cast<int>((n - off) < static_cast<uint64_t>(PT) ? (n - off) : PT);
+    __syncthreads();
+    const uint32_t c = part_local_small<K, HV, CNT>(keys + lo + off, HV ? s.vals + lo + off : nullptr,
+                                                    cnt, piv, s.le != 0, s.xf, sk, sv, scr, cmp);
+    if (threadIdx.x == 0) {
+      s.counts[t] = c;
+      atomicAdd(&s.desc->L, static_cast<unsigned long long>(c));
+    }
   }
   if (CNT) flush_count(cmp, &s.desc->cmp);
 }
 
-__global__ static void __launch_bounds__(NT) k_g_part_scan(DState* S) {
+__global__ static void __launch_bounds__(NT) k_g_part_chunks(DState* S) {
   count_launch(S);
   DState& s = *S;
   if (!s.active) return;
-  __shared__ uint64_t scr[NWARP + 1];
-  const uint64_t lo = s.lo, hi = s.hi;
-  const uint32_t ntiles = static_cast<uint32_t>((hi - lo + TILE - 1) / TILE);
-  const uint32_t* counts = s.counts;
-  uint64_t sum = 0;
-  for (uint32_t t = threadIdx.x; t < ntiles; t += NT) sum += counts[t];
-  uint64_t L;
-  (void)block_excl_scan_u64(sum, scr, &L);
-  const uint64_t sb = lo + L;
-  const uint32_t chunk = (ntiles + NT - 1) / NT;
-  const uint32_t t0 = threadIdx.x * chunk;
-  const uint32_t t1 = (t0 + chunk < ntiles) ? t0 + chunk : ntiles;
-  uint64_t sl = 0, sr = 0;
-  for (uint32_t t = t0; t < t1; ++t) {
-    const uint64_t ts = lo + static_cast<uint64_t>(t) * TILE;
-    const uint64_t te = (ts + TILE < hi) ? ts + TILE : hi;
-    const uint64_t cs = ts + counts[t];
-    const uint64_t lend = te < sb ? te : sb;
-    const uint64_t rbeg = ts > sb ? ts : sb;
-    sl += lend > cs ? lend - cs : 0;
-    sr += cs > rbeg ? cs - rbeg : 0;
-  }
-  uint64_t totl, totr;
-  uint64_t bl = block_excl_scan_u64(sl, scr, &totl);
-  uint64_t br = block_excl_scan_u64(sr, scr, &totr);
-  for (uint32_t t = t0; t < t1; ++t) {
-    s.pml[t] = bl;
-    s.pmr[t] = br;
-    const uint64_t ts = lo + static_cast<uint64_t>(t) * TILE;
-    const uint64_t te = (ts + TILE < hi) ? ts + TILE : hi;
-    const uint64_t cs = ts + counts[t];
-    const uint64_t lend = te < sb ? te : sb;
-    const uint64_t rbeg = ts > sb ? ts : sb;
-    bl += lend > cs ? lend - cs : 0;
-    br += cs > rbeg ? cs - rbeg : 0;
-  }
-  if (threadIdx.x == 0) {
-    s.pml[ntiles] = totl;
-    s.pmr[ntiles] = totr;
-    s.desc->L = L;
-    s.desc->mis = totl;
-    if (totl != totr) {
-      s.desc->err |= 1u;
-      s.active = 0;
-    }
-    size_node(s, s.pass2 ? DN_EXCH2 : DN_EXCH1,
-              (totl + static_cast<unsigned long long>(NT) * EXV - 1) / (static_cast<unsigned long long>(NT) * EXV));
+  scan_chunks_body(s.lo, s.hi, s.counts, s.desc);
+}
+
+__global__ static void __launch_bounds__(NT) k_g_part_prefix(DState* S) {
+  count_launch(S);
+  DState& s = *S;
+  if (!s.active) return;
+  scan_prefix_body(s.lo, s.hi, s.counts, reinterpret_cast<uint64_t*>(s.pml),
+                   reinterpret_cast<uint64_t*>(s.pmr), s.wtl, s.wtr, s.desc);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (s.desc->err) s.active = 0;
+    const unsigned long long per = static_cast<unsigned long long>(NT) * EXW;
+    size_node(s, s.pass2 ? DN_EXCH2 : DN_EXCH1, (s.desc->mis + per - 1) / per);
   }
 }
 
@@ -355,13 +335,12 @@ __global__ void __launch_bounds__(NT) k_g_part_exchange(DState* S) {
   if (!s.active) return;
   const uint64_t mis = s.desc->mis, lo = s.lo;
   const uint64_t sb = lo + s.desc->L;
-  const uint32_t ntiles = static_cast<uint32_t>((s.hi - lo + TILE - 1) / TILE);
-  for (uint64_t j0 = (blockIdx.x * static_cast<uint64_t>(NT) + threadIdx.x) * EXV; j0 < mis;
-       j0 += static_cast<uint64_t>(gridDim.x) * NT * EXV) {
-    exchange_ranks<K, HV>(static_cast<K*>(s.keys), s.vals, lo, sb, s.counts,
-                          reinterpret_cast<const uint64_t*>(s.pml), reinterpret_cast<const uint64_t*>(s.pmr),
-                          ntiles, j0, mis);
-  }
+  const uint64_t w0 = (blockIdx.x * static_cast<uint64_t>(NT) + threadIdx.x) >> 5;
+  const uint64_t nw = (static_cast<uint64_t>(gridDim.x) * NT) >> 5;
+  for (uint64_t jw = w0 * EXJ; jw < mis; jw += nw * EXJ)
+    exchange_warp<K, HV>(static_cast<K*>(s.keys), s.vals, lo, sb, s.counts,
+                         reinterpret_cast<const uint64_t*>(s.pml), reinterpret_cast<const uint64_t*>(s.pmr),
+                         s.wtl, s.wtr, jw, mis);
 }
 
 template <class K, bool HV>
@@ -380,7 +359,12 @@ __global__ void k_g_mid(DState* S, cudaGraphConditionalHandle h_pass2) {
       s.le = 1;
       s.parked = ~0ull;
       s.pass2 = 1;
-      size_node(s, DN_PART2, (s.hi - s.lo + TILE - 1) / TILE);
+      s.desc->L = 0;
+      const uint64_t nt = (s.hi - s.lo + PT - 1) / PT;
+      const uint64_t ch = scan_chunk(nt);
+      size_node(s, DN_PART2, nt);
+      size_node(s, DN_CHUNK2, (nt + ch - 1) / ch);
+      size_node(s, DN_PREF2, (nt + ch - 1) / ch);
     }
   }
   cudaGraphSetConditional(h_pass2, s.pass2);

@@ -26,7 +26,15 @@ struct Desc {
   unsigned int tie;  // pivot sample saw a tie: run the second (<=) pass
   unsigned int err;  // nonzero: an internal consistency check failed
   unsigned int hist[256];
+  unsigned long long csum[2 * 1024];  // per-chunk misplaced sums of the partition scan
 };
+
+// The partition scan works on chunks of scan_chunk(ntiles) tiles, at most
+// 1024 chunks.
+__host__ __device__ inline uint64_t scan_chunk(uint64_t ntiles) {
+  const uint64_t c = (ntiles + 1023) / 1024;
+  return c < 2048 ? 2048 : c;
+}
 
 // ---------------------------------------------------------------------------
 // Base case / Mergesort leaves: sort tiles of P[0, m); with to_buf the
@@ -262,21 +270,27 @@ __global__ void k_mom_place(K* keys, uint32_t* vals, uint64_t b, uint64_t e, uin
 // In-place partition of [lo, hi) around desc->pivot (Sec. 2; every element is
 // compared with the pivot once).
 
-// Step 1: local partition of every tile, left count per tile.
+// Step 1: local partition of every partition tile (PT keys, PNT threads),
+// left count per tile.
 template <class K, bool HV, bool CNT>
-__global__ void __launch_bounds__(NT) k_part_local(K* keys, uint32_t* vals, uint64_t lo, uint64_t hi,
-                                                   int le, int xf, Desc* desc, uint32_t* counts) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  const auto s = TileSmem<K, HV>::carve(smem);
+__global__ void __launch_bounds__(PNT) k_part_local(K* keys, uint32_t* vals, uint64_t lo, uint64_t hi,
+                                                    int le, int xf, Desc* desc, uint32_t* counts) {
+  __shared__ K sk[pk_len<K>()];
+  __shared__ uint32_t sv[HV ? pv_len() : 1];
+  __shared__ uint32_t scr[PNWARP + 1];
   uint64_t cmp = 0;
   const K piv = static_cast<K>(desc->pivot);
-  const uint64_t n = hi - lo, ntiles = (n + TILE - 1) / TILE;
+  const uint64_t n = hi - lo, ntiles = (n + PT - 1) / PT;
   for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const uint64_t off = t * TILE;
-    const int cnt = static_cast<int>((n - off) < static_cast<uint64_t>(TILE) ? (n - off) : TILE);
-    const uint32_t c = part_local_tile<K, HV, CNT>(s, keys + lo + off, HV ? vals + lo + off : nullptr,
-                                                   cnt, piv, le != 0, xf, cmp);
-    if (threadIdx.x == 0) counts[t] = c;
+    const uint64_t off = t * PT;
+    const int cnt = static_cast<int>((n - off) < static_cast<uint64_t>(PT) ? (n - off) : PT);
+    __syncthreads();
+    const uint32_t c = part_local_small<K, HV, CNT>(keys + lo + off, HV ? vals + lo + off : nullptr, cnt,
+                                                    piv, le != 0, xf, sk, sv, scr, cmp);
+    if (threadIdx.x == 0) {
+      counts[t] = c;
+      atomicAdd(&desc->L, static_cast<unsigned long long>(c));
+    }
   }
   if (CNT) flush_count(cmp, &desc->cmp);
 }
@@ -311,65 +325,130 @@ __device__ __forceinline__ uint64_t block_excl_scan_u64(uint64_t x, uint64_t* sc
   return r;
 }
 
-// Step 2 (one block): L = sum of counts, then the per-tile misplaced run
-// lengths and their exclusive prefix sums pml / pmr (ntiles + 1 entries).
-static __global__ void __launch_bounds__(NT) k_part_scan(const uint32_t* counts, uint32_t ntiles, uint64_t lo,
-                                                  uint64_t hi, uint64_t* pml, uint64_t* pmr,
-                                                  Desc* desc) {
+// Step 2: with L (the number of left keys, summed by step 1) known, the
+// misplaced run lengths of every tile and their exclusive prefix sums pml /
+// pmr (ntiles + 1 entries).  Two parallel passes over chunks of tiles: the
+// sums of each chunk, then each chunk's prefixes.
+
+__device__ __forceinline__ void tile_mis(uint64_t lo, uint64_t hi, uint64_t sb, uint32_t t, uint32_t c,
+                                         uint64_t* ml, uint64_t* mr) {
+  const uint64_t ts = lo + static_cast<uint64_t>(t) * PT;
+  const uint64_t te = (ts + PT < hi) ? ts + PT : hi;
+  const uint64_t cs = ts + c;
+  const uint64_t lend = te < sb ? te : sb;
+  const uint64_t rbeg = ts > sb ? ts : sb;
+  *ml = lend > cs ? lend - cs : 0;
+  *mr = cs > rbeg ? cs - rbeg : 0;
+}
+
+__device__ __forceinline__ void scan_chunks_body(uint64_t lo, uint64_t hi, const uint32_t* counts,
+                                                 Desc* desc) {
   __shared__ uint64_t scr[NWARP + 1];
-  uint64_t sum = 0;
-  for (uint32_t t = threadIdx.x; t < ntiles; t += NT) sum += counts[t];
-  uint64_t L;
-  (void)block_excl_scan_u64(sum, scr, &L);
-  const uint64_t s = lo + L;
-  const uint32_t chunk = (ntiles + NT - 1) / NT;
-  const uint32_t t0 = threadIdx.x * chunk;
-  const uint32_t t1 = (t0 + chunk < ntiles) ? t0 + chunk : ntiles;
+  const uint32_t ntiles = static_cast<uint32_t>((hi - lo + PT - 1) / PT);
+  const uint64_t ch = scan_chunk(ntiles);
+  const uint64_t sb = lo + desc->L;
+  const uint64_t t0 = blockIdx.x * ch;
+  const uint64_t t1 = (t0 + ch < ntiles) ? t0 + ch : ntiles;
   uint64_t sl = 0, sr = 0;
-  for (uint32_t t = t0; t < t1; ++t) {
-    const uint64_t ts = lo + static_cast<uint64_t>(t) * TILE;
-    const uint64_t te = (ts + TILE < hi) ? ts + TILE : hi;
-    const uint64_t cs = ts + counts[t];
-    const uint64_t lend = te < s ? te : s;
-    const uint64_t rbeg = ts > s ? ts : s;
-    sl += lend > cs ? lend - cs : 0;
-    sr += cs > rbeg ? cs - rbeg : 0;
+  for (uint64_t t = t0 + threadIdx.x; t < t1; t += NT) {
+    uint64_t ml, mr;
+    tile_mis(lo, hi, sb, static_cast<uint32_t>(t), counts[t], &ml, &mr);
+    sl += ml;
+    sr += mr;
   }
-  uint64_t totl, totr;
-  uint64_t bl = block_excl_scan_u64(sl, scr, &totl);
-  uint64_t br = block_excl_scan_u64(sr, scr, &totr);
-  for (uint32_t t = t0; t < t1; ++t) {
-    pml[t] = bl;
-    pmr[t] = br;
-    const uint64_t ts = lo + static_cast<uint64_t>(t) * TILE;
-    const uint64_t te = (ts + TILE < hi) ? ts + TILE : hi;
-    const uint64_t cs = ts + counts[t];
-    const uint64_t lend = te < s ? te : s;
-    const uint64_t rbeg = ts > s ? ts : s;
-    bl += lend > cs ? lend - cs : 0;
-    br += cs > rbeg ? cs - rbeg : 0;
-  }
+  uint64_t tl, tr;
+  (void)block_excl_scan_u64(sl, scr, &tl);
+  (void)block_excl_scan_u64(sr, scr, &tr);
   if (threadIdx.x == 0) {
-    pml[ntiles] = totl;
-    pmr[ntiles] = totr;
-    desc->L = L;
-    desc->mis = totl;
-    if (totl != totr) desc->err |= 1u;
+    desc->csum[2 * blockIdx.x] = tl;
+    desc->csum[2 * blockIdx.x + 1] = tr;
   }
 }
 
-// Step 3: exchange the misplaced elements by rank.
+__device__ __forceinline__ void scan_prefix_body(uint64_t lo, uint64_t hi, const uint32_t* counts,
+                                                 uint64_t* pml, uint64_t* pmr, uint32_t* wtl,
+                                                 uint32_t* wtr, Desc* desc) {
+  __shared__ uint64_t scr[NWARP + 1];
+  const uint32_t ntiles = static_cast<uint32_t>((hi - lo + PT - 1) / PT);
+  const uint64_t ch = scan_chunk(ntiles);
+  const uint32_t nchunks = static_cast<uint32_t>((ntiles + ch - 1) / ch);
+  const uint64_t sb = lo + desc->L;
+  // prefix of the chunk sums before this chunk (and the totals)
+  uint64_t bl = 0, br = 0, al = 0, ar = 0;
+  for (uint32_t c = threadIdx.x; c < nchunks; c += NT) {
+    const uint64_t l = desc->csum[2 * c], r = desc->csum[2 * c + 1];
+    if (c < blockIdx.x) {
+      bl += l;
+      br += r;
+    }
+    al += l;
+    ar += r;
+  }
+  uint64_t base_l, base_r, tot_l, tot_r;
+  (void)block_excl_scan_u64(bl, scr, &base_l);
+  (void)block_excl_scan_u64(br, scr, &base_r);
+  (void)block_excl_scan_u64(al, scr, &tot_l);
+  (void)block_excl_scan_u64(ar, scr, &tot_r);
+  // this chunk: each thread a contiguous run of tiles
+  const uint64_t t0 = blockIdx.x * ch;
+  const uint64_t t1 = (t0 + ch < ntiles) ? t0 + ch : ntiles;
+  const uint64_t per = (t1 - t0 + NT - 1) / NT;
+  const uint64_t u0 = t0 + threadIdx.x * per;
+  const uint64_t u1 = (u0 + per < t1) ? u0 + per : t1;
+  uint64_t sl = 0, sr = 0;
+  for (uint64_t t = u0; t < u1; ++t) {
+    uint64_t ml, mr;
+    tile_mis(lo, hi, sb, static_cast<uint32_t>(t), counts[t], &ml, &mr);
+    sl += ml;
+    sr += mr;
+  }
+  uint64_t dummy;
+  uint64_t pl = base_l + block_excl_scan_u64(sl, scr, &dummy);
+  uint64_t pr = base_r + block_excl_scan_u64(sr, scr, &dummy);
+  for (uint64_t t = u0; t < u1; ++t) {
+    pml[t] = pl;
+    pmr[t] = pr;
+    uint64_t ml, mr;
+    tile_mis(lo, hi, sb, static_cast<uint32_t>(t), counts[t], &ml, &mr);
+    // exchange warps whose first left / right rank falls in this tile
+    for (uint64_t w = (pl + EXJ - 1) / EXJ; w * EXJ < pl + ml; ++w) wtl[w] = static_cast<uint32_t>(t);
+    for (uint64_t w = (pr + EXJ - 1) / EXJ; w * EXJ < pr + mr; ++w) wtr[w] = static_cast<uint32_t>(t);
+    pl += ml;
+    pr += mr;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    pml[ntiles] = tot_l;
+    pmr[ntiles] = tot_r;
+    desc->mis = tot_l;
+    if (tot_l != tot_r) desc->err |= 1u;
+  }
+}
+
+static __global__ void __launch_bounds__(NT) k_part_chunks(uint64_t lo, uint64_t hi,
+                                                           const uint32_t* counts, Desc* desc) {
+  scan_chunks_body(lo, hi, counts, desc);
+}
+
+static __global__ void __launch_bounds__(NT) k_part_prefix(uint64_t lo, uint64_t hi,
+                                                           const uint32_t* counts, uint64_t* pml,
+                                                           uint64_t* pmr, uint32_t* wtl,
+                                                           uint32_t* wtr, Desc* desc) {
+  scan_prefix_body(lo, hi, counts, pml, pmr, wtl, wtr, desc);
+}
+
+// Step 3: exchange the misplaced elements by rank (one warp per chunk of
+// EXJ ranks).
 template <class K, bool HV>
 __global__ void __launch_bounds__(NT) k_part_exchange(K* keys, uint32_t* vals, uint64_t lo,
                                                       const uint32_t* counts, const uint64_t* pml,
-                                                      const uint64_t* pmr, uint32_t ntiles,
-                                                      const Desc* desc) {
+                                                      const uint64_t* pmr, const uint32_t* wtl,
+                                                      const uint32_t* wtr, const Desc* desc) {
   const uint64_t mis = desc->mis;
   const uint64_t s = lo + desc->L;
-  for (uint64_t j0 = (blockIdx.x * static_cast<uint64_t>(NT) + threadIdx.x) * EXV; j0 < mis;
-       j0 += static_cast<uint64_t>(gridDim.x) * NT * EXV) {
-    exchange_ranks<K, HV>(keys, vals, lo, s, counts, pml, pmr, ntiles, j0, mis);
-  }
+  const uint64_t w0 = (blockIdx.x * static_cast<uint64_t>(NT) + threadIdx.x) >> 5;
+  const uint64_t nw = (static_cast<uint64_t>(gridDim.x) * NT) >> 5;
+  for (uint64_t jw = w0 * EXJ; jw < mis; jw += nw * EXJ)
+    exchange_warp<K, HV>(keys, vals, lo, s, counts, pml, pmr, wtl, wtr, jw, mis);
 }
 
 // Step 4: the pivot parked at position `parked` moves to its final index

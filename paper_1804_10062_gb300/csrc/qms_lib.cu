@@ -58,6 +58,34 @@ struct DescHead {
 };
 
 // Device workspace for one sort: descriptor + per-tile counters.
+constexpr size_t round256(size_t x) { return (x + 255) / 256 * 256; }
+
+// Byte offsets of one sort's workspace: round descriptor, per-tile left
+// counts, the two misplaced-rank prefixes, merge splits and the exchange
+// warps' start tiles.
+struct WsLayout {
+  size_t counts = 0, pml = 0, pmr = 0, splits = 0, wtl = 0, wtr = 0, total = 0;
+  constexpr explicit WsLayout(uint64_t n) {
+    const uint64_t nt = n / PT + 2;
+    const uint64_t ns = n / 1024 + 3;  // merge tiles of at least 1024 outputs
+    const uint64_t nw = n / EXJ + 2;   // at most n / 2 misplaced ranks
+    size_t off = round256(sizeof(Desc));
+    counts = off;
+    off += round256(nt * 4);
+    pml = off;
+    off += round256((nt + 1) * 8);
+    pmr = off;
+    off += round256((nt + 1) * 8);
+    splits = off;
+    off += round256(ns * 8);
+    wtl = off;
+    off += round256(nw * 4);
+    wtr = off;
+    off += round256(nw * 4);
+    total = off;
+  }
+};
+
 struct Workspace {
   unsigned char* base = nullptr;
   size_t bytes = 0;
@@ -66,14 +94,21 @@ struct Workspace {
   uint64_t* pml = nullptr;
   uint64_t* pmr = nullptr;
   uint64_t* splits = nullptr;
+  uint32_t* wtl = nullptr;
+  uint32_t* wtr = nullptr;
   cudaStream_t st = nullptr;
 
-  static constexpr uint64_t kMinMergeTile = 1024;  // smallest MergeCfg<K, HV>::MT
-  static size_t size_for(uint64_t n) {
-    const uint64_t nt = n / TILE + 2;
-    const uint64_t ns = n / kMinMergeTile + 3;
-    return ((sizeof(Desc) + 255) / 256) * 256 + ((nt * 4 + 255) / 256) * 256 + 2 * (nt + 1) * 8 +
-           ns * 8;
+  static size_t size_for(uint64_t n) { return WsLayout(n).total; }
+  // Points the arrays into [p, p + size_for(n)).
+  void place(unsigned char* p, uint64_t n) {
+    const WsLayout w(n);
+    desc = reinterpret_cast<Desc*>(p);
+    counts = reinterpret_cast<uint32_t*>(p + w.counts);
+    pml = reinterpret_cast<uint64_t*>(p + w.pml);
+    pmr = reinterpret_cast<uint64_t*>(p + w.pmr);
+    splits = reinterpret_cast<uint64_t*>(p + w.splits);
+    wtl = reinterpret_cast<uint32_t*>(p + w.wtl);
+    wtr = reinterpret_cast<uint32_t*>(p + w.wtr);
   }
   void alloc(uint64_t n, cudaStream_t s) {
     st = s;
@@ -83,17 +118,7 @@ struct Workspace {
       (void)cudaGetLastError();
       throw Err{QMS_ENOMEM};
     }
-    const uint64_t nt = n / TILE + 2;
-    size_t off = 0;
-    desc = reinterpret_cast<Desc*>(base);
-    off += ((sizeof(Desc) + 255) / 256) * 256;
-    counts = reinterpret_cast<uint32_t*>(base + off);
-    off += ((nt * 4 + 255) / 256) * 256;
-    pml = reinterpret_cast<uint64_t*>(base + off);
-    off += (nt + 1) * 8;
-    pmr = reinterpret_cast<uint64_t*>(base + off);
-    off += (nt + 1) * 8;
-    splits = reinterpret_cast<uint64_t*>(base + off);
+    place(base, n);
     ck(cudaMemsetAsync(desc, 0, sizeof(Desc), s));
   }
   ~Workspace() {
@@ -162,7 +187,7 @@ class Sorter {
     static bool a1 = false, a2 = false, a3 = false, a4 = false;
     allow_smem(k_leaf_sort<K, HV, CNT>, tile_smem_bytes<K, HV>(), a1);
     (void)a2;
-    allow_smem(k_part_local<K, HV, CNT>, tile_smem_bytes<K, HV>(), a3);
+    (void)a3;
     allow_smem(k_pivot_sample<K, HV, CNT>, tile_smem_bytes<K, true>(), a4);
   }
 
@@ -261,21 +286,26 @@ class Sorter {
   // Returns L, the number of left elements.
   uint64_t partition(uint64_t lo, uint64_t hi, bool le, uint64_t parked, unsigned* tie) {
     const uint64_t n = hi - lo;
-    const uint64_t nt = (n + TILE - 1) / TILE;
+    const uint64_t nt = (n + PT - 1) / PT;
     if (n > 0) {
+      ck(cudaMemsetAsync(&ws_.desc->L, 0, sizeof(unsigned long long), st_));
       prof_.begin(st_);
-      k_part_local<K, HV, CNT><<<grid_of(nt), NT, tile_smem_bytes<K, HV>(), st_>>>(
-          keys_, vals_, lo, hi, le ? 1 : 0, xf_, ws_.desc, ws_.counts);
+      k_part_local<K, HV, CNT><<<grid_of(nt), PNT, 0, st_>>>(keys_, vals_, lo, hi, le ? 1 : 0, xf_,
+                                                             ws_.desc, ws_.counts);
       prof_.end(st_, QMS_K_PART_LOCAL, 2 * n * ES);
+      const uint64_t ch = scan_chunk(nt);
+      const unsigned nch = static_cast<unsigned>((nt + ch - 1) / ch);
       prof_.begin(st_);
-      k_part_scan<<<1, NT, 0, st_>>>(ws_.counts, static_cast<uint32_t>(nt), lo, hi, ws_.pml,
-                                     ws_.pmr, ws_.desc);
+      k_part_chunks<<<nch, NT, 0, st_>>>(lo, hi, ws_.counts, ws_.desc);
+      k_part_prefix<<<nch, NT, 0, st_>>>(lo, hi, ws_.counts, ws_.pml, ws_.pmr, ws_.wtl, ws_.wtr,
+                                         ws_.desc);
       prof_.end(st_, QMS_K_PART_SCAN, nt * 20);
+      launched();
       const uint64_t maxmis = n / 2 + 1;
-      const uint64_t per = static_cast<uint64_t>(NT) * EXV;
+      const uint64_t per = static_cast<uint64_t>(NT) * EXW;
       prof_.begin(st_);
       k_part_exchange<K, HV><<<grid_of((maxmis + per - 1) / per), NT, 0, st_>>>(
-          keys_, vals_, lo, ws_.counts, ws_.pml, ws_.pmr, static_cast<uint32_t>(nt), ws_.desc);
+          keys_, vals_, lo, ws_.counts, ws_.pml, ws_.pmr, ws_.wtl, ws_.wtr, ws_.desc);
       prof_.end(st_, QMS_K_PART_EXCHANGE, 0);  // bytes added once mis is known
       launched(3);
     } else {
@@ -366,8 +396,8 @@ class Sorter {
 // each, so concurrent calls use separate instances from a pool.
 
 struct GraphInst {
-  cudaGraphDeviceNode_t dn[7] = {};
-  unsigned int gcap[7] = {};  // built-in grid of each work node
+  cudaGraphDeviceNode_t dn[DN_COUNT] = {};
+  unsigned int gcap[DN_COUNT] = {};  // built-in grid of each work node
   unsigned int dyn = 0;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -380,12 +410,7 @@ struct GraphInst {
   bool busy = false;
 };
 
-inline size_t graph_ws_bytes(uint64_t cap) {
-  const uint64_t nt = cap / TILE + 2;
-  const uint64_t ns = cap / 1024 + 3;  // merge tiles of at least 1024 outputs
-  return ((sizeof(Desc) + 255) / 256) * 256 + ((nt * 4 + 255) / 256) * 256 + 2 * (nt + 1) * 8 +
-         ns * 8;
-}
+inline size_t graph_ws_bytes(uint64_t cap) { return WsLayout(cap).total; }
 
 std::mutex g_graph_mu;
 std::map<std::tuple<int, int, int, int, int>, std::vector<GraphInst*>> g_graphs;
@@ -448,8 +473,6 @@ class GraphRunner {
     const size_t tsm = tile_smem_bytes<K, HV>(), tsm_s = tile_smem_bytes<K, true>();
     static std::once_flag once;
     std::call_once(once, [&] {
-      cudaFuncSetAttribute(reinterpret_cast<const void*>(k_g_part_local<K, HV, CNT>),
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(tsm));
       cudaFuncSetAttribute(reinterpret_cast<const void*>(k_g_leaf<K, HV, CNT>),
                            cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(tsm));
       cudaFuncSetAttribute(reinterpret_cast<const void*>(k_g_final<K, HV, CNT>),
@@ -462,7 +485,7 @@ class GraphRunner {
       ck(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, f, block, smem));
       return static_cast<unsigned>(sms * std::max(o, 1));
     };
-    const unsigned g_part = occ(reinterpret_cast<const void*>(k_g_part_local<K, HV, CNT>), NT, tsm) * 2;
+    const unsigned g_part = occ(reinterpret_cast<const void*>(k_g_part_local<K, HV, CNT>), PNT, 0) * 2;
     const unsigned g_leaf = occ(reinterpret_cast<const void*>(k_g_leaf<K, HV, CNT>), NT, tsm) * 2;
     const unsigned g_exch = static_cast<unsigned>(sms) * 4;
     const unsigned g_split = static_cast<unsigned>(sms) * 4;
@@ -506,10 +529,17 @@ class GraphRunner {
     gi->gcap[DN_LEAF] = g_leaf;
     gi->gcap[DN_SPLIT] = g_split;
     gi->gcap[DN_MERGE] = g_merge;
+    const unsigned g_scan = 1024;  // at most 1024 chunks
+    gi->gcap[DN_CHUNK1] = gi->gcap[DN_PREF1] = gi->gcap[DN_CHUNK2] = gi->gcap[DN_PREF2] = g_scan;
     auto add_pass = [&](cudaGraph_t gr, cudaGraphNode_t d, int ip, int ie) {
-      d = add_kernel(gr, d, reinterpret_cast<const void*>(k_g_part_local<K, HV, CNT>), g_part, NT, tsm,
+      d = add_kernel(gr, d, reinterpret_cast<const void*>(k_g_part_local<K, HV, CNT>), g_part, PNT, 0,
                      a_s, dn ? dn + ip : nullptr);
-      d = add_kernel(gr, d, reinterpret_cast<const void*>(k_g_part_scan), 1, NT, 0, a_s);
+      const int ic = (ip == DN_PART1) ? DN_CHUNK1 : DN_CHUNK2;
+      const int ipf = (ip == DN_PART1) ? DN_PREF1 : DN_PREF2;
+      d = add_kernel(gr, d, reinterpret_cast<const void*>(k_g_part_chunks), g_scan, NT, 0, a_s,
+                     dn ? dn + ic : nullptr);
+      d = add_kernel(gr, d, reinterpret_cast<const void*>(k_g_part_prefix), g_scan, NT, 0, a_s,
+                     dn ? dn + ipf : nullptr);
       d = add_kernel(gr, d, reinterpret_cast<const void*>(k_g_part_exchange<K, HV>), g_exch, NT, 0, a_s,
                      dn ? dn + ie : nullptr);
       return d;
@@ -534,13 +564,13 @@ class GraphRunner {
     add_kernel(body, n, reinterpret_cast<const void*>(k_g_end), 1, 32, 0, a_round);
     add_kernel(g, w_round, reinterpret_cast<const void*>(k_g_final<K, HV, CNT>), 1, NT, tsm, a_s);
     bool all = dyn;
-    for (int i = 0; i < 7 && dyn; ++i) all = all && gi->dn[i] != nullptr;
+    for (int i = 0; i < DN_COUNT && dyn; ++i) all = all && gi->dn[i] != nullptr;
     gi->dyn = all ? 1u : 0u;
     if (cudaGraphInstantiate(&gi->exec, g, 0) != cudaSuccess) {
       (void)cudaGetLastError();
       cudaGraphDestroy(g);
       if (dyn) {  // device-updatable nodes not accepted here: fixed grids
-        for (int i = 0; i < 7; ++i) gi->dn[i] = nullptr;
+        for (int i = 0; i < DN_COUNT; ++i) gi->dn[i] = nullptr;
         build_impl(gi, pivot, false);
         return;
       }
@@ -550,7 +580,7 @@ class GraphRunner {
       (void)cudaGetLastError();
       cudaGraphExecDestroy(gi->exec);
       cudaGraphDestroy(g);
-      for (int i = 0; i < 7; ++i) gi->dn[i] = nullptr;
+      for (int i = 0; i < DN_COUNT; ++i) gi->dn[i] = nullptr;
       build_impl(gi, pivot, false);
       return;
     }
@@ -616,7 +646,6 @@ class GraphRunner {
       ~Rel() { release(g); }
     } rel{gi};
     const uint64_t cap = gi->cap;
-    const uint64_t nt = cap / TILE + 2;
     unsigned char* w = gi->ws;
     DState& h = *gi->h_state;
     std::memset(&h, 0, sizeof(DState));
@@ -625,19 +654,17 @@ class GraphRunner {
     h.n = n;
     h.xf = xform_of(dtype);
     h.pivot = pivot;
-    size_t off = 0;
+    const WsLayout wl(cap);
     h.desc = reinterpret_cast<Desc*>(w);
-    off += ((sizeof(Desc) + 255) / 256) * 256;
-    h.counts = reinterpret_cast<uint32_t*>(w + off);
-    off += ((nt * 4 + 255) / 256) * 256;
-    h.pml = reinterpret_cast<unsigned long long*>(w + off);
-    off += (nt + 1) * 8;
-    h.pmr = reinterpret_cast<unsigned long long*>(w + off);
-    off += (nt + 1) * 8;
-    h.splits = reinterpret_cast<unsigned long long*>(w + off);
+    h.counts = reinterpret_cast<uint32_t*>(w + wl.counts);
+    h.pml = reinterpret_cast<unsigned long long*>(w + wl.pml);
+    h.pmr = reinterpret_cast<unsigned long long*>(w + wl.pmr);
+    h.splits = reinterpret_cast<unsigned long long*>(w + wl.splits);
+    h.wtl = reinterpret_cast<uint32_t*>(w + wl.wtl);
+    h.wtr = reinterpret_cast<uint32_t*>(w + wl.wtr);
     h.b = 0;
     h.e = n;
-    for (int i = 0; i < 7; ++i) {
+    for (int i = 0; i < DN_COUNT; ++i) {
       h.dn[i] = gi->dn[i];
       h.cap[i] = gi->gcap[i];
     }
@@ -862,17 +889,13 @@ int run_batched(void* keys, uint32_t* vals, const uint64_t* d_off, size_t nseg, 
 // descriptor and the per-tile counters of one sort live in a fixed-size
 // file-scope device array instead of a workspace allocated per call.
 
-constexpr size_t round256(size_t x) { return (x + 255) / 256 * 256; }
 constexpr uint64_t kNoallocMaxN = QMS_NOALLOC_MAX_N;
-constexpr size_t kNoallocTiles = kNoallocMaxN / TILE + 2;
-constexpr size_t kNoallocSplits = kNoallocMaxN / 1024 + 3;
-constexpr size_t kNoallocBytes = round256(sizeof(Desc)) + round256(kNoallocTiles * 4) +
-                                 2 * (kNoallocTiles + 1) * 8 + kNoallocSplits * 8;
+constexpr size_t kNoallocBytes = WsLayout(kNoallocMaxN).total;
 
 }  // namespace
 }  // namespace qms
 
-// Scratch of qms_sort_noalloc (about 170 KB).  Every GPU that loads this
+// Scratch of qms_sort_noalloc (about 840 KB).  Every GPU that loads this
 // library holds it until the process exits.  All calls share it.
 static __device__ __align__(256) unsigned char qms_noalloc_scratch[qms::kNoallocBytes];
 
@@ -912,16 +935,7 @@ int run_noalloc(void* keys, uint64_t n, int dtype, int pivot, cudaStream_t st,
   Workspace ws;  // base stays null: nothing is allocated and nothing is freed
   ws.st = st;
   ws.bytes = kNoallocBytes;
-  size_t off = 0;
-  ws.desc = reinterpret_cast<Desc*>(base + off);
-  off += round256(sizeof(Desc));
-  ws.counts = reinterpret_cast<uint32_t*>(base + off);
-  off += round256(kNoallocTiles * 4);
-  ws.pml = reinterpret_cast<uint64_t*>(base + off);
-  off += (kNoallocTiles + 1) * 8;
-  ws.pmr = reinterpret_cast<uint64_t*>(base + off);
-  off += (kNoallocTiles + 1) * 8;
-  ws.splits = reinterpret_cast<uint64_t*>(base + off);
+  ws.place(base, kNoallocMaxN);
   // The array keeps the previous call's contents: the descriptor (counters,
   // flags, selection state) must start from zero.
   ck(cudaMemsetAsync(ws.desc, 0, sizeof(Desc), st));
