@@ -209,12 +209,15 @@ __device__ __forceinline__ int merge_path_smem(const K* sk, int a0, int la, int 
 }
 
 // Serial stable merge of V outputs starting at A index ai / B index bi.
-// Keys land in k[], the source indices (for payloads) in src[].
+// Keys land in k[], the source indices (for payloads) in src[].  Branch
+// free: one shared-memory load per output, of the element that replaces the
+// one just taken.  A load past a run's end stays inside the tile's array and
+// is never used (the bound checks decide first).
 template <class K, bool CNT>
 __device__ __forceinline__ void serial_merge(const K* sk, int ai, int ae, int bi, int be, K (&k)[V],
                                              int (&src)[V], uint64_t& cmp) {
-  K ka = (ai < ae) ? sk[sk_i<K>(ai)] : key_max<K>();
-  K kb = (bi < be) ? sk[sk_i<K>(bi)] : key_max<K>();
+  K ka = sk[sk_i<K>(ai)];
+  K kb = sk[sk_i<K>(bi)];
 #pragma unroll
   for (int j = 0; j < V; ++j) {
     const bool a_ok = ai < ae, b_ok = bi < be;
@@ -222,21 +225,68 @@ __device__ __forceinline__ void serial_merge(const K* sk, int ai, int ae, int bi
     const bool tb = b_ok && (!a_ok || kb < ka);
     k[j] = tb ? kb : ka;
     src[j] = tb ? bi : ai;
-    if (tb) {
-      ++bi;
-      if (bi < be) kb = sk[sk_i<K>(bi)];
-    } else {
-      ++ai;
-      if (ai < ae) ka = sk[sk_i<K>(ai)];
+    ai += tb ? 0 : 1;
+    bi += tb ? 1 : 0;
+    const K nk = sk[sk_i<K>(tb ? bi : ai)];
+    ka = tb ? ka : nk;
+    kb = tb ? nk : kb;
+  }
+}
+
+// Batcher's merge-exchange network (Knuth, TAOCP 5.2.2, Algorithm M) for
+// N = 2^t inputs, as a compile-time comparator list.
+struct NetPair {
+  int a, b;
+};
+template <int N>
+struct MergeExchangeNet {
+  NetPair c[N * N];
+  int len;
+  constexpr MergeExchangeNet() : c{}, len(0) {
+    int t = 0;
+    while ((1 << t) < N) ++t;
+    for (int p = 1 << (t - 1); p > 0; p >>= 1) {
+      int q = 1 << (t - 1), r = 0, d = p;
+      for (;;) {
+        for (int i = 0; i + d < N; ++i)
+          if ((i & p) == r) c[len++] = NetPair{i, i + d};
+        if (q == p) break;
+        d = q - p;
+        q >>= 1;
+        r = p;
+      }
     }
+  }
+};
+template <int N>
+inline constexpr MergeExchangeNet<N> kNet{};
+
+// Sorts the V register items of one thread with the network (comparator I
+// onwards).
+template <class K, bool HV, int I = 0>
+__device__ __forceinline__ void net_sort(K (&k)[V], uint32_t (&v)[V]) {
+  if constexpr (I < kNet<V>.len) {
+    constexpr int a = kNet<V>.c[I].a, b = kNet<V>.c[I].b;
+    const bool sw = k[b] < k[a];
+    const K lo = sw ? k[b] : k[a];
+    const K hi = sw ? k[a] : k[b];
+    k[a] = lo;
+    k[b] = hi;
+    if (HV) {
+      const uint32_t x = sw ? v[b] : v[a];
+      const uint32_t y = sw ? v[a] : v[b];
+      v[a] = x;
+      v[b] = y;
+    }
+    net_sort<K, HV, I + 1>(k, v);
   }
 }
 
 // ---------------------------------------------------------------------------
-// Base case X: stable sort of one full tile in shared memory.
-// Register odd-even transposition sort of V items per thread (compare-
-// exchange network, shuffles not needed since items are thread-local), then
-// log2(NT) rounds of merge-path merges in shared memory.
+// Base case X: sort of one full tile in shared memory.  A sorting network
+// on the V items each thread holds in registers (Batcher's merge exchange,
+// 63 comparators for V = 16), then log2(NT) rounds of merge-path merges in
+// shared memory.
 
 template <class K, bool HV, bool CNT>
 __device__ void block_sort_tile(TileSmem<K, HV> s, uint64_t& cmp, int P = NT) {
@@ -253,23 +303,8 @@ __device__ void block_sort_tile(TileSmem<K, HV> s, uint64_t& cmp, int P = NT) {
       k[j] = s.k[sk_i<K>(tid * V + j)];
       if (HV) v[j] = s.v[sv_i(tid * V + j)];
     }
-#pragma unroll
-    for (int r = 0; r < V; ++r) {
-#pragma unroll
-      for (int i = r & 1; i + 1 < V; i += 2) {
-        if (k[i + 1] < k[i]) {
-          const K t = k[i];
-          k[i] = k[i + 1];
-          k[i + 1] = t;
-          if (HV) {
-            const uint32_t u = v[i];
-            v[i] = v[i + 1];
-            v[i + 1] = u;
-          }
-        }
-      }
-    }
-    if (CNT) cmp += V * (V - 1) / 2;
+    net_sort<K, HV>(k, v);
+    if (CNT) cmp += kNet<V>.len;
   }
   __syncthreads();
   if (tid < P) {

@@ -4,6 +4,8 @@ Key-only results must be byte-identical to the oracle (the ascending order is
 unique).  Key-value results must have byte-identical keys and the same
 (key, payload) multiset (payload = original index, so every pair is
 identified); the order among equal keys is not fixed."""
+import math
+
 import numpy as np
 import pytest
 
@@ -152,10 +154,13 @@ def test_config1_permutation_m3(q):
     st = q.qms_sort(d, pivot="m3", count_cmps=True, dtype="u32")
     out = _host(d, "u32")
     assert out.tobytes() == ref.tobytes()
-    assert st["comparisons"] > 0
-    # the GPU runs other networks than the oracle's merges; its count is
-    # reported, bounded here only loosely
-    assert st["comparisons"] < 40 * n * 20
+    # No comparison sort decides a permutation of n keys with fewer than
+    # lg(n!) comparisons.  The GPU's merges add merge-path searches and its
+    # leaves run sorting networks, so it compares more than the oracle's
+    # Fig. 3 Mergesort, but by a bounded factor (1.38 measured at 2^20).
+    lg_fact = math.lgamma(n + 1) / math.log(2)
+    assert st["comparisons"] >= lg_fact
+    assert c_ref <= st["comparisons"] <= 1.7 * c_ref
 
 
 @pytest.mark.parametrize("pivot", ["m3", "sqrtn", "mom", "hybrid"])
