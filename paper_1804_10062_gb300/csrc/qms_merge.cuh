@@ -45,59 +45,70 @@ struct MGeom {
 // loaded from the A/B slices and from the buffer tile by the same thread,
 // which then stores its buffer value into that X slot: the tile's consumed
 // slots receive exactly its buffer elements.
+//
+// Shared-memory indices carry one padding element per 128 bytes.  For the
+// striped element i = j*MBT + thread that is j*(MBT + MBT/PE) + pad(thread),
+// and for the blocked element d + j (d = thread*VM, a multiple of VM, and
+// PE a multiple of 2*VM) it is pad(d) + j: both a per-thread base plus a
+// compile-time offset.
 template <class K, bool HV, bool CNT>
-__device__ __forceinline__ void merge_level_tile(K* keys, uint32_t* vals, uint64_t X, uint64_t Y,
-                                                 uint64_t m, uint64_t L, const uint64_t* splits,
-                                                 int xf, Desc* desc, uint64_t t) {
+__device__ __forceinline__ void merge_level_tile_impl(K* keys, uint32_t* vals,
+                                                      const MGeom<MergeCfg<K, HV>::MT>& gm,
+                                                      uint64_t a_lo, uint64_t a_hi, K* gy,
+                                                      uint32_t* gyv, uint64_t X, int xf, Desc* desc,
+                                                      K* sin, K* sout, uint32_t* svin,
+                                                      uint32_t* svout) {
   using C = MergeCfg<K, HV>;
   constexpr int VM = C::VM, MT = C::MT;
-  __shared__ K sin[C::IN_K];
-  __shared__ K sout[C::IN_K];
-  __shared__ uint32_t svin[HV ? C::IN_V : 1];
-  __shared__ uint32_t svout[HV ? C::IN_V : 1];
+  constexpr int PE = 128 / static_cast<int>(sizeof(K));  // keys per padded row
+  static_assert(PE % (2 * VM) == 0 || VM % PE == 0, "blocked rows must not straddle padding");
+  constexpr int SK = MBT + MBT / PE;  // padded stride of one striped row of keys
+  constexpr int SV = MBT + MBT / 32;
   uint64_t cmp = 0;
-  const MGeom<MT> gm(m, L, t);
-  const uint64_t a_lo = splits[t];
-  const uint64_t a_hi = (gm.d1 == gm.la + gm.lb) ? gm.la : splits[t + 1];
-  const uint64_t b_lo = gm.d0 - a_lo;
-  K* ga = keys + X + gm.pbase + a_lo;
-  K* gb = keys + X + gm.pbase + gm.la + b_lo;
-  K* gy = keys + Y + t * MT;
-  uint32_t* gav = HV ? vals + X + gm.pbase + a_lo : nullptr;
-  uint32_t* gbv = HV ? vals + X + gm.pbase + gm.la + b_lo : nullptr;
-  uint32_t* gyv = HV ? vals + Y + t * MT : nullptr;
+  const int tid = threadIdx.x;
   const int cnt = static_cast<int>(gm.d1 - gm.d0);
   const int na = static_cast<int>(a_hi - a_lo), nb = cnt - na;
+  const uint64_t b_lo = gm.d0 - a_lo;
+  // element i < na comes from A[a_lo + i], element i >= na from B[b_lo + i - na]
+  K* ga = keys + X + gm.pbase + a_lo;
+  K* gb = keys + X + gm.pbase + gm.la + b_lo - na;
+  uint32_t* gav = HV ? vals + X + gm.pbase + a_lo : nullptr;
+  uint32_t* gbv = HV ? vals + X + gm.pbase + gm.la + b_lo - na : nullptr;
+  const int ps = tid + tid / PE;  // padded striped base
+  const int pv = tid + tid / 32;
   K x[VM], y[VM];
   uint32_t xv[VM], yv[VM];
 #pragma unroll
   for (int j = 0; j < VM; ++j) {
-    const int i = j * MBT + threadIdx.x;
+    const int i = j * MBT + tid;
     if (i < cnt) {
-      x[j] = (i < na) ? ga[i] : gb[i - na];
+      K* src = (i < na ? ga : gb) + i;
+      x[j] = *src;
       y[j] = gy[i];
       if (HV) {
-        xv[j] = (i < na) ? gav[i] : gbv[i - na];
+        xv[j] = (i < na ? gav : gbv)[i];
         yv[j] = gyv[i];
       }
     }
   }
 #pragma unroll
   for (int j = 0; j < VM; ++j) {
-    const int i = j * MBT + threadIdx.x;
+    const int i = j * MBT + tid;
     if (i < cnt) {
-      sin[sk_i<K>(i)] = enc_key(x[j], xf);
-      *((i < na) ? ga + i : gb + (i - na)) = y[j];
+      sin[ps + j * SK] = enc_key(x[j], xf);
+      (i < na ? ga : gb)[i] = y[j];
       if (HV) {
-        svin[sv_i(i)] = xv[j];
-        *((i < na) ? gav + i : gbv + (i - na)) = yv[j];
+        svin[pv + j * SV] = xv[j];
+        (i < na ? gav : gbv)[i] = yv[j];
       }
     }
   }
   __syncthreads();
   // Staged layout: A at logical [0, na), B at [na, cnt).  Thread produces
   // outputs [d, d + VM).
-  const int d = threadIdx.x * VM;
+  const int d = tid * VM;
+  const int pd = d + d / PE;  // padded blocked base
+  const int pdv = d + d / 32;
   if (d < cnt) {
     int lo = d > nb ? d - nb : 0, hi = d < na ? d : na;
     while (lo < hi) {
@@ -106,36 +117,56 @@ __device__ __forceinline__ void merge_level_tile(K* keys, uint32_t* vals, uint64
       if (!(sin[sk_i<K>(na + d - 1 - mid)] < sin[sk_i<K>(mid)])) lo = mid + 1; else hi = mid;
     }
     int ai = lo, bi = na + d - lo;
-    K ka = ai < na ? sin[sk_i<K>(ai)] : key_max<K>();
-    K kb = bi < cnt ? sin[sk_i<K>(bi)] : key_max<K>();
+    // Once both runs are exhausted (only in the last, partial tile) ai keeps
+    // advancing, but never past d + VM <= MT, so every read stays inside
+    // sin; such values are discarded by the bound checks.
+    K ka = sin[sk_i<K>(ai)];
+    K kb = sin[sk_i<K>(bi)];
 #pragma unroll
     for (int j = 0; j < VM; ++j) {
       const bool a_ok = ai < na, b_ok = bi < cnt;
       if (CNT && a_ok && b_ok) ++cmp;
       const bool tb = b_ok && (!a_ok || kb < ka);
       if (d + j < cnt) {
-        sout[sk_i<K>(d + j)] = tb ? kb : ka;
-        if (HV) svout[sv_i(d + j)] = svin[sv_i(tb ? bi : ai)];
+        sout[pd + j] = tb ? kb : ka;
+        if (HV) svout[pdv + j] = svin[sv_i(tb ? bi : ai)];
       }
-      if (tb) {
-        ++bi;
-        if (bi < cnt) kb = sin[sk_i<K>(bi)];
-      } else {
-        ++ai;
-        if (ai < na) ka = sin[sk_i<K>(ai)];
-      }
+      ai += tb ? 0 : 1;
+      bi += tb ? 1 : 0;
+      const K nk = sin[sk_i<K>(tb ? bi : ai)];
+      ka = tb ? ka : nk;
+      kb = tb ? nk : kb;
     }
   }
   __syncthreads();
 #pragma unroll
   for (int j = 0; j < VM; ++j) {
-    const int i = j * MBT + threadIdx.x;
+    const int i = j * MBT + tid;
     if (i < cnt) {
-      gy[i] = dec_key(sout[sk_i<K>(i)], xf);
-      if (HV) gyv[i] = svout[sv_i(i)];
+      gy[i] = dec_key(sout[ps + j * SK], xf);
+      if (HV) gyv[i] = svout[pv + j * SV];
     }
   }
   if (CNT) flush_count(cmp, &desc->cmp);
+}
+
+template <class K, bool HV, bool CNT>
+__device__ __forceinline__ void merge_level_tile(K* keys, uint32_t* vals, uint64_t X, uint64_t Y,
+                                                 uint64_t m, uint64_t L, const uint64_t* splits,
+                                                 int xf, Desc* desc, uint64_t t) {
+  using C = MergeCfg<K, HV>;
+  constexpr int MT = C::MT;
+  const MGeom<MT> gm(m, L, t);
+  const uint64_t a_lo = splits[t];
+  const uint64_t a_hi = (gm.d1 == gm.la + gm.lb) ? gm.la : splits[t + 1];
+  K* gy = keys + Y + t * MT;
+  uint32_t* gyv = HV ? vals + Y + t * MT : nullptr;
+  __shared__ K sin[C::IN_K];
+  __shared__ K sout[C::IN_K];
+  __shared__ uint32_t svin[HV ? C::IN_V : 1];
+  __shared__ uint32_t svout[HV ? C::IN_V : 1];
+  merge_level_tile_impl<K, HV, CNT>(keys, vals, gm, a_lo, a_hi, gy, gyv, X, xf, desc, sin, sout,
+                                    svin, svout);
 }
 
 template <class K, bool HV, bool CNT>
