@@ -14,6 +14,7 @@
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
 #include <cuda_runtime.h>
 
 namespace qms {
@@ -41,6 +42,35 @@ __device__ __forceinline__ uint64_t enc_key(uint64_t b, int xf) {
 }
 __device__ __forceinline__ uint64_t dec_key(uint64_t u, int xf) {
   return xf == XF_I64 ? (u ^ 0x8000000000000000ull) : u;
+}
+
+// The same transforms with the kind fixed at compile time, and with_xf,
+// which calls f with the kind of a launch as such a constant: one uniform
+// branch per call instead of a test per element.
+template <int X>
+using XfC = std::integral_constant<int, X>;
+template <int X>
+__device__ __forceinline__ uint32_t enc_key(uint32_t b, XfC<X>) {
+  return X == XF_F32 ? enc_key(b, XF_F32) : b;
+}
+template <int X>
+__device__ __forceinline__ uint32_t dec_key(uint32_t u, XfC<X>) {
+  return X == XF_F32 ? dec_key(u, XF_F32) : u;
+}
+template <int X>
+__device__ __forceinline__ uint64_t enc_key(uint64_t b, XfC<X>) {
+  return X == XF_I64 ? (b ^ 0x8000000000000000ull) : b;
+}
+template <int X>
+__device__ __forceinline__ uint64_t dec_key(uint64_t u, XfC<X>) {
+  return X == XF_I64 ? (u ^ 0x8000000000000000ull) : u;
+}
+template <class K, class F>
+__device__ __forceinline__ void with_xf(int xf, F&& f) {
+  if (xf == XF_NONE)
+    f(XfC<XF_NONE>{});
+  else
+    f(XfC<sizeof(K) == 4 ? XF_F32 : XF_I64>{});
 }
 
 template <class K>
@@ -730,17 +760,19 @@ __device__ __forceinline__ uint32_t part_local_small(K* g, uint32_t* gv, int cnt
       if (HV) y[j] = gv[i];
     }
   }
+  with_xf<K>(xf, [&](auto xc) {
 #pragma unroll
-  for (int j = 0; j < V; ++j) {
-    const int i = j * PNT + threadIdx.x;
-    if (i < cnt) {
-      const K u = enc_key(x[j], xf);
-      const bool l = le ? !(piv < u) : (u < piv);
-      flags |= static_cast<uint32_t>(l) << j;
-      lc += l;
-      ++nc;
+    for (int j = 0; j < V; ++j) {
+      const int i = j * PNT + threadIdx.x;
+      if (i < cnt) {
+        const K u = enc_key(x[j], xc);
+        const bool l = le ? !(piv < u) : (u < piv);
+        flags |= static_cast<uint32_t>(l) << j;
+        lc += l;
+        ++nc;
+      }
     }
-  }
+  });
   if (CNT) cmp += nc;
   uint32_t tot;
   const uint32_t ex = pblock_excl_scan(lc | ((nc - lc) << 16), scratch, &tot);

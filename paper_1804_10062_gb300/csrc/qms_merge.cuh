@@ -91,18 +91,20 @@ __device__ __forceinline__ void merge_level_tile_impl(K* keys, uint32_t* vals,
       }
     }
   }
+  with_xf<K>(xf, [&](auto xc) {
 #pragma unroll
-  for (int j = 0; j < VM; ++j) {
-    const int i = j * MBT + tid;
-    if (i < cnt) {
-      sin[ps + j * SK] = enc_key(x[j], xf);
-      (i < na ? ga : gb)[i] = y[j];
-      if (HV) {
-        svin[pv + j * SV] = xv[j];
-        (i < na ? gav : gbv)[i] = yv[j];
+    for (int j = 0; j < VM; ++j) {
+      const int i = j * MBT + tid;
+      if (i < cnt) {
+        sin[ps + j * SK] = enc_key(x[j], xc);
+        (i < na ? ga : gb)[i] = y[j];
+        if (HV) {
+          svin[pv + j * SV] = xv[j];
+          (i < na ? gav : gbv)[i] = yv[j];
+        }
       }
     }
-  }
+  });
   __syncthreads();
   // Staged layout: A at logical [0, na), B at [na, cnt).  Thread produces
   // outputs [d, d + VM).
@@ -139,14 +141,16 @@ __device__ __forceinline__ void merge_level_tile_impl(K* keys, uint32_t* vals,
     }
   }
   __syncthreads();
+  with_xf<K>(xf, [&](auto xc) {
 #pragma unroll
-  for (int j = 0; j < VM; ++j) {
-    const int i = j * MBT + tid;
-    if (i < cnt) {
-      gy[i] = dec_key(sout[ps + j * SK], xf);
-      if (HV) gyv[i] = svout[pv + j * SV];
+    for (int j = 0; j < VM; ++j) {
+      const int i = j * MBT + tid;
+      if (i < cnt) {
+        gy[i] = dec_key(sout[ps + j * SK], xc);
+        if (HV) gyv[i] = svout[pv + j * SV];
+      }
     }
-  }
+  });
   if (CNT) flush_count(cmp, &desc->cmp);
 }
 
