@@ -87,6 +87,11 @@ typedef struct {
 #define QMS_FLAG_HOST_DRIVEN 2 /* run the rounds from the host (one launch per step,
                                   one device-to-host read per round) instead of the
                                   device-driven CUDA graph; implied by `profile`     */
+#define QMS_FLAG_LARGER_SIDE 4 /* Mergesort the larger side, with a buffer of half its
+                                  size from the other side (Sec. 2, Fig. 1; Fig. 3's
+                                  "out" with its overlapped final merge), whenever it
+                                  exceeds 8192 keys and that buffer fits.  Default:
+                                  Fig. 3's side rule with a full-size buffer          */
 
 typedef struct {
   int pivot;       /* QMS_PIVOT_*                                              */
@@ -100,7 +105,7 @@ typedef struct {
 
 typedef struct {
   uint64_t comparisons; /* element comparisons made (count_cmps only)          */
-  uint64_t aux_bytes;   /* device workspace used (about n/20 bytes + 18 KB)    */
+  uint64_t aux_bytes;   /* device workspace used (about n/19 bytes + 18 KB)    */
   uint64_t rounds;      /* partition rounds                                      */
   uint64_t mom_rounds;  /* rounds that used a median-of-medians pivot            */
   uint64_t launches;    /* kernels launched                                      */
@@ -226,6 +231,16 @@ int qms_partition(void* d_keys, uint32_t* d_vals, size_t n, int dtype, int pivot
  * and its order permuted. */
 int qms_mergesort(void* d_keys, uint32_t* d_vals, size_t m, size_t buf, int dtype, void* stream);
 
+/* Mergesort with a half-size buffer (Fig. 3 "out" itself): sorts d_keys[0, m)
+ * using the ceil(m/2) slots d_keys[buf, buf + ceil(m/2)) as buffer (buf >= m).
+ * The second half is sorted into the buffer, the first half into the tail of
+ * the part, and the overlapped final merge fills the part.  The buffer's
+ * multiset is preserved and its order permuted.  Errors: QMS_EINVAL (bad
+ * dtype, d_keys NULL with m > 1, buf < m), QMS_ENOMEM, QMS_ECUDA,
+ * QMS_EINTERNAL (a bounded wait of the overlapped merge ran out). */
+int qms_mergesort_half(void* d_keys, uint32_t* d_vals, size_t m, size_t buf, int dtype,
+                       void* stream);
+
 /* ---- Allocation-free sort -------------------------------------------- */
 
 /* Largest n accepted by qms_sort_noalloc. */
@@ -237,7 +252,7 @@ int qms_mergesort(void* d_keys, uint32_t* d_vals, size_t m, size_t buf, int dtyp
  * allocator and forbids any other cudaMalloc, or a latency-critical loop in
  * which an allocation could synchronise the device or fail under memory
  * pressure.  The sort's round descriptor and per-tile counters live in one
- * fixed file-scope device array of about 840 KB, which every GPU that loads
+ * fixed file-scope device array of about 900 KB, which every GPU that loads
  * the library holds until the process exits.  The caller passes the keys as
  * with qms_sort (keys only; opt->profile must be NULL).
  *   - n > QMS_NOALLOC_MAX_N (2^24) returns QMS_EINVAL; nothing runs.

@@ -35,27 +35,32 @@ struct DState {
   unsigned long long* pml;
   unsigned long long* pmr;
   unsigned long long* splits;
+  unsigned* flags;  // overlapped-merge tile flags
   uint32_t* wtl;
   uint32_t* wtr;
+  int fig3;  // always Fig. 3's side rule
   // driver state
   unsigned long long b, e;          // remaining range
   unsigned long long lo, hi, parked;  // current partition pass
   unsigned long long k, eq;         // pivot block of the round
-  unsigned long long P, Bb, m;      // Mergesort part and buffer
+  unsigned long long P0, M0, B0;    // the round's Mergesort: part, size, buffer
+  unsigned long long P, Bb, m;      // current phase: part, size, buffer
   unsigned long long X, Y, L;       // current merge level
   unsigned long long rounds, mom_rounds;
   unsigned long long launches;  // kernels of the graph that ran (all nodes count)
   unsigned int le, levels, to_buf, mom_next, rule, active, pass2, pad;
+  unsigned int half, phase;  // larger side with a half buffer: phases 0 and 1
   // Work nodes whose grid the control kernels size to the round's work
   // (device-updatable kernel nodes); null when the graph was built with
   // fixed grids.  cap: the fixed grid the node was built with.
-  cudaGraphDeviceNode_t dn[11];
-  unsigned int cap[11];
+  cudaGraphDeviceNode_t dn[14];
+  unsigned int cap[14];
   unsigned int dyn;
 };
 
 enum : int { DN_PART1 = 0, DN_EXCH1 = 1, DN_PART2 = 2, DN_EXCH2 = 3, DN_LEAF = 4, DN_SPLIT = 5,
-             DN_MERGE = 6, DN_CHUNK1 = 7, DN_PREF1 = 8, DN_CHUNK2 = 9, DN_PREF2 = 10, DN_COUNT = 11 };
+             DN_MERGE = 6, DN_CHUNK1 = 7, DN_PREF1 = 8, DN_CHUNK2 = 9, DN_PREF2 = 10,
+             DN_OSPLIT = 11, DN_OMERGE = 12, DN_ODEPS = 13, DN_COUNT = 14 };
 
 // Sets a work node's grid to cover `units` blocks (at least 1, at most its
 // built-in grid).
@@ -370,13 +375,58 @@ __global__ void k_g_mid(DState* S, cudaGraphConditionalHandle h_pass2) {
   cudaGraphSetConditional(h_pass2, s.pass2);
 }
 
+// Sets up Mergesort phase ph of the round: the part, its buffer, the
+// number of levels and where the leaves go, so that the sorted part ends in
+// its own range (Fig. 3 rule, one phase) or in its target (half-buffer
+// rounds: phase 0 sorts the second half into the buffer, phase 1 the first
+// half into the tail of the part).
 template <class K, bool HV>
-__global__ void k_g_side(DState* S, cudaGraphConditionalHandle h_level) {
+__device__ __forceinline__ void setup_phase(DState& s, unsigned ph, cudaGraphConditionalHandle h_level) {
+  bool into_buf = false;
+  if (!s.half) {
+    s.P = s.P0;
+    s.m = s.M0;
+    s.Bb = s.B0;
+  } else {
+    const unsigned long long q = s.M0 / 2, r = s.M0 - q;
+    into_buf = true;
+    if (ph == 0) {
+      s.P = s.P0 + q;
+      s.m = r;
+      s.Bb = s.B0;
+    } else {
+      s.P = s.P0;
+      s.m = q;
+      s.Bb = s.P0 + r;
+    }
+  }
+  s.phase = ph;
+  const uint64_t leaves = (s.m + TILE - 1) / TILE;
+  unsigned levels = 0;
+  while ((1ull << levels) < leaves) ++levels;
+  s.levels = levels;
+  s.to_buf = ((levels & 1u) != 0) != into_buf ? 1u : 0u;
+  s.X = s.to_buf ? s.Bb : s.P;
+  s.Y = s.to_buf ? s.P : s.Bb;
+  s.L = TILE;
+  size_node(s, DN_LEAF, leaves);
+  const unsigned long long mt = MergeCfg<K, HV>::MT;
+  const unsigned long long mtiles = (s.m + mt - 1) / mt;
+  size_node(s, DN_SPLIT, (mtiles + 255) / 256);
+  size_node(s, DN_MERGE, mtiles);
+  cudaGraphSetConditional(h_level, s.levels > 0 ? 1u : 0u);
+}
+
+template <class K, bool HV>
+__global__ void k_g_side(DState* S, cudaGraphConditionalHandle h_level,
+                         cudaGraphConditionalHandle h_phase, cudaGraphConditionalHandle h_ovl) {
   count_launch(S);
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   DState& s = *S;
   s.levels = 0;
   s.m = 0;
+  s.M0 = 0;
+  s.half = 0;
   if (s.active) {
     const uint64_t b = s.b, e = s.e, nn = e - b, k = s.k;
     const uint64_t eq = s.pass2 ? s.desc->L : 0;
@@ -387,33 +437,90 @@ __global__ void k_g_side(DState* S, cudaGraphConditionalHandle h_level) {
     }
     const uint64_t rb = k + 1 + eq;
     const uint64_t nl = k - b, nr = e - rb;
-    const bool left = (eq == 0) ? (k < b + nn / 2) : (nl <= nr);
-    if (left) {
-      s.P = b;
-      s.m = nl;
-      s.Bb = rb;
+    const int side = choose_side(b, e, k, eq, s.fig3 != 0);
+    s.half = (side == SIDE_LARGER_LEFT || side == SIDE_LARGER_RIGHT) ? 1u : 0u;
+    if (side == SIDE_LEFT || side == SIDE_LARGER_LEFT) {
+      s.P0 = b;
+      s.M0 = nl;
+      s.B0 = rb;
       s.b = rb;
     } else {
-      s.P = rb;
-      s.m = nr;
-      s.Bb = b;
+      s.P0 = rb;
+      s.M0 = nr;
+      s.B0 = b;
       s.e = k;
     }
-    const uint64_t leaves = (s.m + TILE - 1) / TILE;
-    unsigned levels = 0;
-    while ((1ull << levels) < leaves) ++levels;
-    s.levels = levels;
-    s.to_buf = levels & 1u;
-    s.X = s.to_buf ? s.Bb : s.P;
-    s.Y = s.to_buf ? s.P : s.Bb;
-    s.L = TILE;
-    size_node(s, DN_LEAF, leaves);
-    const unsigned long long mt = MergeCfg<K, HV>::MT;
-    const unsigned long long mtiles = (s.m + mt - 1) / mt;
-    size_node(s, DN_SPLIT, (mtiles + 255) / 256);
-    size_node(s, DN_MERGE, mtiles);
+    setup_phase<K, HV>(s, 0, h_level);
+    if (s.half) {
+      const unsigned long long mt = MergeCfg<K, HV>::MT;
+      const unsigned long long mtiles = (s.M0 + mt - 1) / mt;
+      size_node(s, DN_OSPLIT, (mtiles + 255) / 256);
+      size_node(s, DN_ODEPS, (mtiles + 255) / 256);
+      size_node(s, DN_OMERGE, mtiles);
+    }
+  } else {
+    cudaGraphSetConditional(h_level, 0u);
   }
-  cudaGraphSetConditional(h_level, s.levels > 0 ? 1u : 0u);
+  cudaGraphSetConditional(h_phase, s.active ? 1u : 0u);
+  cudaGraphSetConditional(h_ovl, s.active && s.half ? 1u : 0u);
+}
+
+// After a Mergesort phase: the next phase of a half-buffer round, or done.
+template <class K, bool HV>
+__global__ void k_g_phase_end(DState* S, cudaGraphConditionalHandle h_phase,
+                              cudaGraphConditionalHandle h_level) {
+  count_launch(S);
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  DState& s = *S;
+  if (s.active && s.half && s.phase == 0 && !s.desc->err) {
+    setup_phase<K, HV>(s, 1, h_level);
+    cudaGraphSetConditional(h_phase, 1u);
+  } else {
+    cudaGraphSetConditional(h_phase, 0u);
+  }
+}
+
+template <class K, bool HV, bool CNT>
+__global__ void __launch_bounds__(256) k_g_ovl_split(DState* S) {
+  count_launch(S);
+  const DState& s = *S;
+  if (!s.active) return;
+  const uint64_t q = s.M0 / 2, r = s.M0 - q;
+  uint64_t cmp = 0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) s.desc->oticket = 0;
+  const uint64_t nw = (static_cast<uint64_t>(gridDim.x) * blockDim.x) >> 5;
+  const uint64_t ngroups = (s.M0 + MergeCfg<K, HV>::MT * 32ull - 1) / (MergeCfg<K, HV>::MT * 32ull);
+  for (uint64_t w = (blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x) >> 5; w < ngroups;
+       w += nw)
+    ovl_split_group<K, HV, CNT>(static_cast<const K*>(s.keys), s.B0, r, s.P0, q, s.xf,
+                                reinterpret_cast<uint64_t*>(s.splits), s.flags, w, cmp);
+  if (CNT) flush_count(cmp, &s.desc->cmp);
+}
+
+// The wait ranges live in the exchange start tables, which the partition
+// alone uses.
+template <class K, bool HV>
+__global__ void __launch_bounds__(256) k_g_ovl_deps(DState* S) {
+  count_launch(S);
+  const DState& s = *S;
+  if (!s.active) return;
+  constexpr int MT = MergeCfg<K, HV>::MT;
+  const uint64_t q = s.M0 / 2, r = s.M0 - q;
+  const uint64_t ntiles = (s.M0 + MT - 1) / MT;
+  for (uint64_t t = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; t < ntiles;
+       t += static_cast<uint64_t>(gridDim.x) * blockDim.x)
+    ovl_deps_tile<MT>(r, q, reinterpret_cast<const uint64_t*>(s.splits), s.wtl, s.wtr, t);
+}
+
+template <class K, bool HV, bool CNT>
+__global__ void __launch_bounds__(MBT, MergeCfg<K, HV>::MINB) k_g_ovl_merge(DState* S) {
+  count_launch(S);
+  const DState& s = *S;
+  if (!s.active) return;
+  const uint64_t q = s.M0 / 2, r = s.M0 - q;
+  ovl_merge_loop<K, HV, CNT>(static_cast<K*>(s.keys), s.vals, s.B0, r, s.P0, q,
+                             reinterpret_cast<const uint64_t*>(s.splits), s.wtl, s.wtr, s.flags,
+                             s.xf, s.desc);
 }
 
 template <class K, bool HV, bool CNT>

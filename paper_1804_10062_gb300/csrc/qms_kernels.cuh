@@ -23,11 +23,33 @@ struct Desc {
   unsigned long long sel_eq;
   unsigned long long pos;
   unsigned long long bytes;       // algorithmic bytes reported by the batched form
+  unsigned long long oticket;     // next tile of the overlapped merge
   unsigned int tie;  // pivot sample saw a tie: run the second (<=) pass
   unsigned int err;  // nonzero: an internal consistency check failed
   unsigned int hist[256];
   unsigned long long csum[2 * 1024];  // per-chunk misplaced sums of the partition scan
 };
+
+// Side choice of a round on [b, e) whose pivot block is [k, k + 1 + eq).
+//   SIDE_LARGER_*: Mergesort the larger side with a buffer of half its size
+//     taken from the front of the other side (Sec. 2 allows either side when
+//     the other one can hold the buffer; Fig. 1 takes the larger one), used
+//     when that side is longer than one tile and the buffer fits.
+//   SIDE_LEFT / SIDE_RIGHT: Fig. 3's rule, a full-size buffer: the left side
+//     iff the pivot lies left of the integer midpoint; after a three-way
+//     split, the smaller side.
+enum : int { SIDE_LEFT = 0, SIDE_RIGHT = 1, SIDE_LARGER_LEFT = 2, SIDE_LARGER_RIGHT = 3 };
+__host__ __device__ inline int choose_side(uint64_t b, uint64_t e, uint64_t k, uint64_t eq,
+                                           bool fig3) {
+  const uint64_t nn = e - b, rb = k + 1 + eq, nl = k - b, nr = e - rb;
+  if (!fig3) {
+    const uint64_t big = nl > nr ? nl : nr, small = nl > nr ? nr : nl;
+    if (big > static_cast<uint64_t>(TILE) && big - big / 2 <= small)
+      return nl >= nr ? SIDE_LARGER_LEFT : SIDE_LARGER_RIGHT;
+  }
+  const bool left = (eq == 0) ? (k < b + nn / 2) : (nl <= nr);
+  return left ? SIDE_LEFT : SIDE_RIGHT;
+}
 
 // The partition scan works on chunks of scan_chunk(ntiles) tiles, at most
 // 1024 chunks.

@@ -61,10 +61,10 @@ struct DescHead {
 constexpr size_t round256(size_t x) { return (x + 255) / 256 * 256; }
 
 // Byte offsets of one sort's workspace: round descriptor, per-tile left
-// counts, the two misplaced-rank prefixes, merge splits and the exchange
-// warps' start tiles.
+// counts, the two misplaced-rank prefixes, merge splits, overlapped-merge
+// tile flags and the exchange warps' start tiles.
 struct WsLayout {
-  size_t counts = 0, pml = 0, pmr = 0, splits = 0, wtl = 0, wtr = 0, total = 0;
+  size_t counts = 0, pml = 0, pmr = 0, splits = 0, flags = 0, wtl = 0, wtr = 0, total = 0;
   constexpr explicit WsLayout(uint64_t n) {
     const uint64_t nt = n / PT + 2;
     const uint64_t ns = n / 1024 + 3;  // merge tiles of at least 1024 outputs
@@ -78,6 +78,8 @@ struct WsLayout {
     off += round256((nt + 1) * 8);
     splits = off;
     off += round256(ns * 8);
+    flags = off;  // overlapped-merge tile flags, one per split
+    off += round256(ns * 4);
     wtl = off;
     off += round256(nw * 4);
     wtr = off;
@@ -85,6 +87,12 @@ struct WsLayout {
     total = off;
   }
 };
+
+// Status of a finished sort from the descriptor's error bits.
+inline int err_code(unsigned err) {
+  if (err == 0) return QMS_OK;
+  return (err & kErrOvlWait) ? QMS_ETIMEOUT : QMS_EINTERNAL;
+}
 
 struct Workspace {
   unsigned char* base = nullptr;
@@ -94,6 +102,7 @@ struct Workspace {
   uint64_t* pml = nullptr;
   uint64_t* pmr = nullptr;
   uint64_t* splits = nullptr;
+  unsigned* flags = nullptr;
   uint32_t* wtl = nullptr;
   uint32_t* wtr = nullptr;
   cudaStream_t st = nullptr;
@@ -107,6 +116,7 @@ struct Workspace {
     pml = reinterpret_cast<uint64_t*>(p + w.pml);
     pmr = reinterpret_cast<uint64_t*>(p + w.pmr);
     splits = reinterpret_cast<uint64_t*>(p + w.splits);
+    flags = reinterpret_cast<unsigned*>(p + w.flags);
     wtl = reinterpret_cast<uint32_t*>(p + w.wtl);
     wtr = reinterpret_cast<uint32_t*>(p + w.wtr);
   }
@@ -193,6 +203,7 @@ class Sorter {
 
   uint64_t rounds = 0, mom_rounds = 0, launches = 0;
   uint64_t exchanged_bytes = 0;  // algorithmic bytes of the exchange steps
+  bool fig3_side = true;         // Fig. 3's side rule; false: the larger side when it fits
 
   // ---- steps ------------------------------------------------------------
 
@@ -210,16 +221,19 @@ class Sorter {
 
   // Mergesort of P[0, m) with the disjoint buffer Bb[0, m) (Fig. 3 "out"
   // with a full-size buffer: every level merges one region into the other).
-  void mergesort(uint64_t P, uint64_t m, uint64_t Bb) {
-    if (m <= 1) return;
-    if (m <= static_cast<uint64_t>(TILE)) {
+  // The sorted keys end in P, or with into_buf in Bb (and Bb's old contents
+  // in P).
+  void mergesort(uint64_t P, uint64_t m, uint64_t Bb, bool into_buf = false) {
+    if (m == 0 || (m == 1 && !into_buf)) return;
+    if (m <= static_cast<uint64_t>(TILE) && !into_buf) {
       leaf(P, m, false, 0);
       return;
     }
     const uint64_t leaves = (m + TILE - 1) / TILE;
     int levels = 0;
     while ((1ull << levels) < leaves) ++levels;
-    const bool to_buf = (levels & 1) != 0;
+    // each level moves the runs to the other region
+    const bool to_buf = ((levels & 1) != 0) != into_buf;
     leaf(P, m, to_buf, Bb);
     uint64_t X = to_buf ? Bb : P, Y = to_buf ? P : Bb;
     constexpr uint64_t MT = MergeCfg<K, HV>::MT;
@@ -237,6 +251,32 @@ class Sorter {
       launched(2);
       std::swap(X, Y);
     }
+  }
+
+  // Fig. 3 "out" with its half-size buffer: sorts P[0, m) using the
+  // ceil(m/2) slots Bb[0, ceil(m/2)) (disjoint from the part).  The second
+  // half is sorted into the buffer, the first half into the tail of the
+  // part, then the overlapped merge fills the part; the buffer's elements
+  // end, permuted, in Bb.
+  void out_half(uint64_t P, uint64_t m, uint64_t Bb) {
+    if (m <= 1) return;
+    const uint64_t q = m / 2, r = m - q;
+    mergesort(P + q, r, Bb, true);
+    mergesort(P, q, P + r, true);
+    constexpr uint64_t MT = MergeCfg<K, HV>::MT;
+    const uint64_t mtiles = (m + MT - 1) / MT;
+    prof_.begin(st_);
+    k_ovl_split<K, HV, CNT><<<grid_of((mtiles + 255) / 256), 256, 0, st_>>>(
+        keys_, Bb, r, P, q, xf_, ws_.splits, ws_.flags, ws_.desc);
+    // wait ranges in the exchange start tables (unused outside partitions)
+    k_ovl_deps<K, HV><<<grid_of((mtiles + 255) / 256), 256, 0, st_>>>(r, q, ws_.splits, ws_.wtl,
+                                                                      ws_.wtr);
+    prof_.end(st_, QMS_K_MERGE_SPLIT, 0);
+    prof_.begin(st_);
+    k_ovl_merge<K, HV, CNT><<<grid_of(mtiles), MBT, 0, st_>>>(
+        keys_, vals_, Bb, r, P, q, ws_.splits, ws_.wtl, ws_.wtr, ws_.flags, xf_, ws_.desc);
+    prof_.end(st_, QMS_K_MERGE, 4 * m * ES);
+    launched(3);
   }
 
   // Parks a pivot of [b, e) at e - 1 (rule: QMS_PIVOT_*, MOM for HYBRID's
@@ -325,7 +365,7 @@ class Sorter {
     ck(cudaMemcpyAsync(&h.tie, &ws_.desc->tie, 2 * sizeof(unsigned), cudaMemcpyDeviceToHost, st_));
     ck(cudaStreamSynchronize(st_));
     ck(cudaGetLastError());
-    if (h.err) throw Err{QMS_EINTERNAL};
+    if (h.err) throw Err{err_code(h.err)};
     if (tie) *tie = h.tie;
     exchanged_bytes += (n > 0) ? 4 * h.mis * ES : 0;
     return h.L;
@@ -357,10 +397,14 @@ class Sorter {
       }
       const uint64_t rb = k + 1 + eq;
       const uint64_t nl = k - b, nr = e - rb;
-      // Two-way split: Fig. 3 rule (Mergesort the left side iff the pivot is
-      // left of the integer midpoint).  Three-way split: the smaller side.
-      const bool left = (eq == 0) ? (k < b + nn / 2) : (nl <= nr);
-      if (left) {
+      const int side = choose_side(b, e, k, eq, fig3_side);
+      if (side == SIDE_LARGER_LEFT) {
+        out_half(b, nl, rb);
+        b = rb;
+      } else if (side == SIDE_LARGER_RIGHT) {
+        out_half(rb, nr, b);
+        e = k;
+      } else if (side == SIDE_LEFT) {
         mergesort(b, nl, rb);
         b = rb;
       } else {
@@ -490,19 +534,27 @@ class GraphRunner {
     const unsigned g_exch = static_cast<unsigned>(sms) * 4;
     const unsigned g_split = static_cast<unsigned>(sms) * 4;
     const unsigned g_merge = occ(reinterpret_cast<const void*>(k_g_merge<K, HV, CNT>), MBT, 0) * 2;
+    // Tiles are handed out through a ticket: with device-sized grids one
+    // block per tile, else one wave of blocks that loop.
+    const unsigned g_omerge =
+        dyn ? (1u << 30) : occ(reinterpret_cast<const void*>(k_g_ovl_merge<K, HV, CNT>), MBT, 0);
     const unsigned g_mom = static_cast<unsigned>(sms) * 8;
 
     cudaGraph_t g = nullptr;
     ck(cudaGraphCreate(&g, 0));
-    cudaGraphConditionalHandle h_round, h_pass2, h_level;
+    cudaGraphConditionalHandle h_round, h_pass2, h_level, h_phase, h_ovl;
     ck(cudaGraphConditionalHandleCreate(&h_round, g, 1, cudaGraphCondAssignDefault));
     ck(cudaGraphConditionalHandleCreate(&h_pass2, g, 0, cudaGraphCondAssignDefault));
     ck(cudaGraphConditionalHandleCreate(&h_level, g, 0, cudaGraphCondAssignDefault));
+    ck(cudaGraphConditionalHandleCreate(&h_phase, g, 0, cudaGraphCondAssignDefault));
+    ck(cudaGraphConditionalHandleCreate(&h_ovl, g, 0, cudaGraphCondAssignDefault));
     DState* S = gi->d_state;
     void* a_s[] = {&S};
     void* a_round[] = {&S, &h_round};
     void* a_pass2[] = {&S, &h_pass2};
     void* a_level[] = {&S, &h_level};
+    void* a_side[] = {&S, &h_level, &h_phase, &h_ovl};
+    void* a_phase[] = {&S, &h_phase, &h_level};
     cudaGraph_t body = nullptr;
     cudaGraphNode_t w_round = add_cond(g, nullptr, h_round, cudaGraphCondTypeWhile, &body);
     cudaGraphNode_t n = add_kernel(body, nullptr, reinterpret_cast<const void*>(k_g_begin<K, HV, CNT>),
@@ -529,6 +581,8 @@ class GraphRunner {
     gi->gcap[DN_LEAF] = g_leaf;
     gi->gcap[DN_SPLIT] = g_split;
     gi->gcap[DN_MERGE] = g_merge;
+    gi->gcap[DN_OSPLIT] = gi->gcap[DN_ODEPS] = g_split;
+    gi->gcap[DN_OMERGE] = g_omerge;
     const unsigned g_scan = 1024;  // at most 1024 chunks
     gi->gcap[DN_CHUNK1] = gi->gcap[DN_PREF1] = gi->gcap[DN_CHUNK2] = gi->gcap[DN_PREF2] = g_scan;
     auto add_pass = [&](cudaGraph_t gr, cudaGraphNode_t d, int ip, int ie) {
@@ -549,22 +603,45 @@ class GraphRunner {
     cudaGraph_t p2 = nullptr;
     n = add_cond(body, n, h_pass2, cudaGraphCondTypeIf, &p2);
     add_pass(p2, nullptr, DN_PART2, DN_EXCH2);
-    n = add_kernel(body, n, reinterpret_cast<const void*>(k_g_side<K, HV>), 1, 32, 0, a_level);
-    n = add_kernel(body, n, reinterpret_cast<const void*>(k_g_leaf<K, HV, CNT>), g_leaf, NT, tsm, a_s,
-                   dn ? dn + DN_LEAF : nullptr);
-    cudaGraph_t lv = nullptr;
-    n = add_cond(body, n, h_level, cudaGraphCondTypeWhile, &lv);
+    n = add_kernel(body, n, reinterpret_cast<const void*>(k_g_side<K, HV>), 1, 32, 0, a_side);
+    // Mergesort phases: one (Fig. 3 rule) or two (half-buffer rounds)
+    cudaGraph_t ph = nullptr;
+    n = add_cond(body, n, h_phase, cudaGraphCondTypeWhile, &ph);
     {
-      cudaGraphNode_t q = add_kernel(lv, nullptr, reinterpret_cast<const void*>(k_g_split<K, HV, CNT>),
-                                     g_split, 256, 0, a_s, dn ? dn + DN_SPLIT : nullptr);
-      q = add_kernel(lv, q, reinterpret_cast<const void*>(k_g_merge<K, HV, CNT>), g_merge, MBT, 0, a_s,
-                     dn ? dn + DN_MERGE : nullptr);
-      add_kernel(lv, q, reinterpret_cast<const void*>(k_g_level_end), 1, 32, 0, a_level);
+      cudaGraphNode_t p = add_kernel(ph, nullptr, reinterpret_cast<const void*>(k_g_leaf<K, HV, CNT>),
+                                     g_leaf, NT, tsm, a_s, dn ? dn + DN_LEAF : nullptr);
+      cudaGraph_t lv = nullptr;
+      p = add_cond(ph, p, h_level, cudaGraphCondTypeWhile, &lv);
+      {
+        cudaGraphNode_t q = add_kernel(lv, nullptr, reinterpret_cast<const void*>(k_g_split<K, HV, CNT>),
+                                       g_split, 256, 0, a_s, dn ? dn + DN_SPLIT : nullptr);
+        q = add_kernel(lv, q, reinterpret_cast<const void*>(k_g_merge<K, HV, CNT>), g_merge, MBT, 0,
+                       a_s, dn ? dn + DN_MERGE : nullptr);
+        add_kernel(lv, q, reinterpret_cast<const void*>(k_g_level_end), 1, 32, 0, a_level);
+      }
+      add_kernel(ph, p, reinterpret_cast<const void*>(k_g_phase_end<K, HV>), 1, 32, 0, a_phase);
+    }
+    // the overlapped final merge of half-buffer rounds
+    cudaGraph_t ov = nullptr;
+    n = add_cond(body, n, h_ovl, cudaGraphCondTypeIf, &ov);
+    {
+      cudaGraphNode_t q = add_kernel(ov, nullptr, reinterpret_cast<const void*>(k_g_ovl_split<K, HV, CNT>),
+                                     g_split, 256, 0, a_s, dn ? dn + DN_OSPLIT : nullptr);
+      q = add_kernel(ov, q, reinterpret_cast<const void*>(k_g_ovl_deps<K, HV>), g_split, 256, 0, a_s,
+                     dn ? dn + DN_ODEPS : nullptr);
+      add_kernel(ov, q, reinterpret_cast<const void*>(k_g_ovl_merge<K, HV, CNT>), g_omerge, MBT, 0, a_s,
+                 dn ? dn + DN_OMERGE : nullptr);
     }
     add_kernel(body, n, reinterpret_cast<const void*>(k_g_end), 1, 32, 0, a_round);
     add_kernel(g, w_round, reinterpret_cast<const void*>(k_g_final<K, HV, CNT>), 1, NT, tsm, a_s);
     bool all = dyn;
     for (int i = 0; i < DN_COUNT && dyn; ++i) all = all && gi->dn[i] != nullptr;
+    if (dyn && !all) {  // some node is not device-updatable: fixed grids throughout
+      cudaGraphDestroy(g);
+      for (int i = 0; i < DN_COUNT; ++i) gi->dn[i] = nullptr;
+      build_impl(gi, pivot, false);
+      return;
+    }
     gi->dyn = all ? 1u : 0u;
     if (cudaGraphInstantiate(&gi->exec, g, 0) != cudaSuccess) {
       (void)cudaGetLastError();
@@ -637,8 +714,8 @@ class GraphRunner {
   }
 
   // Enqueues the sort of keys[0, n) on st; with stats, waits and fills them.
-  static int run(K* keys, uint32_t* vals, uint64_t n, int dtype, int pivot, cudaStream_t st,
-                 qms_stats* stats) {
+  static int run(K* keys, uint32_t* vals, uint64_t n, int dtype, int pivot, bool fig3,
+                 cudaStream_t st, qms_stats* stats) {
     const auto t0 = std::chrono::steady_clock::now();
     GraphInst* gi = acquire(n, pivot);
     struct Rel {
@@ -660,6 +737,8 @@ class GraphRunner {
     h.pml = reinterpret_cast<unsigned long long*>(w + wl.pml);
     h.pmr = reinterpret_cast<unsigned long long*>(w + wl.pmr);
     h.splits = reinterpret_cast<unsigned long long*>(w + wl.splits);
+    h.flags = reinterpret_cast<unsigned*>(w + wl.flags);
+    h.fig3 = fig3 ? 1 : 0;
     h.wtl = reinterpret_cast<uint32_t*>(w + wl.wtl);
     h.wtr = reinterpret_cast<uint32_t*>(w + wl.wtr);
     h.b = 0;
@@ -681,7 +760,7 @@ class GraphRunner {
       ck(cudaEventRecord(gi->done, st));
       ck(cudaStreamSynchronize(st));
       ck(cudaGetLastError());
-      if (err) throw Err{QMS_EINTERNAL};
+      if (err) throw Err{err_code(err)};
       stats->comparisons = cmp;
       stats->aux_bytes = gi->ws_bytes;
       stats->rounds = gi->h_state->rounds;
@@ -716,10 +795,13 @@ int run_typed(const Args& a, qms_stats* stats, Fn&& fn) {
   Sorter<K, HV, CNT> s(static_cast<K*>(a.keys), a.vals, xform_of(a.dtype), a.st, ws, prof);
   fn(s);
   unsigned long long cmp = 0;
+  unsigned err = 0;
   if (CNT) ck(cudaMemcpyAsync(&cmp, &ws.desc->cmp, sizeof(cmp), cudaMemcpyDeviceToHost, a.st));
+  ck(cudaMemcpyAsync(&err, &ws.desc->err, sizeof(err), cudaMemcpyDeviceToHost, a.st));
   ck(cudaStreamSynchronize(a.st));
   ck(cudaGetLastError());
   prof.flush();
+  if (err) throw Err{err_code(err)};
   if (a.prof) a.prof->bytes[QMS_K_PART_EXCHANGE] += s.exchanged_bytes;
   if (stats) {
     stats->comparisons = cmp;
@@ -895,7 +977,7 @@ constexpr size_t kNoallocBytes = WsLayout(kNoallocMaxN).total;
 }  // namespace
 }  // namespace qms
 
-// Scratch of qms_sort_noalloc (about 840 KB).  Every GPU that loads this
+// Scratch of qms_sort_noalloc (about 900 KB).  Every GPU that loads this
 // library holds it until the process exits.  All calls share it.
 static __device__ __align__(256) unsigned char qms_noalloc_scratch[qms::kNoallocBytes];
 
@@ -943,9 +1025,12 @@ int run_noalloc(void* keys, uint64_t n, int dtype, int pivot, cudaStream_t st,
   Sorter<K, false, CNT> s(static_cast<K*>(keys), nullptr, xform_of(dtype), st, ws, prof);
   s.sort(n, pivot);
   unsigned long long cmp = 0;
+  unsigned err = 0;
   if (CNT) ck(cudaMemcpyAsync(&cmp, &ws.desc->cmp, sizeof(cmp), cudaMemcpyDeviceToHost, st));
+  ck(cudaMemcpyAsync(&err, &ws.desc->err, sizeof(err), cudaMemcpyDeviceToHost, st));
   ck(cudaStreamSynchronize(st));
   ck(cudaGetLastError());
+  if (err) return err_code(err);
   if (stats) {
     stats->comparisons = cmp;
     stats->aux_bytes = kNoallocBytes;
@@ -992,14 +1077,20 @@ static int sort_common(void* d_keys, uint32_t* d_vals, size_t n, int dtype, cons
   Args a{d_keys, d_vals, n, dtype, pivot, opt && opt->count_cmps, static_cast<cudaStream_t>(stream),
          opt ? opt->profile : nullptr};
   const bool host_driven = (opt && (opt->profile || (opt->flags & QMS_FLAG_HOST_DRIVEN)));
-  if (host_driven) return dispatch(a, stats, [&](auto& s) { s.sort(n, pivot); });
+  const bool fig3 = !(opt && (opt->flags & QMS_FLAG_LARGER_SIDE));
+  if (host_driven)
+    return dispatch(a, stats, [&](auto& s) {
+      s.fig3_side = fig3;
+      s.sort(n, pivot);
+    });
   qms_stats local{};
   qms_stats* st = stats ? stats : ((opt && (opt->flags & QMS_FLAG_ASYNC)) ? nullptr : &local);
   try {
     const bool u64 = (dtype == QMS_U64 || dtype == QMS_I64);
     const bool hv = d_vals != nullptr, cnt = a.count;
     const cudaStream_t s = a.st;
-#define QMS_G(K, H, C) GraphRunner<K, H, C>::run(static_cast<K*>(d_keys), d_vals, n, dtype, pivot, s, st)
+#define QMS_G(K, H, C) \
+  GraphRunner<K, H, C>::run(static_cast<K*>(d_keys), d_vals, n, dtype, pivot, fig3, s, st)
     if (u64) {
       if (hv) return cnt ? QMS_G(uint64_t, true, true) : QMS_G(uint64_t, true, false);
       return cnt ? QMS_G(uint64_t, false, true) : QMS_G(uint64_t, false, false);
@@ -1053,6 +1144,15 @@ int qms_mergesort(void* d_keys, uint32_t* d_vals, size_t m, size_t buf, int dtyp
   if (m <= 1) return QMS_OK;
   Args a{d_keys, d_vals, buf + m, dtype, 0, false, static_cast<cudaStream_t>(stream), nullptr};
   return dispatch(a, nullptr, [&](auto& s) { s.mergesort(0, m, buf); });
+}
+
+int qms_mergesort_half(void* d_keys, uint32_t* d_vals, size_t m, size_t buf, int dtype,
+                       void* stream) {
+  if (!valid_dtype(dtype) || (m > 1 && d_keys == nullptr) || buf < m) return QMS_EINVAL;
+  if (m <= 1) return QMS_OK;
+  Args a{d_keys, d_vals, buf + (m - m / 2), dtype, 0, false, static_cast<cudaStream_t>(stream),
+         nullptr};
+  return dispatch(a, nullptr, [&](auto& s) { s.out_half(0, m, buf); });
 }
 
 int qms_sort_noalloc(void* d_keys, size_t n, int dtype, const qms_options* opt, void* stream,

@@ -41,73 +41,23 @@ struct MGeom {
   }
 };
 
-// One output tile per block.  Element i of the tile (i = j*MBT + thread) is
-// loaded from the A/B slices and from the buffer tile by the same thread,
-// which then stores its buffer value into that X slot: the tile's consumed
-// slots receive exactly its buffer elements.
-//
-// Shared-memory indices carry one padding element per 128 bytes.  For the
-// striped element i = j*MBT + thread that is j*(MBT + MBT/PE) + pad(thread),
-// and for the blocked element d + j (d = thread*VM, a multiple of VM, and
-// PE a multiple of 2*VM) it is pad(d) + j: both a per-thread base plus a
-// compile-time offset.
+// Merges the tile staged in shared memory (A at logical [0, na), B at
+// [na, cnt), encoded keys) and writes the cnt outputs, decoded, to gy/gyv.
+// Call after a __syncthreads that made the staged tile visible.  Thread
+// produces outputs [d, d + VM).
 template <class K, bool HV, bool CNT>
-__device__ __forceinline__ void merge_level_tile_impl(K* keys, uint32_t* vals,
-                                                      const MGeom<MergeCfg<K, HV>::MT>& gm,
-                                                      uint64_t a_lo, uint64_t a_hi, K* gy,
-                                                      uint32_t* gyv, uint64_t X, int xf, Desc* desc,
-                                                      K* sin, K* sout, uint32_t* svin,
-                                                      uint32_t* svout) {
+__device__ __forceinline__ void merge_staged_out(const K* sin, K* sout, const uint32_t* svin,
+                                                 uint32_t* svout, int na, int cnt, K* gy,
+                                                 uint32_t* gyv, int xf, uint64_t& cmp) {
   using C = MergeCfg<K, HV>;
-  constexpr int VM = C::VM, MT = C::MT;
-  constexpr int PE = 128 / static_cast<int>(sizeof(K));  // keys per padded row
-  static_assert(PE % (2 * VM) == 0 || VM % PE == 0, "blocked rows must not straddle padding");
-  constexpr int SK = MBT + MBT / PE;  // padded stride of one striped row of keys
+  constexpr int VM = C::VM;
+  constexpr int PE = 128 / static_cast<int>(sizeof(K));
+  constexpr int SK = MBT + MBT / PE;
   constexpr int SV = MBT + MBT / 32;
-  uint64_t cmp = 0;
   const int tid = threadIdx.x;
-  const int cnt = static_cast<int>(gm.d1 - gm.d0);
-  const int na = static_cast<int>(a_hi - a_lo), nb = cnt - na;
-  const uint64_t b_lo = gm.d0 - a_lo;
-  // element i < na comes from A[a_lo + i], element i >= na from B[b_lo + i - na]
-  K* ga = keys + X + gm.pbase + a_lo;
-  K* gb = keys + X + gm.pbase + gm.la + b_lo - na;
-  uint32_t* gav = HV ? vals + X + gm.pbase + a_lo : nullptr;
-  uint32_t* gbv = HV ? vals + X + gm.pbase + gm.la + b_lo - na : nullptr;
-  const int ps = tid + tid / PE;  // padded striped base
+  const int nb = cnt - na;
+  const int ps = tid + tid / PE;
   const int pv = tid + tid / 32;
-  K x[VM], y[VM];
-  uint32_t xv[VM], yv[VM];
-#pragma unroll
-  for (int j = 0; j < VM; ++j) {
-    const int i = j * MBT + tid;
-    if (i < cnt) {
-      K* src = (i < na ? ga : gb) + i;
-      x[j] = *src;
-      y[j] = gy[i];
-      if (HV) {
-        xv[j] = (i < na ? gav : gbv)[i];
-        yv[j] = gyv[i];
-      }
-    }
-  }
-  with_xf<K>(xf, [&](auto xc) {
-#pragma unroll
-    for (int j = 0; j < VM; ++j) {
-      const int i = j * MBT + tid;
-      if (i < cnt) {
-        sin[ps + j * SK] = enc_key(x[j], xc);
-        (i < na ? ga : gb)[i] = y[j];
-        if (HV) {
-          svin[pv + j * SV] = xv[j];
-          (i < na ? gav : gbv)[i] = yv[j];
-        }
-      }
-    }
-  });
-  __syncthreads();
-  // Staged layout: A at logical [0, na), B at [na, cnt).  Thread produces
-  // outputs [d, d + VM).
   const int d = tid * VM;
   const int pd = d + d / PE;  // padded blocked base
   const int pdv = d + d / 32;
@@ -151,6 +101,74 @@ __device__ __forceinline__ void merge_level_tile_impl(K* keys, uint32_t* vals,
       }
     }
   });
+}
+
+// One output tile per block.  Element i of the tile (i = j*MBT + thread) is
+// loaded from the A/B slices and from the buffer tile by the same thread,
+// which then stores its buffer value into that X slot: the tile's consumed
+// slots receive exactly its buffer elements.
+//
+// Shared-memory indices carry one padding element per 128 bytes.  For the
+// striped element i = j*MBT + thread that is j*(MBT + MBT/PE) + pad(thread),
+// and for the blocked element d + j (d = thread*VM, a multiple of VM, and
+// PE a multiple of 2*VM) it is pad(d) + j: both a per-thread base plus a
+// compile-time offset.
+template <class K, bool HV, bool CNT>
+__device__ __forceinline__ void merge_level_tile_impl(K* keys, uint32_t* vals,
+                                                      const MGeom<MergeCfg<K, HV>::MT>& gm,
+                                                      uint64_t a_lo, uint64_t a_hi, K* gy,
+                                                      uint32_t* gyv, uint64_t X, int xf, Desc* desc,
+                                                      K* sin, K* sout, uint32_t* svin,
+                                                      uint32_t* svout) {
+  using C = MergeCfg<K, HV>;
+  constexpr int VM = C::VM;
+  constexpr int PE = 128 / static_cast<int>(sizeof(K));  // keys per padded row
+  static_assert(PE % (2 * VM) == 0 || VM % PE == 0, "blocked rows must not straddle padding");
+  constexpr int SK = MBT + MBT / PE;  // padded stride of one striped row of keys
+  constexpr int SV = MBT + MBT / 32;
+  uint64_t cmp = 0;
+  const int tid = threadIdx.x;
+  const int cnt = static_cast<int>(gm.d1 - gm.d0);
+  const int na = static_cast<int>(a_hi - a_lo);
+  const uint64_t b_lo = gm.d0 - a_lo;
+  // element i < na comes from A[a_lo + i], element i >= na from B[b_lo + i - na]
+  K* ga = keys + X + gm.pbase + a_lo;
+  K* gb = keys + X + gm.pbase + gm.la + b_lo - na;
+  uint32_t* gav = HV ? vals + X + gm.pbase + a_lo : nullptr;
+  uint32_t* gbv = HV ? vals + X + gm.pbase + gm.la + b_lo - na : nullptr;
+  const int ps = tid + tid / PE;  // padded striped base
+  const int pv = tid + tid / 32;
+  K x[VM], y[VM];
+  uint32_t xv[VM], yv[VM];
+#pragma unroll
+  for (int j = 0; j < VM; ++j) {
+    const int i = j * MBT + tid;
+    if (i < cnt) {
+      K* src = (i < na ? ga : gb) + i;
+      x[j] = *src;
+      y[j] = gy[i];
+      if (HV) {
+        xv[j] = (i < na ? gav : gbv)[i];
+        yv[j] = gyv[i];
+      }
+    }
+  }
+  with_xf<K>(xf, [&](auto xc) {
+#pragma unroll
+    for (int j = 0; j < VM; ++j) {
+      const int i = j * MBT + tid;
+      if (i < cnt) {
+        sin[ps + j * SK] = enc_key(x[j], xc);
+        (i < na ? ga : gb)[i] = y[j];
+        if (HV) {
+          svin[pv + j * SV] = xv[j];
+          (i < na ? gav : gbv)[i] = yv[j];
+        }
+      }
+    }
+  });
+  __syncthreads();
+  merge_staged_out<K, HV, CNT>(sin, sout, svin, svout, na, cnt, gy, gyv, xf, cmp);
   if (CNT) flush_count(cmp, &desc->cmp);
 }
 
@@ -240,6 +258,312 @@ __global__ void __launch_bounds__(256) k_merge_split3(const K* keys, uint64_t X,
   split_group<K, HV, CNT>(keys, X, m, L, xf, splits,
                           (blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x) >> 5, cmp);
   if (CNT) flush_count(cmp, &desc->cmp);
+}
+
+// ---------------------------------------------------------------------------
+// Overlapped final merge of Fig. 3 "out" (rounds that Mergesort the larger
+// side with a buffer of half its size).
+//
+// A = keys[Ab, Ab + la) (the sorted second half, in the buffer region) and
+// B = keys[Ob + la, Ob + la + lb) (the sorted first half, at the tail of the
+// target) merge into keys[Ob, Ob + m), m = la + lb.  The la slots
+// keys[Ob, Ob + la) hold buffer elements at the start; at the end they are
+// in A's slots.  Output tile t covers target positions [t*MT, t*MT + MT).
+//
+// Slot Ob + p with p >= la holds B[p - la] until that element is consumed,
+// and B[j] is output at a position <= la + j.  So a tile's window holds only
+// buffer elements and its own B elements once every earlier tile that
+// consumed a B element of the window has finished.  Such a tile moves its
+// buffer elements into its own consumed A slots and into its consumed B
+// slots beyond its window (those lie in later windows, whose tiles wait for
+// it).  The counts match exactly: the window holds cnt - (own B elements in
+// the window) buffer elements, and the tile frees na A slots plus
+// nb - (own B elements in the window) B slots beyond the window.
+//
+// Tiles are taken in increasing order from a ticket, and a tile waits only
+// for earlier tiles, which are already running: the waits cannot deadlock.
+// Every wait is bounded; on expiry the tile records the error in the round
+// descriptor, which makes all further waits give up, and goes on (the sort
+// then reports the error).
+
+// Split step: for every output tile the number of A elements before its
+// first output (a warp per 32 tiles, exact anchors at the group's ends, then
+// one binary search per lane inside the window they bound).  Also clears the
+// tiles' completion flags and the ticket.
+template <class K, bool HV, bool CNT>
+__device__ __forceinline__ void ovl_split_group(const K* keys, uint64_t Ab, uint64_t la, uint64_t Ob,
+                                                uint64_t lb, int xf, uint64_t* splits,
+                                                unsigned* flags, uint64_t w, uint64_t& cmp) {
+  constexpr int MT = MergeCfg<K, HV>::MT;
+  const uint64_t m = la + lb;
+  const uint64_t ntiles = (m + MT - 1) / MT;
+  const unsigned lane = threadIdx.x & 31u;
+  const uint64_t t0 = w * 32;
+  if (t0 >= ntiles) return;
+  const K* A = keys + Ab;
+  const K* B = keys + Ob + la;
+  const uint64_t d0 = t0 * MT;
+  const uint64_t te = (t0 + 32 < ntiles) ? t0 + 32 : ntiles;
+  const uint64_t d1 = (te * MT < m) ? te * MT : m;
+  const uint64_t a0 = (d0 == 0) ? 0 : merge_path_warp<K, CNT>(A, la, B, lb, d0, xf, cmp);
+  const uint64_t a1 = (d1 >= m) ? la : merge_path_warp<K, CNT>(A, la, B, lb, d1, xf, cmp);
+  const uint64_t t = t0 + lane;
+  if (t < ntiles) {
+    const uint64_t d = t * MT;
+    uint64_t lo = d > lb ? d - lb : 0, hi = d < la ? d : la;
+    const uint64_t lo2 = (a1 > d1 - d) ? a1 - (d1 - d) : 0;
+    const uint64_t hi2 = a0 + (d - d0);
+    lo = lo > a0 ? lo : a0;
+    lo = lo > lo2 ? lo : lo2;
+    hi = hi < a1 ? hi : a1;
+    hi = hi < hi2 ? hi : hi2;
+    while (lo < hi) {
+      const uint64_t mid = (lo + hi) >> 1;
+      if (CNT) ++cmp;
+      if (!(enc_key(B[d - 1 - mid], xf) < enc_key(A[mid], xf))) lo = mid + 1; else hi = mid;
+    }
+    splits[t] = lo;
+    flags[t] = 0;
+  }
+}
+
+template <class K, bool HV, bool CNT>
+__global__ void __launch_bounds__(256) k_ovl_split(const K* keys, uint64_t Ab, uint64_t la,
+                                                   uint64_t Ob, uint64_t lb, int xf,
+                                                   uint64_t* splits, unsigned* flags, Desc* desc) {
+  uint64_t cmp = 0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) desc->oticket = 0;
+  const uint64_t nw = (static_cast<uint64_t>(gridDim.x) * blockDim.x) >> 5;
+  const uint64_t ngroups = (la + lb + MergeCfg<K, HV>::MT * 32ull - 1) / (MergeCfg<K, HV>::MT * 32ull);
+  for (uint64_t w = (blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x) >> 5; w < ngroups;
+       w += nw)
+    ovl_split_group<K, HV, CNT>(keys, Ab, la, Ob, lb, xf, splits, flags, w, cmp);
+  if (CNT) flush_count(cmp, &desc->cmp);
+}
+
+// Wait ranges: tile t of the overlapped merge must wait for the tiles
+// [dep_lo[t], dep_hi[t]), the earlier tiles that consumed B elements lying
+// in its window.  Window positions p >= la hold B[p - la]; B[j0, j1) are the
+// ones consumed before tile t (j < b_lo(t) = t*MT - splits[t]), and the
+// tiles holding B[j0] and B[j1 - 1] bound the range (b_lo is nondecreasing
+// in the tile).  One thread per tile.
+template <int MT>
+__device__ __forceinline__ void ovl_deps_tile(uint64_t la, uint64_t lb, const uint64_t* splits,
+                                              uint32_t* dep_lo, uint32_t* dep_hi, uint64_t t) {
+  const uint64_t m = la + lb;
+  const uint64_t o0 = t * MT, o1 = (o0 + MT < m) ? o0 + MT : m;
+  const uint64_t b_lo = o0 - splits[t];
+  uint32_t lo_t = 0, hi_t = 0;
+  if (o1 > la) {
+    const uint64_t j0 = (o0 > la ? o0 : la) - la;
+    const uint64_t j1 = (o1 - la < b_lo) ? o1 - la : b_lo;
+    if (j0 < j1) {
+      // last tile u < t with u*MT - splits[u] <= j (tile 0 qualifies)
+      auto holder = [&](uint64_t j) {
+        uint64_t lo = 0, hi = t;
+        while (hi - lo > 1) {
+          const uint64_t mid = (lo + hi) >> 1;
+          if (mid * MT - splits[mid] <= j) lo = mid; else hi = mid;
+        }
+        return lo;
+      };
+      lo_t = static_cast<uint32_t>(holder(j0));
+      hi_t = static_cast<uint32_t>(holder(j1 - 1) + 1);
+    }
+  }
+  dep_lo[t] = lo_t;
+  dep_hi[t] = hi_t;
+}
+
+template <class K, bool HV>
+__global__ void __launch_bounds__(256) k_ovl_deps(uint64_t la, uint64_t lb, const uint64_t* splits,
+                                                  uint32_t* dep_lo, uint32_t* dep_hi) {
+  constexpr int MT = MergeCfg<K, HV>::MT;
+  const uint64_t ntiles = (la + lb + MT - 1) / MT;
+  for (uint64_t t = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; t < ntiles;
+       t += static_cast<uint64_t>(gridDim.x) * blockDim.x)
+    ovl_deps_tile<MT>(la, lb, splits, dep_lo, dep_hi, t);
+}
+
+constexpr unsigned kOvlSpinLimit = 1u << 20;  // polls of one flag (about a second)
+constexpr unsigned kErrOvlWait = 8u;          // Desc::err bit: a wait ran out
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Waits until flags[u] != 0 for every u in [u0, u1) (the block's threads
+// share the flags); false if a wait ran out.  The first wait that runs out
+// sets kErrOvlWait in *err, and every wait, current or later, that sees the
+// bit gives up at once: one stuck tile costs one wait, not one per tile.
+__device__ __forceinline__ bool wait_flags(const unsigned* flags, uint64_t u0, uint64_t u1,
+                                           unsigned* err) {
+  bool ok = (ld_acquire_u32(err) & kErrOvlWait) == 0;
+  for (uint64_t u = u0 + threadIdx.x; u < u1 && ok; u += blockDim.x) {
+    unsigned it = 0;
+    while (ld_acquire_u32(flags + u) == 0) {
+      if ((++it & 255u) == 0 && (ld_acquire_u32(err) & kErrOvlWait) != 0) {
+        ok = false;
+        break;
+      }
+      if (it > kOvlSpinLimit) {
+        atomicOr(err, kErrOvlWait);
+        ok = false;
+        break;
+      }
+      __nanosleep(100);
+    }
+  }
+  return __syncthreads_and(ok) != 0;
+}
+
+// One output tile of the overlapped merge; returns false if a wait ran out.
+//
+// Element i of the tile (i = j*MBT + thread) is A[a_lo + i] for i < na and
+// B[b_lo + i - na] otherwise.  The first W B elements lie inside the window
+// (their slots get outputs); every other element's slot receives one of the
+// window's G = cnt - W buffer elements: the g-th, with g = i for i < na and
+// g = i - W beyond, where the window's buffer elements are numbered in
+// position order around the W own slots.  The thread that loads element i
+// also moves that buffer element into its slot, so the tile needs no
+// barrier between reading its elements and overwriting their slots.
+template <class K, bool HV, bool CNT>
+__device__ __forceinline__ bool ovl_merge_tile(K* keys, uint32_t* vals, uint64_t Ab, uint64_t la,
+                                               uint64_t Ob, uint64_t lb, const uint64_t* splits,
+                                               const uint32_t* dep_lo, const uint32_t* dep_hi,
+                                               unsigned* flags, unsigned* err, int xf, uint64_t t,
+                                               K* sin, K* sout, uint32_t* svin, uint32_t* svout,
+                                               uint64_t& cmp) {
+  using C = MergeCfg<K, HV>;
+  constexpr int VM = C::VM, MT = C::MT;
+  constexpr int PE = 128 / static_cast<int>(sizeof(K));
+  constexpr int SK = MBT + MBT / PE;
+  constexpr int SV = MBT + MBT / 32;
+  const int tid = threadIdx.x;
+  const uint64_t m = la + lb;
+  const uint64_t o0 = t * MT, o1 = (o0 + MT < m) ? o0 + MT : m;
+  const int cnt = static_cast<int>(o1 - o0);
+  const uint64_t a_lo = splits[t], a_hi = (o1 == m) ? la : splits[t + 1];
+  const uint64_t b_lo = o0 - a_lo, b_hi = o1 - a_hi;
+  const int na = static_cast<int>(a_hi - a_lo);
+  const uint64_t Bs = Ob + la;  // B[j] lives at keys[Bs + j] until consumed
+  // Own B slots, target-relative: [la + b_lo, la + b_hi); la + b_lo >= o0
+  // (an element is output no later than its slot).  Window-relative, the own
+  // slots inside the window are [w_lo, w_lo + W).
+  const uint64_t own_lo = la + b_lo, own_hi = la + b_hi;
+  const int w_lo = static_cast<int>((own_lo < o1 ? own_lo : o1) - o0);
+  const int W = static_cast<int>((own_hi < o1 ? own_hi : o1) - o0) - w_lo;
+  // 1. Wait for the earlier tiles that consumed B elements of the window.
+  bool ok = true;
+  {
+    const uint64_t u0 = dep_lo[t], u1 = dep_hi[t];
+    if (u0 < u1) ok = wait_flags(flags, u0, u1, err);
+  }
+  // 2. Load the tile's elements and the buffer elements bound for their
+  //    slots together.
+  K* ga = keys + Ab + a_lo;
+  K* gb = keys + Bs + b_lo - na;
+  uint32_t* gav = HV ? vals + Ab + a_lo : nullptr;
+  uint32_t* gbv = HV ? vals + Bs + b_lo - na : nullptr;
+  const K* win = keys + Ob + o0;
+  const uint32_t* winv = HV ? vals + Ob + o0 : nullptr;
+  const int ps = tid + tid / PE;
+  const int pv = tid + tid / 32;
+  K x[VM], gk[VM];
+  uint32_t xv[VM], gv[VM];
+#pragma unroll
+  for (int j = 0; j < VM; ++j) {
+    const int i = j * MBT + tid;
+    if (i < cnt) {
+      x[j] = (i < na ? ga : gb)[i];
+      if (HV) xv[j] = (i < na ? gav : gbv)[i];
+      if (i < na || i >= na + W) {
+        const int g = i < na ? i : i - W;
+        const int src = g < w_lo ? g : g + W;
+        gk[j] = __ldcg(win + src);
+        if (HV) gv[j] = __ldcg(winv + src);
+      }
+    }
+  }
+  with_xf<K>(xf, [&](auto xc) {
+#pragma unroll
+    for (int j = 0; j < VM; ++j) {
+      const int i = j * MBT + tid;
+      if (i < cnt) {
+        sin[ps + j * SK] = enc_key(x[j], xc);
+        if (HV) svin[pv + j * SV] = xv[j];
+        if (i < na || i >= na + W) {
+          (i < na ? ga : gb)[i] = gk[j];
+          if (HV) (i < na ? gav : gbv)[i] = gv[j];
+        }
+      }
+    }
+  });
+  __syncthreads();
+  // 3. Merge and write the window (its buffer elements are all read).
+  merge_staged_out<K, HV, CNT>(sin, sout, svin, svout, na, cnt, keys + Ob + o0,
+                               HV ? vals + Ob + o0 : nullptr, xf, cmp);
+  // 4. Publish.  A tile that moved buffer elements into later windows makes
+  //    them visible before its flag; any other tile has nothing a later tile
+  //    reads and only sets the flag.
+  if (static_cast<uint64_t>(W) < b_hi - b_lo) {
+    __syncthreads();
+    if (tid == 0) {
+      __threadfence();
+      st_release_u32(flags + t, 1u);
+    }
+  } else if (tid == 0) {
+    st_release_u32(flags + t, 1u);
+  }
+  return ok;
+}
+
+template <class K, bool HV, bool CNT>
+__device__ __forceinline__ void ovl_merge_loop(K* keys, uint32_t* vals, uint64_t Ab, uint64_t la,
+                                               uint64_t Ob, uint64_t lb, const uint64_t* splits,
+                                               const uint32_t* dep_lo, const uint32_t* dep_hi,
+                                               unsigned* flags, int xf, Desc* desc) {
+  using C = MergeCfg<K, HV>;
+  __shared__ K sin[C::IN_K];
+  __shared__ K sout[C::IN_K];
+  __shared__ uint32_t svin[HV ? C::IN_V : 1];
+  __shared__ uint32_t svout[HV ? C::IN_V : 1];
+  __shared__ unsigned long long ticket;
+  const uint64_t ntiles = (la + lb + C::MT - 1) / C::MT;
+  uint64_t cmp = 0;
+  bool ok = true;
+  // Tickets are taken one tile ahead: the atomic's latency overlaps the
+  // current tile.  A block finishes every tile it took, and waits still
+  // point only to smaller tiles, so this keeps the waits deadlock-free.
+  // With a grid of at least ntiles blocks each block takes one ticket.
+  const bool one = gridDim.x >= ntiles;
+  if (threadIdx.x == 0) ticket = atomicAdd(&desc->oticket, 1ull);
+  __syncthreads();
+  uint64_t t = ticket;
+  while (t < ntiles) {
+    __syncthreads();  // every thread has read the ticket
+    if (!one && threadIdx.x == 0) ticket = atomicAdd(&desc->oticket, 1ull);
+    ok = ovl_merge_tile<K, HV, CNT>(keys, vals, Ab, la, Ob, lb, splits, dep_lo, dep_hi, flags,
+                                    &desc->err, xf, t, sin, sout, svin, svout, cmp) && ok;
+    if (one) break;
+    __syncthreads();
+    t = ticket;
+  }
+  if (!ok && threadIdx.x == 0) atomicOr(&desc->err, kErrOvlWait);
+  if (CNT) flush_count(cmp, &desc->cmp);
+}
+
+template <class K, bool HV, bool CNT>
+__global__ void __launch_bounds__(MBT, MergeCfg<K, HV>::MINB)
+    k_ovl_merge(K* keys, uint32_t* vals, uint64_t Ab, uint64_t la, uint64_t Ob, uint64_t lb,
+                const uint64_t* splits, const uint32_t* dep_lo, const uint32_t* dep_hi,
+                unsigned* flags, int xf, Desc* desc) {
+  ovl_merge_loop<K, HV, CNT>(keys, vals, Ab, la, Ob, lb, splits, dep_lo, dep_hi, flags, xf, desc);
 }
 
 }  // namespace qms

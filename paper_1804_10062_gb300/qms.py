@@ -97,6 +97,7 @@ def lib():
                                       ctypes.POINTER(qms_stats)], i),
                 "qms_partition": ([vp, vp, sz, i, i, vp, u64p, u64p], i),
                 "qms_mergesort": ([vp, vp, sz, sz, i, vp], i),
+                "qms_mergesort_half": ([vp, vp, sz, sz, i, vp], i),
                 "qms_sort_noalloc": ([vp, sz, i, ctypes.POINTER(qms_options), vp,
                                       ctypes.POINTER(qms_stats)], i),
                 "qms_server_create": ([sz, i, i, i, ctypes.POINTER(vp)], i),
@@ -162,6 +163,8 @@ def _raise(rc, what):
 
 QMS_FLAG_ASYNC = 1
 QMS_FLAG_HOST_DRIVEN = 2
+QMS_FLAG_LARGER_SIDE = 4
+SIDES = {"fig3": 0, "larger": QMS_FLAG_LARGER_SIDE}
 
 
 def _options(pivot, count_cmps, profile, flags=0):
@@ -172,15 +175,19 @@ def _options(pivot, count_cmps, profile, flags=0):
 
 
 def qms_sort(keys, pivot: str = "m3", count_cmps: bool = False, stream=None, dtype=None,
-             profile: qms_profile | None = None, host_driven: bool = False, wait: bool = True):
+             profile: qms_profile | None = None, host_driven: bool = False, wait: bool = True,
+             side: str = "fig3"):
     """Sorts ``keys`` in place; returns the qms_stats fields as a dict (or
     None with ``wait=False``: the sort is only enqueued on the stream).
 
     ``profile`` (a qms_profile) accumulates per-kernel device times (this
     runs the rounds from the host); ``host_driven`` selects that driver
-    without profiling."""
+    without profiling.  ``side``: "fig3" (Fig. 3's rule, full-size buffer) or
+    "larger" (Mergesort the larger side with a half-size buffer when it
+    fits)."""
     code = _check_keys(keys, dtype)
-    flags = (QMS_FLAG_HOST_DRIVEN if host_driven else 0) | (0 if wait else QMS_FLAG_ASYNC)
+    flags = ((QMS_FLAG_HOST_DRIVEN if host_driven else 0) | (0 if wait else QMS_FLAG_ASYNC)
+             | SIDES[side])
     opt = _options(pivot, count_cmps, profile, flags)
     st = qms_stats()
     rc = lib().qms_sort(ctypes.c_void_p(keys.data_ptr()), keys.numel(), code, ctypes.byref(opt),
@@ -190,11 +197,13 @@ def qms_sort(keys, pivot: str = "m3", count_cmps: bool = False, stream=None, dty
 
 
 def qms_sort_pairs(keys, vals, pivot: str = "m3", count_cmps: bool = False, stream=None, dtype=None,
-                   profile: qms_profile | None = None, host_driven: bool = False):
+                   profile: qms_profile | None = None, host_driven: bool = False,
+                   side: str = "fig3"):
     """Sorts ``keys`` in place, moving ``vals`` with them; returns stats."""
     code = _check_keys(keys, dtype)
     vp = _check_vals(vals, keys.numel())
-    opt = _options(pivot, count_cmps, profile, QMS_FLAG_HOST_DRIVEN if host_driven else 0)
+    opt = _options(pivot, count_cmps, profile,
+                   (QMS_FLAG_HOST_DRIVEN if host_driven else 0) | SIDES[side])
     st = qms_stats()
     rc = lib().qms_sort_pairs(ctypes.c_void_p(keys.data_ptr()), vp, keys.numel(), code,
                               ctypes.byref(opt), _stream(stream), ctypes.byref(st))
@@ -245,6 +254,17 @@ def qms_mergesort(keys, m: int, buf: int, vals=None, stream=None, dtype=None):
     rc = lib().qms_mergesort(ctypes.c_void_p(keys.data_ptr()), _check_vals(vals, keys.numel()), m,
                              buf, code, _stream(stream))
     _raise(rc, "qms_mergesort")
+
+
+def qms_mergesort_half(keys, m: int, buf: int, vals=None, stream=None, dtype=None):
+    """Sorts keys[0:m] using the ceil(m/2) slots keys[buf:...] as swap buffer
+    (buf >= m): Fig. 3 "out" with its overlapped final merge."""
+    code = _check_keys(keys, dtype)
+    if buf < m or buf + (m - m // 2) > keys.numel():
+        raise ValueError("buffer out of range")
+    rc = lib().qms_mergesort_half(ctypes.c_void_p(keys.data_ptr()), _check_vals(vals, keys.numel()),
+                                  m, buf, code, _stream(stream))
+    _raise(rc, "qms_mergesort_half")
 
 
 QMS_NOALLOC_MAX_N = 1 << 24

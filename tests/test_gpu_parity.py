@@ -141,6 +141,59 @@ def test_mergesort_swap_buffer(q, dtype, m):
     assert k[vo].tobytes() == ko.tobytes()
 
 
+@pytest.mark.parametrize("dtype", ["u32", "u64", "f32", "i64"])
+@pytest.mark.parametrize("m", [2, 3, 100, TILE, TILE + 1, 2 * TILE + 3, 3 * TILE - 5, 8 * TILE,
+                               9 * TILE + 17, 100001, (1 << 20) + 7])
+def test_mergesort_half_buffer(q, dtype, m):
+    """Fig. 3 "out" with its ceil(m/2) buffer (overlapped final merge)."""
+    r = m - m // 2
+    k = _dist_keys("normal" if dtype == "f32" else "uniform", dtype, m + 5 + r, m + 1)
+    v = gen.payload_index(m + 5 + r)
+    d, dv = _dev(k), _dev(v)
+    q.qms_mergesort_half(d, m, m + 5, dv, dtype=dtype)
+    ko, vo = _host(d, dtype), _host(dv, "u32")
+    assert ko[:m].tobytes() == oracle.reference_sorted(k[:m]).tobytes()
+    # every part key travels with its payload
+    assert np.array_equal(np.sort(vo[:m]), np.arange(m, dtype=np.uint32))
+    assert np.array_equal(ko[:m], k[vo[:m]])
+    assert ko[m:m + 5].tobytes() == k[m:m + 5].tobytes()
+    # the buffer keeps its (key, payload) multiset
+    assert np.array_equal(np.sort(vo[m + 5:]), v[m + 5:])
+    assert np.array_equal(ko[m + 5:], k[vo[m + 5:]])
+
+
+@pytest.mark.parametrize("dist", ["sorted", "reverse", "mod16", "organ"])
+@pytest.mark.parametrize("m", [4 * TILE + 1, 300001])
+def test_mergesort_half_vs_oracle_out(q, dist, m):
+    """The same step on inputs whose halves do not interleave (every window
+    of the overlapped merge waits on early tiles, or none does) and with
+    many ties, against the oracle's Fig. 3 "out" on the same array."""
+    r = m - m // 2
+    k = gen.keys(dist, "u32", m + r, 9)
+    ref = k.copy()
+    oracle.out_u32(ref, 0, m, m)
+    d = _dev(k)
+    q.qms_mergesort_half(d, m, m, dtype="u32")
+    ko = _host(d, "u32")
+    assert ko[:m].tobytes() == ref[:m].tobytes()
+    assert np.array_equal(np.sort(ko[m:]), np.sort(ref[m:]))
+
+
+@pytest.mark.parametrize("side", ["larger", "fig3"])
+@pytest.mark.parametrize("host_driven", [False, True])
+@pytest.mark.parametrize("dist", ["uniform", "sorted", "mod16", "killer"])
+def test_sort_side_policies(q, side, host_driven, dist):
+    n = 3 * (1 << 17) + 4321
+    if dist == "killer":
+        k, _ = oracle.adversary_u32(n, "hybrid", "paper")
+    else:
+        k = gen.keys(dist, "u32", n, 21)
+    ref = oracle.reference_sorted(k)
+    d = _dev(k)
+    q.qms_sort(d, pivot="hybrid", dtype="u32", side=side, host_driven=host_driven)
+    assert _host(d, "u32").tobytes() == ref.tobytes()
+
+
 # ---------------------------------------------------------------------------
 # Whole sort against the oracle
 
