@@ -450,6 +450,46 @@ __device__ uint64_t merge_path_warp(const K* A, uint64_t la, const K* B, uint64_
   return lo;
 }
 
+// The same search for two diagonals at once: each half-warp (16 lanes, 16
+// probes per round) searches its own d over its own runs.  Every lane
+// returns its half's answer.
+template <class K, bool CNT>
+__device__ uint64_t merge_path_halfwarp(const K* A, uint64_t la, const K* B, uint64_t lb,
+                                        uint64_t d, int xf, uint64_t& cmp) {
+  const unsigned lane = threadIdx.x & 31u, g = lane & 15u, half = lane >> 4;
+  uint64_t lo = d > lb ? d - lb : 0;
+  uint64_t hi = d < la ? d : la;
+  bool done = !(hi > lo);
+  while (__any_sync(0xffffffffu, !done)) {
+    uint64_t step = 1;
+    bool p = false;
+    if (!done) {
+      const uint64_t span = hi - lo;
+      step = span <= 16u ? 1 : (span + 15u) / 16u;
+      const uint64_t m = lo + static_cast<uint64_t>(g) * step;
+      if (m < hi) {
+        if (CNT) ++cmp;
+        p = !(enc_key(B[d - 1 - m], xf) < enc_key(A[m], xf));
+      }
+    }
+    const int c = __popc((__ballot_sync(0xffffffffu, p) >> (half * 16u)) & 0xffffu);
+    if (!done) {
+      if (step == 1) {
+        lo += static_cast<uint64_t>(c);
+        done = true;
+      } else if (c == 0) {
+        done = true;  // P(lo) fails: the answer is lo
+      } else {
+        const uint64_t nhi = lo + static_cast<uint64_t>(c) * step;
+        lo = lo + static_cast<uint64_t>(c - 1) * step + 1;
+        if (nhi < hi) hi = nhi;
+        done = !(hi > lo);
+      }
+    }
+  }
+  return lo;
+}
+
 // Geometry of output tile t of a level: its run pair and diagonals.
 struct MergeGeom {
   uint64_t pbase, la, lb, d0, d1;

@@ -62,6 +62,10 @@ enum : int { DN_PART1 = 0, DN_EXCH1 = 1, DN_PART2 = 2, DN_EXCH2 = 3, DN_LEAF = 4
              DN_MERGE = 6, DN_CHUNK1 = 7, DN_PREF1 = 8, DN_CHUNK2 = 9, DN_PREF2 = 10,
              DN_OSPLIT = 11, DN_OMERGE = 12, DN_ODEPS = 13, DN_COUNT = 14 };
 
+// Loads a call's state (its parameters travel with the launch, so the host
+// copy may be reused at once).
+__global__ static void k_g_load_state(DState* S, DState v) { *S = v; }
+
 // Sets a work node's grid to cover `units` blocks (at least 1, at most its
 // built-in grid).
 __device__ __forceinline__ void size_node(DState& s, int i, unsigned long long units) {
@@ -417,7 +421,9 @@ __device__ __forceinline__ void setup_phase(DState& s, unsigned ph, cudaGraphCon
   cudaGraphSetConditional(h_level, s.levels > 0 ? 1u : 0u);
 }
 
-template <class K, bool HV>
+// HALF: the graph holds the phase loop and the overlapped merge (handles
+// h_phase and h_ovl); without it every round takes Fig. 3's rule.
+template <class K, bool HV, bool HALF>
 __global__ void k_g_side(DState* S, cudaGraphConditionalHandle h_level,
                          cudaGraphConditionalHandle h_phase, cudaGraphConditionalHandle h_ovl) {
   count_launch(S);
@@ -437,7 +443,7 @@ __global__ void k_g_side(DState* S, cudaGraphConditionalHandle h_level,
     }
     const uint64_t rb = k + 1 + eq;
     const uint64_t nl = k - b, nr = e - rb;
-    const int side = choose_side(b, e, k, eq, s.fig3 != 0);
+    const int side = choose_side(b, e, k, eq, !HALF || s.fig3 != 0);
     s.half = (side == SIDE_LARGER_LEFT || side == SIDE_LARGER_RIGHT) ? 1u : 0u;
     if (side == SIDE_LEFT || side == SIDE_LARGER_LEFT) {
       s.P0 = b;
@@ -461,8 +467,10 @@ __global__ void k_g_side(DState* S, cudaGraphConditionalHandle h_level,
   } else {
     cudaGraphSetConditional(h_level, 0u);
   }
-  cudaGraphSetConditional(h_phase, s.active ? 1u : 0u);
-  cudaGraphSetConditional(h_ovl, s.active && s.half ? 1u : 0u);
+  if (HALF) {
+    cudaGraphSetConditional(h_phase, s.active ? 1u : 0u);
+    cudaGraphSetConditional(h_ovl, s.active && s.half ? 1u : 0u);
+  }
 }
 
 // After a Mergesort phase: the next phase of a half-buffer round, or done.

@@ -446,18 +446,20 @@ struct GraphInst {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   DState* d_state = nullptr;
-  DState* h_state = nullptr;  // pinned staging copy
+  DState* h_state = nullptr;  // pinned copy read back for the statistics
   unsigned char* ws = nullptr;
   uint64_t cap = 0;
   size_t ws_bytes = 0;
-  cudaEvent_t done = nullptr;
-  bool busy = false;
+  cudaEvent_t done = nullptr;    // recorded after the instance's last launch
+  cudaStream_t last = nullptr;   // stream of that launch
+  bool used = false;             // launched at least once
+  bool busy = false;             // a call is setting it up on the host
 };
 
 inline size_t graph_ws_bytes(uint64_t cap) { return WsLayout(cap).total; }
 
 std::mutex g_graph_mu;
-std::map<std::tuple<int, int, int, int, int>, std::vector<GraphInst*>> g_graphs;
+std::map<std::tuple<int, int, int, int, int, int>, std::vector<GraphInst*>> g_graphs;
 
 cudaGraphNode_t add_kernel(cudaGraph_t g, cudaGraphNode_t dep, const void* func, unsigned grid,
                            unsigned block, size_t smem, void** args,
@@ -506,11 +508,14 @@ class GraphRunner {
  public:
   // Builds the graph of one instance (kernel arguments: the instance's
   // device state and the three condition handles).
-  static void build(GraphInst* gi, int pivot) {
-    build_impl(gi, pivot, true);
+  static void build(GraphInst* gi, int pivot, bool half) {
+    build_impl(gi, pivot, true, half);
   }
 
-  static void build_impl(GraphInst* gi, int pivot, bool dyn) {
+  // half: the round body also holds the larger-side machinery (two Mergesort
+  // phases and the overlapped merge); without it a round runs Fig. 3's rule
+  // with no extra conditional nodes.
+  static void build_impl(GraphInst* gi, int pivot, bool dyn, bool half) {
     int dev = 0, sms = 0;
     ck(cudaGetDevice(&dev));
     ck(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -542,12 +547,14 @@ class GraphRunner {
 
     cudaGraph_t g = nullptr;
     ck(cudaGraphCreate(&g, 0));
-    cudaGraphConditionalHandle h_round, h_pass2, h_level, h_phase, h_ovl;
+    cudaGraphConditionalHandle h_round, h_pass2, h_level, h_phase = 0, h_ovl = 0;
     ck(cudaGraphConditionalHandleCreate(&h_round, g, 1, cudaGraphCondAssignDefault));
     ck(cudaGraphConditionalHandleCreate(&h_pass2, g, 0, cudaGraphCondAssignDefault));
     ck(cudaGraphConditionalHandleCreate(&h_level, g, 0, cudaGraphCondAssignDefault));
-    ck(cudaGraphConditionalHandleCreate(&h_phase, g, 0, cudaGraphCondAssignDefault));
-    ck(cudaGraphConditionalHandleCreate(&h_ovl, g, 0, cudaGraphCondAssignDefault));
+    if (half) {
+      ck(cudaGraphConditionalHandleCreate(&h_phase, g, 0, cudaGraphCondAssignDefault));
+      ck(cudaGraphConditionalHandleCreate(&h_ovl, g, 0, cudaGraphCondAssignDefault));
+    }
     DState* S = gi->d_state;
     void* a_s[] = {&S};
     void* a_round[] = {&S, &h_round};
@@ -603,28 +610,31 @@ class GraphRunner {
     cudaGraph_t p2 = nullptr;
     n = add_cond(body, n, h_pass2, cudaGraphCondTypeIf, &p2);
     add_pass(p2, nullptr, DN_PART2, DN_EXCH2);
-    n = add_kernel(body, n, reinterpret_cast<const void*>(k_g_side<K, HV>), 1, 32, 0, a_side);
-    // Mergesort phases: one (Fig. 3 rule) or two (half-buffer rounds)
-    cudaGraph_t ph = nullptr;
-    n = add_cond(body, n, h_phase, cudaGraphCondTypeWhile, &ph);
-    {
-      cudaGraphNode_t p = add_kernel(ph, nullptr, reinterpret_cast<const void*>(k_g_leaf<K, HV, CNT>),
-                                     g_leaf, NT, tsm, a_s, dn ? dn + DN_LEAF : nullptr);
+    auto add_levels = [&](cudaGraph_t gr, cudaGraphNode_t d) {
+      d = add_kernel(gr, d, reinterpret_cast<const void*>(k_g_leaf<K, HV, CNT>), g_leaf, NT, tsm, a_s,
+                     dn ? dn + DN_LEAF : nullptr);
       cudaGraph_t lv = nullptr;
-      p = add_cond(ph, p, h_level, cudaGraphCondTypeWhile, &lv);
-      {
-        cudaGraphNode_t q = add_kernel(lv, nullptr, reinterpret_cast<const void*>(k_g_split<K, HV, CNT>),
-                                       g_split, 256, 0, a_s, dn ? dn + DN_SPLIT : nullptr);
-        q = add_kernel(lv, q, reinterpret_cast<const void*>(k_g_merge<K, HV, CNT>), g_merge, MBT, 0,
-                       a_s, dn ? dn + DN_MERGE : nullptr);
-        add_kernel(lv, q, reinterpret_cast<const void*>(k_g_level_end), 1, 32, 0, a_level);
-      }
+      d = add_cond(gr, d, h_level, cudaGraphCondTypeWhile, &lv);
+      cudaGraphNode_t q = add_kernel(lv, nullptr, reinterpret_cast<const void*>(k_g_split<K, HV, CNT>),
+                                     g_split, 256, 0, a_s, dn ? dn + DN_SPLIT : nullptr);
+      q = add_kernel(lv, q, reinterpret_cast<const void*>(k_g_merge<K, HV, CNT>), g_merge, MBT, 0, a_s,
+                     dn ? dn + DN_MERGE : nullptr);
+      add_kernel(lv, q, reinterpret_cast<const void*>(k_g_level_end), 1, 32, 0, a_level);
+      return d;
+    };
+    if (!half) {
+      n = add_kernel(body, n, reinterpret_cast<const void*>(k_g_side<K, HV, false>), 1, 32, 0, a_side);
+      n = add_levels(body, n);
+    } else {
+      n = add_kernel(body, n, reinterpret_cast<const void*>(k_g_side<K, HV, true>), 1, 32, 0, a_side);
+      // Mergesort phases: one (Fig. 3 rule) or two (half-buffer rounds)
+      cudaGraph_t ph = nullptr;
+      n = add_cond(body, n, h_phase, cudaGraphCondTypeWhile, &ph);
+      cudaGraphNode_t p = add_levels(ph, nullptr);
       add_kernel(ph, p, reinterpret_cast<const void*>(k_g_phase_end<K, HV>), 1, 32, 0, a_phase);
-    }
-    // the overlapped final merge of half-buffer rounds
-    cudaGraph_t ov = nullptr;
-    n = add_cond(body, n, h_ovl, cudaGraphCondTypeIf, &ov);
-    {
+      // the overlapped final merge of half-buffer rounds
+      cudaGraph_t ov = nullptr;
+      n = add_cond(body, n, h_ovl, cudaGraphCondTypeIf, &ov);
       cudaGraphNode_t q = add_kernel(ov, nullptr, reinterpret_cast<const void*>(k_g_ovl_split<K, HV, CNT>),
                                      g_split, 256, 0, a_s, dn ? dn + DN_OSPLIT : nullptr);
       q = add_kernel(ov, q, reinterpret_cast<const void*>(k_g_ovl_deps<K, HV>), g_split, 256, 0, a_s,
@@ -635,11 +645,15 @@ class GraphRunner {
     add_kernel(body, n, reinterpret_cast<const void*>(k_g_end), 1, 32, 0, a_round);
     add_kernel(g, w_round, reinterpret_cast<const void*>(k_g_final<K, HV, CNT>), 1, NT, tsm, a_s);
     bool all = dyn;
-    for (int i = 0; i < DN_COUNT && dyn; ++i) all = all && gi->dn[i] != nullptr;
+    for (int i = 0; i < DN_COUNT && dyn; ++i) {
+      const bool ovl_node = (i == DN_OSPLIT || i == DN_ODEPS || i == DN_OMERGE);
+      if (!half && ovl_node) continue;  // not part of this graph
+      all = all && gi->dn[i] != nullptr;
+    }
     if (dyn && !all) {  // some node is not device-updatable: fixed grids throughout
       cudaGraphDestroy(g);
       for (int i = 0; i < DN_COUNT; ++i) gi->dn[i] = nullptr;
-      build_impl(gi, pivot, false);
+      build_impl(gi, pivot, false, half);
       return;
     }
     gi->dyn = all ? 1u : 0u;
@@ -648,7 +662,7 @@ class GraphRunner {
       cudaGraphDestroy(g);
       if (dyn) {  // device-updatable nodes not accepted here: fixed grids
         for (int i = 0; i < DN_COUNT; ++i) gi->dn[i] = nullptr;
-        build_impl(gi, pivot, false);
+        build_impl(gi, pivot, false, half);
         return;
       }
       throw Err{QMS_ECUDA};
@@ -658,7 +672,7 @@ class GraphRunner {
       cudaGraphExecDestroy(gi->exec);
       cudaGraphDestroy(g);
       for (int i = 0; i < DN_COUNT; ++i) gi->dn[i] = nullptr;
-      build_impl(gi, pivot, false);
+      build_impl(gi, pivot, false, half);
       return;
     }
     gi->graph = g;
@@ -668,31 +682,45 @@ class GraphRunner {
   }
 
   // Takes a free instance able to hold n keys (creating or growing one).
-  static GraphInst* acquire(uint64_t n, int pivot) {
+  // An instance whose last launch went to the same stream can be taken at
+  // once: the stream orders the new launch (and its state load) after the
+  // old one.  Otherwise the last launch must have finished.  The per-thread
+  // default stream is one handle for many streams, so it never counts as the
+  // same stream.
+  static GraphInst* acquire(uint64_t n, int pivot, bool half, cudaStream_t st) {
     int dev = 0;
     ck(cudaGetDevice(&dev));
-    const auto key = std::make_tuple(static_cast<int>(sizeof(K)), HV ? 1 : 0, CNT ? 1 : 0, pivot, dev);
+    const auto key =
+        std::make_tuple(static_cast<int>(sizeof(K)), HV ? 1 : 0, CNT ? 1 : 0, pivot, half ? 1 : 0, dev);
     std::lock_guard<std::mutex> lk(g_graph_mu);
     auto& pool = g_graphs[key];
     GraphInst* gi = nullptr;
+    const bool ordered = st != cudaStreamPerThread;
+    for (GraphInst* c : pool) {  // same stream first
+      if (!c->busy && ordered && c->used && c->last == st) {
+        gi = c;
+        break;
+      }
+    }
     for (GraphInst* c : pool) {
+      if (gi != nullptr) break;
       if (c->busy) continue;
       if (cudaEventQuery(c->done) != cudaSuccess) {
         (void)cudaGetLastError();
         continue;
       }
       gi = c;
-      break;
     }
     if (gi == nullptr) {
       gi = new GraphInst();
       ck(cudaMalloc(reinterpret_cast<void**>(&gi->d_state), sizeof(DState)));
       ck(cudaMallocHost(reinterpret_cast<void**>(&gi->h_state), sizeof(DState)));
       ck(cudaEventCreateWithFlags(&gi->done, cudaEventDisableTiming));
-      build(gi, pivot);
+      build(gi, pivot, half);
       pool.push_back(gi);
     }
     if (gi->cap < n) {
+      if (gi->used) ck(cudaEventSynchronize(gi->done));  // its last launch still uses ws
       if (gi->ws) ck(cudaFree(gi->ws));
       gi->ws = nullptr;
       const uint64_t cap = std::max<uint64_t>(n, 1ull << 20);
@@ -717,14 +745,14 @@ class GraphRunner {
   static int run(K* keys, uint32_t* vals, uint64_t n, int dtype, int pivot, bool fig3,
                  cudaStream_t st, qms_stats* stats) {
     const auto t0 = std::chrono::steady_clock::now();
-    GraphInst* gi = acquire(n, pivot);
+    GraphInst* gi = acquire(n, pivot, !fig3, st);
     struct Rel {
       GraphInst* g;
       ~Rel() { release(g); }
     } rel{gi};
     const uint64_t cap = gi->cap;
     unsigned char* w = gi->ws;
-    DState& h = *gi->h_state;
+    DState h;  // passed by value to the state-load kernel
     std::memset(&h, 0, sizeof(DState));
     h.keys = keys;
     h.vals = vals;
@@ -748,9 +776,11 @@ class GraphRunner {
       h.cap[i] = gi->gcap[i];
     }
     h.dyn = gi->dyn;
-    ck(cudaMemcpyAsync(gi->d_state, &h, sizeof(DState), cudaMemcpyHostToDevice, st));
+    k_g_load_state<<<1, 1, 0, st>>>(gi->d_state, h);
     ck(cudaMemsetAsync(h.desc, 0, sizeof(Desc), st));
     ck(cudaGraphLaunch(gi->exec, st));
+    gi->last = st;
+    gi->used = true;
     if (stats) {
       unsigned long long cmp = 0;
       unsigned err = 0;

@@ -218,14 +218,17 @@ __device__ __forceinline__ void split_group(const K* keys, uint64_t X, uint64_t 
   const bool grouped = 2 * L >= 32ull * MT;  // pairs hold whole groups
   uint64_t a0 = 0, a1 = 0, d0 = 0, d1 = 0;
   if (grouped) {
+    // both ends of the group at once, one per half-warp
     const MGeom<MT> g0(m, L, t0);
     const K* A = keys + X + g0.pbase;
     d0 = g0.d0;
-    a0 = (d0 == 0) ? 0 : merge_path_warp<K, CNT>(A, g0.la, A + g0.la, g0.lb, d0, xf, cmp);
     const uint64_t te = (t0 + 32 < ntiles) ? t0 + 32 : ntiles;
     const uint64_t oe = (te * MT < m) ? te * MT : m;
     d1 = oe - g0.pbase;
-    a1 = (d1 >= g0.la + g0.lb) ? g0.la : merge_path_warp<K, CNT>(A, g0.la, A + g0.la, g0.lb, d1, xf, cmp);
+    const uint64_t r = merge_path_halfwarp<K, CNT>(A, g0.la, A + g0.la, g0.lb, lane < 16 ? d0 : d1,
+                                                   xf, cmp);
+    a0 = __shfl_sync(0xffffffffu, r, 0);
+    a1 = __shfl_sync(0xffffffffu, r, 16);
   }
   const uint64_t t = t0 + lane;
   if (t < ntiles) {
@@ -305,8 +308,9 @@ __device__ __forceinline__ void ovl_split_group(const K* keys, uint64_t Ab, uint
   const uint64_t d0 = t0 * MT;
   const uint64_t te = (t0 + 32 < ntiles) ? t0 + 32 : ntiles;
   const uint64_t d1 = (te * MT < m) ? te * MT : m;
-  const uint64_t a0 = (d0 == 0) ? 0 : merge_path_warp<K, CNT>(A, la, B, lb, d0, xf, cmp);
-  const uint64_t a1 = (d1 >= m) ? la : merge_path_warp<K, CNT>(A, la, B, lb, d1, xf, cmp);
+  const uint64_t r = merge_path_halfwarp<K, CNT>(A, la, B, lb, lane < 16 ? d0 : d1, xf, cmp);
+  const uint64_t a0 = __shfl_sync(0xffffffffu, r, 0);
+  const uint64_t a1 = __shfl_sync(0xffffffffu, r, 16);
   const uint64_t t = t0 + lane;
   if (t < ntiles) {
     const uint64_t d = t * MT;

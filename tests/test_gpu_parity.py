@@ -315,6 +315,22 @@ def test_host_driven_driver_matches_oracle(q, pivot, dtype):
     assert st2["rounds"] >= 1 and st2["launches"] > 0
 
 
+def test_async_sorts_growing_and_two_streams(q):
+    # Back-to-back sorts whose sizes grow (the reused instance's workspace is
+    # replaced while its previous sort may still run) on two streams at once.
+    sizes = [(1 << 18) + 7, (1 << 21) + 3, (1 << 22) + 11, (1 << 19) + 5]
+    arrays = [gen.keys("uniform", "u32", n, 80 + i) for i, n in enumerate(sizes)]
+    ds = [_dev(a) for a in arrays]
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    torch.cuda.synchronize()
+    for i, d in enumerate(ds):
+        s = streams[i % 2]
+        with torch.cuda.stream(s):
+            assert q.qms_sort(d, dtype="u32", wait=False, stream=s) is None
+    for a, d in zip(arrays, ds):
+        assert _host(d, "u32").tobytes() == np.sort(a).tobytes()
+
+
 def test_async_sorts_back_to_back(q):
     # Several device-driven sorts enqueued without host waits on one stream.
     arrays = [gen.keys("uniform", "u32", (1 << 19) + i * 1001, 60 + i) for i in range(4)]
