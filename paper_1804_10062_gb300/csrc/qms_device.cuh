@@ -86,22 +86,25 @@ __device__ __forceinline__ int sk_i(int i) {
 }
 __device__ __forceinline__ int sv_i(int i) { return i + (i >> 5); }
 
-template <class K>
+// Shared-memory tiles hold LT * V keys: LT = NT (8192 keys) everywhere but
+// in the Mergesort leaves of some key types (LeafCfg).
+template <class K, int LT = NT>
 __host__ __device__ constexpr int sk_len() {
-  return TILE + TILE / (128 / static_cast<int>(sizeof(K))) + 4;
+  return LT * V + LT * V / (128 / static_cast<int>(sizeof(K))) + 4;
 }
-__host__ __device__ constexpr int sv_len() { return TILE + TILE / 32 + 4; }
+template <int LT = NT>
+__host__ __device__ constexpr int sv_len() { return LT * V + LT * V / 32 + 4; }
 
 // Scratch words used by block scans and small per-block tables.
 constexpr int SCRATCH_WORDS = 64;
 
-template <class K, bool HV>
+template <class K, bool HV, int LT = NT>
 __host__ __device__ constexpr size_t tile_smem_bytes() {
-  return static_cast<size_t>(sk_len<K>()) * sizeof(K) +
-         (HV ? static_cast<size_t>(sv_len()) * 4 : 0) + SCRATCH_WORDS * 8;
+  return static_cast<size_t>(sk_len<K, LT>()) * sizeof(K) +
+         (HV ? static_cast<size_t>(sv_len<LT>()) * 4 : 0) + SCRATCH_WORDS * 8;
 }
 
-template <class K, bool HV>
+template <class K, bool HV, int LT = NT>
 struct TileSmem {
   K* k;
   uint32_t* v;
@@ -109,12 +112,23 @@ struct TileSmem {
   __device__ __forceinline__ static TileSmem carve(unsigned char* base) {
     TileSmem s;
     s.k = reinterpret_cast<K*>(base);
-    size_t off = static_cast<size_t>(sk_len<K>()) * sizeof(K);
+    size_t off = static_cast<size_t>(sk_len<K, LT>()) * sizeof(K);
     s.v = HV ? reinterpret_cast<uint32_t*>(base + off) : nullptr;
-    if (HV) off += static_cast<size_t>(sv_len()) * 4;
+    if (HV) off += static_cast<size_t>(sv_len<LT>()) * 4;
     s.scratch = reinterpret_cast<uint32_t*>(base + off);
     return s;
   }
+};
+
+// Mergesort leaves: LT threads of V keys each.  4-byte keys without
+// payloads use 16384-key leaves (their tile sort needs 32 registers, so 1024
+// threads fit), which saves one merge level per Mergesort; the others keep
+// 8192.
+template <class K, bool HV>
+struct LeafCfg {
+  static constexpr int LT = (sizeof(K) == 4 && !HV) ? 2 * NT : NT;
+  static constexpr int TILE_L = LT * V;
+  static constexpr int MINB = (LT == 2 * NT) ? 2 : 1;  // resident blocks per SM built for
 };
 
 // ---------------------------------------------------------------------------
@@ -182,23 +196,23 @@ __device__ __forceinline__ void cp_async_wait_all() {
 // ---------------------------------------------------------------------------
 // Tile load / store (striped: item j of thread t is element j*NT + t)
 
-template <class K, bool HV>
-__device__ __forceinline__ void load_tile_enc(TileSmem<K, HV> s, const K* g, const uint32_t* gv,
+template <class K, bool HV, int LT = NT>
+__device__ __forceinline__ void load_tile_enc(TileSmem<K, HV, LT> s, const K* g, const uint32_t* gv,
                                               int cnt, int xf) {
 #pragma unroll 4
   for (int j = 0; j < V; ++j) {
-    const int i = j * NT + threadIdx.x;
+    const int i = j * LT + threadIdx.x;
     s.k[sk_i<K>(i)] = (i < cnt) ? enc_key(g[i], xf) : key_max<K>();
     if (HV) s.v[sv_i(i)] = (i < cnt) ? gv[i] : 0xffffffffu;
   }
 }
 
-template <class K, bool HV>
-__device__ __forceinline__ void store_tile_dec(TileSmem<K, HV> s, K* g, uint32_t* gv, int cnt,
+template <class K, bool HV, int LT = NT>
+__device__ __forceinline__ void store_tile_dec(TileSmem<K, HV, LT> s, K* g, uint32_t* gv, int cnt,
                                                int xf) {
 #pragma unroll
   for (int j = 0; j < V; ++j) {
-    const int i = j * NT + threadIdx.x;
+    const int i = j * LT + threadIdx.x;
     if (i < cnt) {
       g[i] = dec_key(s.k[sk_i<K>(i)], xf);
       if (HV) gv[i] = s.v[sv_i(i)];
@@ -207,10 +221,10 @@ __device__ __forceinline__ void store_tile_dec(TileSmem<K, HV> s, K* g, uint32_t
 }
 
 // Copies cnt elements src -> dst (global to global, no overlap), striped.
-template <class K, bool HV>
+template <class K, bool HV, int LT = NT>
 __device__ __forceinline__ void copy_elems(K* dst, uint32_t* dv, const K* src, const uint32_t* sv,
                                            int cnt) {
-  for (int i = threadIdx.x; i < cnt; i += NT) {
+  for (int i = threadIdx.x; i < cnt; i += LT) {
     dst[i] = src[i];
     if (HV) dv[i] = sv[i];
   }
@@ -318,8 +332,8 @@ __device__ __forceinline__ void net_sort(K (&k)[V], uint32_t (&v)[V]) {
 // 63 comparators for V = 16), then log2(NT) rounds of merge-path merges in
 // shared memory.
 
-template <class K, bool HV, bool CNT>
-__device__ void block_sort_tile(TileSmem<K, HV> s, uint64_t& cmp, int P = NT) {
+template <class K, bool HV, bool CNT, int LT = NT>
+__device__ void block_sort_tile(TileSmem<K, HV, LT> s, uint64_t& cmp, int P = LT) {
   // P (a power of two <= NT): threads holding data; items beyond the data
   // are padding keys, so the first P*V items end up sorted.
   const int tid = threadIdx.x;
@@ -381,26 +395,26 @@ __device__ __forceinline__ int threads_for(int cnt) {
 // are written to buf[0, cnt) and buf's old contents move to g[0, cnt) (the
 // Mergesort leaf "X then swap into the target", Fig. 3 msort); otherwise the
 // tile is sorted in place.
-template <class K, bool HV, bool CNT>
-__device__ __forceinline__ void leaf_sort_tile(TileSmem<K, HV> s, K* g, uint32_t* gv, K* buf, uint32_t* bufv,
+template <class K, bool HV, bool CNT, int LT = NT>
+__device__ __forceinline__ void leaf_sort_tile(TileSmem<K, HV, LT> s, K* g, uint32_t* gv, K* buf, uint32_t* bufv,
                                int cnt, int xf, uint64_t& cmp) {
   const int P = threads_for(cnt);
   __syncthreads();
-  if (P == NT) {
-    load_tile_enc<K, HV>(s, g, gv, cnt, xf);
+  if (P == LT) {
+    load_tile_enc<K, HV, LT>(s, g, gv, cnt, xf);
   } else {
-    for (int i = threadIdx.x; i < P * V; i += NT) {
+    for (int i = threadIdx.x; i < P * V; i += LT) {
       s.k[sk_i<K>(i)] = (i < cnt) ? enc_key(g[i], xf) : key_max<K>();
       if (HV) s.v[sv_i(i)] = (i < cnt) ? gv[i] : 0xffffffffu;
     }
   }
   __syncthreads();
-  if (buf != nullptr) copy_elems<K, HV>(g, gv, buf, bufv, cnt);
-  block_sort_tile<K, HV, CNT>(s, cmp, P);
+  if (buf != nullptr) copy_elems<K, HV, LT>(g, gv, buf, bufv, cnt);
+  block_sort_tile<K, HV, CNT, LT>(s, cmp, P);
   if (buf != nullptr) {
-    store_tile_dec<K, HV>(s, buf, bufv, cnt, xf);
+    store_tile_dec<K, HV, LT>(s, buf, bufv, cnt, xf);
   } else {
-    store_tile_dec<K, HV>(s, g, gv, cnt, xf);
+    store_tile_dec<K, HV, LT>(s, g, gv, cnt, xf);
   }
 }
 

@@ -100,7 +100,7 @@ __global__ void k_g_begin(DState* S, cudaGraphConditionalHandle h_round) {
   count_launch(S);
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   DState& s = *S;
-  if (s.e - s.b <= static_cast<unsigned long long>(TILE)) {
+  if (s.e - s.b <= static_cast<unsigned long long>(LeafCfg<K, HV>::TILE_L)) {
     s.active = 0;
     cudaGraphSetConditional(h_round, 0);
     return;
@@ -405,14 +405,15 @@ __device__ __forceinline__ void setup_phase(DState& s, unsigned ph, cudaGraphCon
     }
   }
   s.phase = ph;
-  const uint64_t leaves = (s.m + TILE - 1) / TILE;
+  constexpr uint64_t TL = LeafCfg<K, HV>::TILE_L;
+  const uint64_t leaves = (s.m + TL - 1) / TL;
   unsigned levels = 0;
   while ((1ull << levels) < leaves) ++levels;
   s.levels = levels;
   s.to_buf = ((levels & 1u) != 0) != into_buf ? 1u : 0u;
   s.X = s.to_buf ? s.Bb : s.P;
   s.Y = s.to_buf ? s.P : s.Bb;
-  s.L = TILE;
+  s.L = TL;
   size_node(s, DN_LEAF, leaves);
   const unsigned long long mt = MergeCfg<K, HV>::MT;
   const unsigned long long mtiles = (s.m + mt - 1) / mt;
@@ -532,23 +533,24 @@ __global__ void __launch_bounds__(MBT, MergeCfg<K, HV>::MINB) k_g_ovl_merge(DSta
 }
 
 template <class K, bool HV, bool CNT>
-__global__ void __launch_bounds__(NT) k_g_leaf(DState* S) {
+__global__ void __launch_bounds__(LeafCfg<K, HV>::LT, LeafCfg<K, HV>::MINB) k_g_leaf(DState* S) {
+  constexpr int LT = LeafCfg<K, HV>::LT, TL = LeafCfg<K, HV>::TILE_L;
   count_launch(S);
   DState& s = *S;
   if (!s.active || s.m <= 1) return;
   extern __shared__ __align__(16) unsigned char smem[];
-  const auto sm = TileSmem<K, HV>::carve(smem);
+  const auto sm = TileSmem<K, HV, LT>::carve(smem);
   uint64_t cmp = 0;
   const uint64_t m = s.m, P = s.P, Bb = s.Bb;
   const bool to_buf = s.to_buf != 0;
   K* keys = static_cast<K*>(s.keys);
-  const uint64_t ntiles = (m + TILE - 1) / TILE;
+  const uint64_t ntiles = (m + TL - 1) / TL;
   for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const uint64_t off = t * TILE;
-    const int cnt = static_cast<int>((m - off) < static_cast<uint64_t>(TILE) ? (m - off) : TILE);
-    leaf_sort_tile<K, HV, CNT>(sm, keys + P + off, HV ? s.vals + P + off : nullptr,
-                               to_buf ? keys + Bb + off : nullptr,
-                               (HV && to_buf) ? s.vals + Bb + off : nullptr, cnt, s.xf, cmp);
+    const uint64_t off = t * TL;
+    const int cnt = static_cast<int>((m - off) < static_cast<uint64_t>(TL) ? (m - off) : TL);
+    leaf_sort_tile<K, HV, CNT, LT>(sm, keys + P + off, HV ? s.vals + P + off : nullptr,
+                                   to_buf ? keys + Bb + off : nullptr,
+                                   (HV && to_buf) ? s.vals + Bb + off : nullptr, cnt, s.xf, cmp);
   }
   if (CNT) flush_count(cmp, &s.desc->cmp);
 }
@@ -593,26 +595,29 @@ __global__ static void k_g_level_end(DState* S, cudaGraphConditionalHandle h_lev
   cudaGraphSetConditional(h_level, s.levels > 0 ? 1u : 0u);
 }
 
-__global__ static void k_g_end(DState* S, cudaGraphConditionalHandle h_round) {
+template <class K, bool HV>
+__global__ void k_g_end(DState* S, cudaGraphConditionalHandle h_round) {
   count_launch(S);
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   DState& s = *S;
-  const bool more = s.active && s.e - s.b > static_cast<unsigned long long>(TILE) && !s.desc->err;
+  const bool more =
+      s.active && s.e - s.b > static_cast<unsigned long long>(LeafCfg<K, HV>::TILE_L) && !s.desc->err;
   cudaGraphSetConditional(h_round, more ? 1u : 0u);
 }
 
 template <class K, bool HV, bool CNT>
-__global__ void __launch_bounds__(NT) k_g_final(DState* S) {
+__global__ void __launch_bounds__(LeafCfg<K, HV>::LT) k_g_final(DState* S) {
+  constexpr int LT = LeafCfg<K, HV>::LT;
   count_launch(S);
   DState& s = *S;
   if (s.desc->err || s.e - s.b <= 1) return;
   extern __shared__ __align__(16) unsigned char smem[];
-  const auto sm = TileSmem<K, HV>::carve(smem);
+  const auto sm = TileSmem<K, HV, LT>::carve(smem);
   uint64_t cmp = 0;
   const uint64_t b = s.b;
   K* keys = static_cast<K*>(s.keys);
-  leaf_sort_tile<K, HV, CNT>(sm, keys + b, HV ? s.vals + b : nullptr, nullptr, nullptr,
-                             static_cast<int>(s.e - b), s.xf, cmp);
+  leaf_sort_tile<K, HV, CNT, LT>(sm, keys + b, HV ? s.vals + b : nullptr, nullptr, nullptr,
+                                 static_cast<int>(s.e - b), s.xf, cmp);
   if (CNT) flush_count(cmp, &s.desc->cmp);
 }
 

@@ -63,20 +63,22 @@ __host__ __device__ inline uint64_t scan_chunk(uint64_t ntiles) {
 // sorted tiles go to the buffer region and the buffer's contents move into P.
 
 template <class K, bool HV, bool CNT>
-__global__ void __launch_bounds__(NT) k_leaf_sort(K* keys, uint32_t* vals, uint64_t P, uint64_t m,
-                                                  uint64_t Bb, int to_buf, int xf, Desc* desc) {
+__global__ void __launch_bounds__(LeafCfg<K, HV>::LT, LeafCfg<K, HV>::MINB) k_leaf_sort(K* keys, uint32_t* vals, uint64_t P,
+                                                                  uint64_t m, uint64_t Bb, int to_buf,
+                                                                  int xf, Desc* desc) {
+  constexpr int LT = LeafCfg<K, HV>::LT, TL = LeafCfg<K, HV>::TILE_L;
   extern __shared__ __align__(16) unsigned char smem[];
-  const auto s = TileSmem<K, HV>::carve(smem);
+  const auto s = TileSmem<K, HV, LT>::carve(smem);
   uint64_t cmp = 0;
-  const uint64_t ntiles = (m + TILE - 1) / TILE;
+  const uint64_t ntiles = (m + TL - 1) / TL;
   for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const uint64_t off = t * TILE;
-    const int cnt = static_cast<int>((m - off) < static_cast<uint64_t>(TILE) ? (m - off) : TILE);
+    const uint64_t off = t * TL;
+    const int cnt = static_cast<int>((m - off) < static_cast<uint64_t>(TL) ? (m - off) : TL);
     K* g = keys + P + off;
     uint32_t* gv = HV ? vals + P + off : nullptr;
     K* b = to_buf ? keys + Bb + off : nullptr;
     uint32_t* bv = (HV && to_buf) ? vals + Bb + off : nullptr;
-    leaf_sort_tile<K, HV, CNT>(s, g, gv, b, bv, cnt, xf, cmp);
+    leaf_sort_tile<K, HV, CNT, LT>(s, g, gv, b, bv, cnt, xf, cmp);
   }
   if (CNT) flush_count(cmp, &desc->cmp);
 }

@@ -195,7 +195,7 @@ class Sorter {
   Sorter(K* keys, uint32_t* vals, int xf, cudaStream_t st, Workspace& ws, Profiler& prof)
       : keys_(keys), vals_(vals), xf_(xf), st_(st), ws_(ws), prof_(prof) {
     static bool a1 = false, a2 = false, a3 = false, a4 = false;
-    allow_smem(k_leaf_sort<K, HV, CNT>, tile_smem_bytes<K, HV>(), a1);
+    allow_smem(k_leaf_sort<K, HV, CNT>, tile_smem_bytes<K, HV, LeafCfg<K, HV>::LT>(), a1);
     (void)a2;
     (void)a3;
     allow_smem(k_pivot_sample<K, HV, CNT>, tile_smem_bytes<K, true>(), a4);
@@ -211,9 +211,10 @@ class Sorter {
 
   void leaf(uint64_t P, uint64_t m, bool to_buf, uint64_t Bb) {
     if (m == 0) return;
-    const uint64_t nt = (m + TILE - 1) / TILE;
+    using LC = LeafCfg<K, HV>;
+    const uint64_t nt = (m + LC::TILE_L - 1) / LC::TILE_L;
     prof_.begin(st_);
-    k_leaf_sort<K, HV, CNT><<<grid_of(nt), NT, tile_smem_bytes<K, HV>(), st_>>>(
+    k_leaf_sort<K, HV, CNT><<<grid_of(nt), LC::LT, tile_smem_bytes<K, HV, LC::LT>(), st_>>>(
         keys_, vals_, P, m, Bb, to_buf ? 1 : 0, xf_, ws_.desc);
     prof_.end(st_, QMS_K_LEAF, (to_buf ? 4 : 2) * m * ES);
     launched();
@@ -225,11 +226,12 @@ class Sorter {
   // in P).
   void mergesort(uint64_t P, uint64_t m, uint64_t Bb, bool into_buf = false) {
     if (m == 0 || (m == 1 && !into_buf)) return;
-    if (m <= static_cast<uint64_t>(TILE) && !into_buf) {
+    constexpr uint64_t TL = LeafCfg<K, HV>::TILE_L;
+    if (m <= TL && !into_buf) {
       leaf(P, m, false, 0);
       return;
     }
-    const uint64_t leaves = (m + TILE - 1) / TILE;
+    const uint64_t leaves = (m + TL - 1) / TL;
     int levels = 0;
     while ((1ull << levels) < leaves) ++levels;
     // each level moves the runs to the other region
@@ -239,7 +241,7 @@ class Sorter {
     constexpr uint64_t MT = MergeCfg<K, HV>::MT;
     const uint64_t mtiles = (m + MT - 1) / MT;
     for (int l = 0; l < levels; ++l) {
-      const uint64_t L = static_cast<uint64_t>(TILE) << l;
+      const uint64_t L = TL << l;
       prof_.begin(st_);
       k_merge_split3<K, HV, CNT><<<grid_of((mtiles + 255) / 256), 256, 0, st_>>>(
           keys_, X, m, L, xf_, ws_.splits, ws_.desc);
@@ -384,7 +386,7 @@ class Sorter {
   void sort(uint64_t n, int rule) {
     uint64_t b = 0, e = n;
     bool mom_next = false;
-    while (e - b > static_cast<uint64_t>(TILE)) {
+    while (e - b > static_cast<uint64_t>(LeafCfg<K, HV>::TILE_L)) {
       ++rounds;
       const uint64_t nn = e - b;
       const bool mom = rule == QMS_PIVOT_MOM || (rule == QMS_PIVOT_HYBRID && mom_next);
@@ -519,13 +521,15 @@ class GraphRunner {
     int dev = 0, sms = 0;
     ck(cudaGetDevice(&dev));
     ck(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    using LC = LeafCfg<K, HV>;
     const size_t tsm = tile_smem_bytes<K, HV>(), tsm_s = tile_smem_bytes<K, true>();
+    const size_t tsm_l = tile_smem_bytes<K, HV, LC::LT>();
     static std::once_flag once;
     std::call_once(once, [&] {
       cudaFuncSetAttribute(reinterpret_cast<const void*>(k_g_leaf<K, HV, CNT>),
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(tsm));
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(tsm_l));
       cudaFuncSetAttribute(reinterpret_cast<const void*>(k_g_final<K, HV, CNT>),
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(tsm));
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(tsm_l));
       cudaFuncSetAttribute(reinterpret_cast<const void*>(k_g_pivot_sample<K, HV, CNT>),
                            cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(tsm_s));
     });
@@ -535,7 +539,7 @@ class GraphRunner {
       return static_cast<unsigned>(sms * std::max(o, 1));
     };
     const unsigned g_part = occ(reinterpret_cast<const void*>(k_g_part_local<K, HV, CNT>), PNT, 0) * 2;
-    const unsigned g_leaf = occ(reinterpret_cast<const void*>(k_g_leaf<K, HV, CNT>), NT, tsm) * 2;
+    const unsigned g_leaf = occ(reinterpret_cast<const void*>(k_g_leaf<K, HV, CNT>), LC::LT, tsm_l) * 2;
     const unsigned g_exch = static_cast<unsigned>(sms) * 4;
     const unsigned g_split = static_cast<unsigned>(sms) * 4;
     const unsigned g_merge = occ(reinterpret_cast<const void*>(k_g_merge<K, HV, CNT>), MBT, 0) * 2;
@@ -611,8 +615,8 @@ class GraphRunner {
     n = add_cond(body, n, h_pass2, cudaGraphCondTypeIf, &p2);
     add_pass(p2, nullptr, DN_PART2, DN_EXCH2);
     auto add_levels = [&](cudaGraph_t gr, cudaGraphNode_t d) {
-      d = add_kernel(gr, d, reinterpret_cast<const void*>(k_g_leaf<K, HV, CNT>), g_leaf, NT, tsm, a_s,
-                     dn ? dn + DN_LEAF : nullptr);
+      d = add_kernel(gr, d, reinterpret_cast<const void*>(k_g_leaf<K, HV, CNT>), g_leaf, LC::LT, tsm_l,
+                     a_s, dn ? dn + DN_LEAF : nullptr);
       cudaGraph_t lv = nullptr;
       d = add_cond(gr, d, h_level, cudaGraphCondTypeWhile, &lv);
       cudaGraphNode_t q = add_kernel(lv, nullptr, reinterpret_cast<const void*>(k_g_split<K, HV, CNT>),
@@ -642,8 +646,8 @@ class GraphRunner {
       add_kernel(ov, q, reinterpret_cast<const void*>(k_g_ovl_merge<K, HV, CNT>), g_omerge, MBT, 0, a_s,
                  dn ? dn + DN_OMERGE : nullptr);
     }
-    add_kernel(body, n, reinterpret_cast<const void*>(k_g_end), 1, 32, 0, a_round);
-    add_kernel(g, w_round, reinterpret_cast<const void*>(k_g_final<K, HV, CNT>), 1, NT, tsm, a_s);
+    add_kernel(body, n, reinterpret_cast<const void*>(k_g_end<K, HV>), 1, 32, 0, a_round);
+    add_kernel(g, w_round, reinterpret_cast<const void*>(k_g_final<K, HV, CNT>), 1, LC::LT, tsm_l, a_s);
     bool all = dyn;
     for (int i = 0; i < DN_COUNT && dyn; ++i) {
       const bool ovl_node = (i == DN_OSPLIT || i == DN_ODEPS || i == DN_OMERGE);
