@@ -311,18 +311,39 @@ template <class K, bool HV, int I = 0>
 __device__ __forceinline__ void net_sort(K (&k)[V], uint32_t (&v)[V]) {
   if constexpr (I < kNet<V>.len) {
     constexpr int a = kNet<V>.c[I].a, b = kNet<V>.c[I].b;
-    const bool sw = k[b] < k[a];
-    const K lo = sw ? k[b] : k[a];
-    const K hi = sw ? k[a] : k[b];
-    k[a] = lo;
-    k[b] = hi;
-    if (HV) {
-      const uint32_t x = sw ? v[b] : v[a];
-      const uint32_t y = sw ? v[a] : v[b];
-      v[a] = x;
-      v[b] = y;
+    if (!HV && sizeof(K) == 4) {
+      const K lo = min(k[a], k[b]);
+      k[b] = max(k[a], k[b]);
+      k[a] = lo;
+    } else {
+      const bool sw = k[b] < k[a];
+      const K lo = sw ? k[b] : k[a];
+      const K hi = sw ? k[a] : k[b];
+      k[a] = lo;
+      k[b] = hi;
+      if (HV) {
+        const uint32_t x = sw ? v[b] : v[a];
+        const uint32_t y = sw ? v[a] : v[b];
+        v[a] = x;
+        v[b] = y;
+      }
     }
     net_sort<K, HV, I + 1>(k, v);
+  }
+}
+
+// Barrier among the threads that share a merge pair of `threads` threads
+// (a power of two) in a tile sort of LT threads: the warp while the pair
+// fits in one, half of a 2*NT-thread block (named barriers 1 and 2) while it
+// fits there, else the block.  Every thread of the block calls it.
+template <int LT>
+__device__ __forceinline__ void tile_sync(int threads) {
+  if (threads <= 32) {
+    __syncwarp();
+  } else if (LT == 2 * NT && threads <= NT) {
+    asm volatile("bar.sync %0, %1;" ::"r"(1 + static_cast<int>(threadIdx.x) / NT), "r"(NT) : "memory");
+  } else {
+    __syncthreads();
   }
 }
 
@@ -334,14 +355,14 @@ __device__ __forceinline__ void net_sort(K (&k)[V], uint32_t (&v)[V]) {
 
 template <class K, bool HV, bool CNT, int LT = NT>
 __device__ void block_sort_tile(TileSmem<K, HV, LT> s, uint64_t& cmp, int P = LT) {
-  // P (a power of two <= NT): threads holding data; items beyond the data
+  // P (a power of two <= LT): threads holding data; items beyond the data
   // are padding keys, so the first P*V items end up sorted.
   const int tid = threadIdx.x;
   K k[V];
   uint32_t v[V];
   int src[V];
   __syncthreads();
-  if (tid < P) {
+  if (tid < P) {  // each thread reads, sorts and writes back its own V keys
 #pragma unroll
     for (int j = 0; j < V; ++j) {
       k[j] = s.k[sk_i<K>(tid * V + j)];
@@ -349,16 +370,13 @@ __device__ void block_sort_tile(TileSmem<K, HV, LT> s, uint64_t& cmp, int P = LT
     }
     net_sort<K, HV>(k, v);
     if (CNT) cmp += kNet<V>.len;
-  }
-  __syncthreads();
-  if (tid < P) {
 #pragma unroll
     for (int j = 0; j < V; ++j) {
       s.k[sk_i<K>(tid * V + j)] = k[j];
       if (HV) s.v[sv_i(tid * V + j)] = v[j];
     }
   }
-  __syncthreads();
+  tile_sync<LT>(2);
   for (int sp = 1; sp < P; sp <<= 1) {
     const int L = sp * V;
     const int g = tid / (2 * sp), r = tid - g * 2 * sp;
@@ -372,7 +390,7 @@ __device__ void block_sort_tile(TileSmem<K, HV, LT> s, uint64_t& cmp, int P = LT
         for (int j = 0; j < V; ++j) v[j] = s.v[sv_i(src[j])];
       }
     }
-    __syncthreads();
+    tile_sync<LT>(2 * sp);  // the pair's reads are done before its writes
     if (tid < P) {
 #pragma unroll
       for (int j = 0; j < V; ++j) {
@@ -380,8 +398,9 @@ __device__ void block_sort_tile(TileSmem<K, HV, LT> s, uint64_t& cmp, int P = LT
         if (HV) s.v[sv_i(a0 + d + j)] = v[j];
       }
     }
-    __syncthreads();
+    if (2 * sp < P) tile_sync<LT>(4 * sp);  // the next round's pairs see the writes
   }
+  __syncthreads();  // the whole sorted tile is visible to the block
 }
 
 // Smallest power of two P with P * V >= cnt (cnt <= TILE).
