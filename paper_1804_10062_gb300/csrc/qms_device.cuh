@@ -879,6 +879,7 @@ __device__ __forceinline__ uint32_t part_local_small(K* g, uint32_t* gv, int cnt
 // consecutive positions inside a run), walking its tiles forward.
 constexpr int EXW = 8;                 // ranks per lane
 constexpr uint64_t EXJ = 32ull * EXW;  // ranks per warp
+constexpr int EXB = 128;               // threads per exchange block (several blocks per SM)
 
 // Swaps the misplaced pairs of ranks [jw, jw + EXJ) (jw a multiple of EXJ).
 // wtl/wtr give, per warp, the tile holding its first left / right rank.

@@ -332,20 +332,20 @@ __global__ static void __launch_bounds__(NT) k_g_part_prefix(DState* S) {
                    reinterpret_cast<uint64_t*>(s.pmr), s.wtl, s.wtr, s.desc);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     if (s.desc->err) s.active = 0;
-    const unsigned long long per = static_cast<unsigned long long>(NT) * EXW;
+    const unsigned long long per = static_cast<unsigned long long>(EXB) * EXW;
     size_node(s, s.pass2 ? DN_EXCH2 : DN_EXCH1, (s.desc->mis + per - 1) / per);
   }
 }
 
 template <class K, bool HV>
-__global__ void __launch_bounds__(NT) k_g_part_exchange(DState* S) {
+__global__ void __launch_bounds__(EXB) k_g_part_exchange(DState* S) {
   count_launch(S);
   DState& s = *S;
   if (!s.active) return;
   const uint64_t mis = s.desc->mis, lo = s.lo;
   const uint64_t sb = lo + s.desc->L;
-  const uint64_t w0 = (blockIdx.x * static_cast<uint64_t>(NT) + threadIdx.x) >> 5;
-  const uint64_t nw = (static_cast<uint64_t>(gridDim.x) * NT) >> 5;
+  const uint64_t w0 = (blockIdx.x * static_cast<uint64_t>(EXB) + threadIdx.x) >> 5;
+  const uint64_t nw = (static_cast<uint64_t>(gridDim.x) * EXB) >> 5;
   for (uint64_t jw = w0 * EXJ; jw < mis; jw += nw * EXJ)
     exchange_warp<K, HV>(static_cast<K*>(s.keys), s.vals, lo, sb, s.counts,
                          reinterpret_cast<const uint64_t*>(s.pml), reinterpret_cast<const uint64_t*>(s.pmr),

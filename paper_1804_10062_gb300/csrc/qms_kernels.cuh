@@ -463,14 +463,14 @@ static __global__ void __launch_bounds__(NT) k_part_prefix(uint64_t lo, uint64_t
 // Step 3: exchange the misplaced elements by rank (one warp per chunk of
 // EXJ ranks).
 template <class K, bool HV>
-__global__ void __launch_bounds__(NT) k_part_exchange(K* keys, uint32_t* vals, uint64_t lo,
-                                                      const uint32_t* counts, const uint64_t* pml,
-                                                      const uint64_t* pmr, const uint32_t* wtl,
-                                                      const uint32_t* wtr, const Desc* desc) {
+__global__ void __launch_bounds__(EXB) k_part_exchange(K* keys, uint32_t* vals, uint64_t lo,
+                                                       const uint32_t* counts, const uint64_t* pml,
+                                                       const uint64_t* pmr, const uint32_t* wtl,
+                                                       const uint32_t* wtr, const Desc* desc) {
   const uint64_t mis = desc->mis;
   const uint64_t s = lo + desc->L;
-  const uint64_t w0 = (blockIdx.x * static_cast<uint64_t>(NT) + threadIdx.x) >> 5;
-  const uint64_t nw = (static_cast<uint64_t>(gridDim.x) * NT) >> 5;
+  const uint64_t w0 = (blockIdx.x * static_cast<uint64_t>(EXB) + threadIdx.x) >> 5;
+  const uint64_t nw = (static_cast<uint64_t>(gridDim.x) * EXB) >> 5;
   for (uint64_t jw = w0 * EXJ; jw < mis; jw += nw * EXJ)
     exchange_warp<K, HV>(keys, vals, lo, s, counts, pml, pmr, wtl, wtr, jw, mis);
 }

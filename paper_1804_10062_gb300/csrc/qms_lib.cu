@@ -344,9 +344,9 @@ class Sorter {
       prof_.end(st_, QMS_K_PART_SCAN, nt * 20);
       launched();
       const uint64_t maxmis = n / 2 + 1;
-      const uint64_t per = static_cast<uint64_t>(NT) * EXW;
+      const uint64_t per = static_cast<uint64_t>(EXB) * EXW;
       prof_.begin(st_);
-      k_part_exchange<K, HV><<<grid_of((maxmis + per - 1) / per), NT, 0, st_>>>(
+      k_part_exchange<K, HV><<<grid_of((maxmis + per - 1) / per), EXB, 0, st_>>>(
           keys_, vals_, lo, ws_.counts, ws_.pml, ws_.pmr, ws_.wtl, ws_.wtr, ws_.desc);
       prof_.end(st_, QMS_K_PART_EXCHANGE, 0);  // bytes added once mis is known
       launched(3);
@@ -540,7 +540,7 @@ class GraphRunner {
     };
     const unsigned g_part = occ(reinterpret_cast<const void*>(k_g_part_local<K, HV, CNT>), PNT, 0) * 2;
     const unsigned g_leaf = occ(reinterpret_cast<const void*>(k_g_leaf<K, HV, CNT>), LC::LT, tsm_l) * 2;
-    const unsigned g_exch = static_cast<unsigned>(sms) * 4;
+    const unsigned g_exch = occ(reinterpret_cast<const void*>(k_g_part_exchange<K, HV>), EXB, 0) * 2;
     const unsigned g_split = static_cast<unsigned>(sms) * 4;
     const unsigned g_merge = occ(reinterpret_cast<const void*>(k_g_merge<K, HV, CNT>), MBT, 0) * 2;
     // Tiles are handed out through a ticket: with device-sized grids one
@@ -605,7 +605,7 @@ class GraphRunner {
                      dn ? dn + ic : nullptr);
       d = add_kernel(gr, d, reinterpret_cast<const void*>(k_g_part_prefix), g_scan, NT, 0, a_s,
                      dn ? dn + ipf : nullptr);
-      d = add_kernel(gr, d, reinterpret_cast<const void*>(k_g_part_exchange<K, HV>), g_exch, NT, 0, a_s,
+      d = add_kernel(gr, d, reinterpret_cast<const void*>(k_g_part_exchange<K, HV>), g_exch, EXB, 0, a_s,
                      dn ? dn + ie : nullptr);
       return d;
     };
