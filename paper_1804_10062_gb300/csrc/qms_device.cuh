@@ -120,15 +120,17 @@ struct TileSmem {
   }
 };
 
-// Mergesort leaves: LT threads of V keys each.  4-byte keys without
-// payloads use 16384-key leaves (their tile sort needs 32 registers, so 1024
-// threads fit), which saves one merge level per Mergesort; the others keep
-// 8192.
+// Mergesort leaves: LT threads of V keys each.  Keys without payloads use
+// 16384-key leaves (1024 threads; the tile sort needs 32 registers for
+// 4-byte keys, two blocks per SM, and about 53 for 8-byte keys, one block of
+// 139 KB shared memory per SM: the same warps as two 512-thread blocks), which
+// saves one merge level per Mergesort.  With payloads the tile sort needs
+// about 128 registers and keeps 8192-key leaves.
 template <class K, bool HV>
 struct LeafCfg {
-  static constexpr int LT = (sizeof(K) == 4 && !HV) ? 2 * NT : NT;
+  static constexpr int LT = !HV ? 2 * NT : NT;
   static constexpr int TILE_L = LT * V;
-  static constexpr int MINB = (LT == 2 * NT) ? 2 : 1;  // resident blocks per SM built for
+  static constexpr int MINB = (LT == 2 * NT && sizeof(K) == 4) ? 2 : 1;  // blocks per SM built for
 };
 
 // ---------------------------------------------------------------------------
