@@ -124,13 +124,14 @@ struct TileSmem {
 // 16384-key leaves (1024 threads; the tile sort needs 32 registers for
 // 4-byte keys, two blocks per SM, and about 53 for 8-byte keys, one block of
 // 139 KB shared memory per SM: the same warps as two 512-thread blocks), which
-// saves one merge level per Mergesort.  With payloads the tile sort needs
-// about 128 registers and keeps 8192-key leaves.
+// saves one merge level per Mergesort.  With payloads the leaves stay at
+// 8192 keys and are built for two 512-thread blocks per SM (64 registers;
+// for 8-byte keys a few spills, still faster than one block per SM).
 template <class K, bool HV>
 struct LeafCfg {
   static constexpr int LT = !HV ? 2 * NT : NT;
   static constexpr int TILE_L = LT * V;
-  static constexpr int MINB = (LT == 2 * NT && sizeof(K) == 4) ? 2 : 1;  // blocks per SM built for
+  static constexpr int MINB = (sizeof(K) == 4 && LT == 2 * NT) || HV ? 2 : 1;  // blocks per SM built for
 };
 
 // ---------------------------------------------------------------------------
@@ -279,6 +280,28 @@ __device__ __forceinline__ void serial_merge(const K* sk, int ai, int ae, int bi
   }
 }
 
+// The same merge, with the payloads read along (no source indices kept).
+template <class K, bool HV, bool CNT>
+__device__ __forceinline__ void serial_merge_kv(const K* sk, const uint32_t* sv, int ai, int ae,
+                                                int bi, int be, K (&k)[V], uint32_t (&v)[V],
+                                                uint64_t& cmp) {
+  K ka = sk[sk_i<K>(ai)];
+  K kb = sk[sk_i<K>(bi)];
+#pragma unroll
+  for (int j = 0; j < V; ++j) {
+    const bool a_ok = ai < ae, b_ok = bi < be;
+    if (CNT && a_ok && b_ok) ++cmp;
+    const bool tb = b_ok && (!a_ok || kb < ka);
+    k[j] = tb ? kb : ka;
+    if (HV) v[j] = sv[sv_i(tb ? bi : ai)];
+    ai += tb ? 0 : 1;
+    bi += tb ? 1 : 0;
+    const K nk = sk[sk_i<K>(tb ? bi : ai)];
+    ka = tb ? ka : nk;
+    kb = tb ? nk : kb;
+  }
+}
+
 // Batcher's merge-exchange network (Knuth, TAOCP 5.2.2, Algorithm M) for
 // N = 2^t inputs, as a compile-time comparator list.
 struct NetPair {
@@ -362,7 +385,6 @@ __device__ void block_sort_tile(TileSmem<K, HV, LT> s, uint64_t& cmp, int P = LT
   const int tid = threadIdx.x;
   K k[V];
   uint32_t v[V];
-  int src[V];
   __syncthreads();
   if (tid < P) {  // each thread reads, sorts and writes back its own V keys
 #pragma unroll
@@ -386,11 +408,7 @@ __device__ void block_sort_tile(TileSmem<K, HV, LT> s, uint64_t& cmp, int P = LT
     const int d = r * V;
     if (tid < P) {
       const int ia = merge_path_smem<K, CNT>(s.k, a0, L, b0, L, d, cmp);
-      serial_merge<K, CNT>(s.k, a0 + ia, a0 + L, b0 + d - ia, b0 + L, k, src, cmp);
-      if (HV) {
-#pragma unroll
-        for (int j = 0; j < V; ++j) v[j] = s.v[sv_i(src[j])];
-      }
+      serial_merge_kv<K, HV, CNT>(s.k, s.v, a0 + ia, a0 + L, b0 + d - ia, b0 + L, k, v, cmp);
     }
     tile_sync<LT>(2 * sp);  // the pair's reads are done before its writes
     if (tid < P) {
