@@ -83,64 +83,6 @@ __global__ void __launch_bounds__(LeafCfg<K, HV>::LT, LeafCfg<K, HV>::MINB) k_le
   if (CNT) flush_count(cmp, &desc->cmp);
 }
 
-// One swap-merge level: runs of length L in region X -> runs of 2L in Y.
-// k_merge_split first records every tile's merge-path window (one warp per
-// tile), then k_merge_level merges and swaps.
-template <class K, bool CNT>
-__global__ void __launch_bounds__(256) k_merge_split(const K* keys, uint64_t X, uint64_t m,
-                                                     uint64_t L, int xf, uint64_t* splits,
-                                                     Desc* desc) {
-  uint64_t cmp = 0;
-  const uint64_t ntiles = (m + TILE - 1) / TILE;
-  const uint64_t w0 = (blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x) >> 5;
-  const uint64_t nw = (static_cast<uint64_t>(gridDim.x) * blockDim.x) >> 5;
-  for (uint64_t t = w0; t < ntiles; t += nw) merge_split_warp<K, CNT>(keys, X, m, L, t, xf, splits, cmp);
-  if (CNT) flush_count(cmp, &desc->cmp);
-}
-
-// Persistent, double-buffered: while tile i merges, tile i+1's slices are in
-// flight into the other shared buffer and its buffer elements into registers.
-template <class K, bool HV, bool CNT>
-__global__ void __launch_bounds__(NT) k_merge_level(K* keys, uint32_t* vals, uint64_t X, uint64_t Y,
-                                                    uint64_t m, uint64_t L, const uint64_t* splits,
-                                                    int xf, Desc* desc) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  const auto s0 = TileSmem<K, HV>::carve(smem);
-  const auto s1 = TileSmem<K, HV>::carve(smem + tile_smem_bytes<K, HV>());
-  uint64_t cmp = 0;
-  const uint64_t ntiles = (m + TILE - 1) / TILE;
-  uint64_t t = blockIdx.x;
-  if (t < ntiles) {
-    TileGeo<K> cur = tile_geo<K, HV>(keys, vals, X, Y, m, L, t, splits);
-    stage_tile<K, HV>(s0, cur);
-    K y[V];
-    uint32_t yv[V];
-    load_y<K, HV>(cur, y, yv);
-    int c = 0;
-    while (true) {
-      const TileSmem<K, HV> sc = c ? s1 : s0, sn = c ? s0 : s1;
-      cp_async_wait_all();
-      put_y<K, HV>(sc, cur, y, yv, xf);
-      __syncthreads();
-      const uint64_t tn = t + gridDim.x;
-      const bool more = tn < ntiles;
-      TileGeo<K> nxt = cur;
-      if (more) {
-        nxt = tile_geo<K, HV>(keys, vals, X, Y, m, L, tn, splits);
-        stage_tile<K, HV>(sn, nxt);
-        load_y<K, HV>(nxt, y, yv);
-      }
-      merge_staged<K, HV, CNT>(sc, cur, xf, cmp);
-      if (!more) break;
-      __syncthreads();
-      cur = nxt;
-      t = tn;
-      c ^= 1;
-    }
-  }
-  if (CNT) flush_count(cmp, &desc->cmp);
-}
-
 // ---------------------------------------------------------------------------
 // Pivot selection.  Each pivot kernel parks the chosen pivot element at
 // position e - 1 and records its order key and whether the sample held a

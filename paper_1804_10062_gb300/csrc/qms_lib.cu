@@ -148,7 +148,6 @@ class Profiler {
       cudaEventDestroy(r.b);
     }
   }
-  bool on() const { return out_ != nullptr; }
   void begin(cudaStream_t st) {
     if (!out_) return;
     Rec r{};
