@@ -202,7 +202,7 @@ __device__ __forceinline__ void cp_async_wait_all() {
 template <class K, bool HV, int LT = NT>
 __device__ __forceinline__ void load_tile_enc(TileSmem<K, HV, LT> s, const K* g, const uint32_t* gv,
                                               int cnt, int xf) {
-#pragma unroll 4
+#pragma unroll 8
   for (int j = 0; j < V; ++j) {
     const int i = j * LT + threadIdx.x;
     s.k[sk_i<K>(i)] = (i < cnt) ? enc_key(g[i], xf) : key_max<K>();
@@ -224,14 +224,35 @@ __device__ __forceinline__ void store_tile_dec(TileSmem<K, HV, LT> s, K* g, uint
 }
 
 // Copies cnt elements src -> dst (global to global, no overlap), striped.
+// cnt <= LT * V: each thread issues its loads in batches of V/4 before the
+// matching stores (four round trips, few registers).
 template <class K, bool HV, int LT = NT>
 __device__ __forceinline__ void copy_elems(K* dst, uint32_t* dv, const K* src, const uint32_t* sv,
                                            int cnt) {
-  for (int i = threadIdx.x; i < cnt; i += LT) {
-    dst[i] = src[i];
-    if (HV) dv[i] = sv[i];
+  constexpr int B = V / 4;
+#pragma unroll
+  for (int jb = 0; jb < V; jb += B) {
+    K t[B];
+    uint32_t tv[B];
+#pragma unroll
+    for (int j = 0; j < B; ++j) {
+      const int i = (jb + j) * LT + threadIdx.x;
+      if (i < cnt) {
+        t[j] = src[i];
+        if (HV) tv[j] = sv[i];
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < B; ++j) {
+      const int i = (jb + j) * LT + threadIdx.x;
+      if (i < cnt) {
+        dst[i] = t[j];
+        if (HV) dv[i] = tv[j];
+      }
+    }
   }
 }
+
 
 // ---------------------------------------------------------------------------
 // Merge path (stable: on equal keys the A element goes first)
