@@ -9,7 +9,7 @@
 //     mid     - place the pivot; IF a sample tie: partition pass 2 ("<=")
 //     side    - Fig. 3 side choice, Mergesort part and buffer, level count
 //     leaves  - base case X on the part (in place or swapped into the buffer)
-//     WHILE (levels left): split, swap-merge, level end
+//     WHILE (levels left): split, swap-merge (its last block ends the level)
 //     end     - continue on the other side
 //   final leaf sort of the last range.
 //
@@ -569,10 +569,14 @@ __global__ void __launch_bounds__(256) k_g_split(DState* S) {
   if (CNT) flush_count(cmp, &s.desc->cmp);
 }
 
+// One swap-merge level of the level loop.  The last block to finish ends
+// the level: doubles the run length, swaps the regions and sets the loop's
+// condition (all other blocks have read the level's state by then).
 template <class K, bool HV, bool CNT>
-__global__ void __launch_bounds__(MBT, MergeCfg<K, HV>::MINB) k_g_merge(DState* S) {
+__global__ void __launch_bounds__(MBT, MergeCfg<K, HV>::MINB)
+    k_g_merge(DState* S, cudaGraphConditionalHandle h_level) {
   count_launch(S);
-  const DState& s = *S;
+  DState& s = *S;
   using C = MergeCfg<K, HV>;
   const uint64_t m = s.m, L = s.L, X = s.X, Y = s.Y;
   const uint64_t ntiles = (m + C::MT - 1) / C::MT;
@@ -581,18 +585,18 @@ __global__ void __launch_bounds__(MBT, MergeCfg<K, HV>::MINB) k_g_merge(DState* 
     merge_level_tile<K, HV, CNT>(static_cast<K*>(s.keys), s.vals, X, Y, m, L,
                                  reinterpret_cast<const uint64_t*>(s.splits), s.xf, s.desc, t);
   }
-}
-
-__global__ static void k_g_level_end(DState* S, cudaGraphConditionalHandle h_level) {
-  count_launch(S);
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  DState& s = *S;
-  s.L *= 2;
-  const unsigned long long x = s.X;
-  s.X = s.Y;
-  s.Y = x;
-  --s.levels;
-  cudaGraphSetConditional(h_level, s.levels > 0 ? 1u : 0u);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(&s.desc->mdone, 1u) == gridDim.x - 1) {
+      s.desc->mdone = 0;
+      s.L = L * 2;
+      s.X = Y;
+      s.Y = X;
+      --s.levels;
+      cudaGraphSetConditional(h_level, s.levels > 0 ? 1u : 0u);
+    }
+  }
 }
 
 template <class K, bool HV>

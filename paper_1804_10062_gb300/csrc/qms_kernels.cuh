@@ -24,6 +24,7 @@ struct Desc {
   unsigned long long pos;
   unsigned long long bytes;       // algorithmic bytes reported by the batched form
   unsigned long long oticket;     // next tile of the overlapped merge
+  unsigned int mdone;             // blocks of the current merge level that finished
   unsigned int tie;  // pivot sample saw a tie: run the second (<=) pass
   unsigned int err;  // nonzero: an internal consistency check failed
   unsigned int hist[256];

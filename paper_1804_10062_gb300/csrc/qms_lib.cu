@@ -620,9 +620,8 @@ class GraphRunner {
       d = add_cond(gr, d, h_level, cudaGraphCondTypeWhile, &lv);
       cudaGraphNode_t q = add_kernel(lv, nullptr, reinterpret_cast<const void*>(k_g_split<K, HV, CNT>),
                                      g_split, 256, 0, a_s, dn ? dn + DN_SPLIT : nullptr);
-      q = add_kernel(lv, q, reinterpret_cast<const void*>(k_g_merge<K, HV, CNT>), g_merge, MBT, 0, a_s,
-                     dn ? dn + DN_MERGE : nullptr);
-      add_kernel(lv, q, reinterpret_cast<const void*>(k_g_level_end), 1, 32, 0, a_level);
+      add_kernel(lv, q, reinterpret_cast<const void*>(k_g_merge<K, HV, CNT>), g_merge, MBT, 0, a_level,
+                 dn ? dn + DN_MERGE : nullptr);
       return d;
     };
     if (!half) {
