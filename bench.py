@@ -185,6 +185,48 @@ def cpu_baseline(args, lg_sample=24, runs=3):
 
 
 # ---------------------------------------------------------------------------
+# all-cores oracle over many arrays (batched form): one oracle run per
+# segment, the segments dealt round-robin to one spawned process per core
+# (spawn: this process already holds a CUDA context)
+
+
+def _oracle_pool_init():
+    import oracle
+    oracle.lib()
+
+
+def _oracle_pool_work(segs):
+    import oracle
+    keys = 0
+    for seg in segs:
+        oracle.sort(seg, variant="m3", mode="paper")
+        keys += seg.size
+    return keys
+
+
+def oracle_all_cores(np, keys, off, every=8):
+    """A seeded sample of the segments keys[off[i]:off[i+1]] (one in `every`)
+    sorted by the oracle, one run per segment, on every host core; returns
+    the keys/s of the timed pool run (pool start excluded)."""
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    nseg = len(off) - 1
+    pick = np.sort(np.random.default_rng(5).choice(nseg, max(1, nseg // every), replace=False))
+    segs = [keys[int(off[i]):int(off[i + 1])].copy() for i in pick]
+    work = [segs[w::cores] for w in range(cores)]
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores, initializer=_oracle_pool_init) as pool:
+        pool.map(_oracle_pool_work, [[segs[0].copy()]] * cores)  # warm the workers
+        t0 = time.perf_counter()
+        done = sum(pool.map(_oracle_pool_work, work))
+        el = time.perf_counter() - t0
+    return {"value": done / el / 1e9, "unit": "GKeys/s", "cores": cores, "kind": "oracle",
+            "sample": "%d seeded segments (one in %d, %d keys), one oracle run per segment "
+                      "(paper mode, median-of-3), %d spawned processes, %.1f s"
+                      % (len(pick), every, done, cores, el)}
+
+
+# ---------------------------------------------------------------------------
 # batched and served forms
 
 
@@ -202,6 +244,7 @@ def bench_batched(args, q, torch, np):
     for dt in ("u32", "f32"):
         k = gen.keys("uniform", dt, n, 1)
         src = torch.from_numpy(k.view(np.int32)).cuda()
+        cpu_all = oracle_all_cores(np, k, off) if (dt == "u32" and not args.no_cpu_baseline) else None
         del k
         work = torch.empty_like(src)
         work.copy_(src)
@@ -239,6 +282,7 @@ def bench_batched(args, q, torch, np):
                    "plain_per_array": {"value": plain_gk, "unit": "GKeys/s",
                                        "sample": "%d seeded segments, one qms_sort each" % len(idx)},
                    "speedup_vs_plain": v / plain_gk,
+                   "cpu_baseline": cpu_all,
                    "roofline": {"bound": "hbm", "kernel": "k_batched",
                                 "achieved": alg / (kern_ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
                                 "frac": alg / (kern_ms / 1e3) / 1e9 / peak,
