@@ -135,14 +135,18 @@ def measured_peak_hbm():
         return 6800.0, "fallback"
 
 
-def source_sha():
+# Sources that define the swap-merge kernel (k_merge_level3 and the device
+# routines it inlines); the driver files around it do not change its code.
+MERGE_SOURCES = ("qms_device.cuh", "qms_kernels.cuh", "qms_merge.cuh")
+
+
+def source_sha(files=MERGE_SOURCES):
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1804_10062_gb300", "csrc")
-    for fn in sorted(os.listdir(csrc)):
-        if fn.endswith((".cu", ".cuh", ".h")):
-            with open(os.path.join(csrc, fn), "rb") as f:
-                h.update(fn.encode())
-                h.update(f.read())
+    for fn in sorted(files):
+        with open(os.path.join(csrc, fn), "rb") as f:
+            h.update(fn.encode())
+            h.update(f.read())
     return h.hexdigest()[:16]
 
 

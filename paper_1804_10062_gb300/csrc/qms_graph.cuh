@@ -599,6 +599,17 @@ __global__ void __launch_bounds__(MBT, MergeCfg<K, HV>::MINB)
   }
 }
 
+// Enters the round loop only if the array is longer than one leaf tile
+// (else the graph goes straight to the final leaf sort).
+template <class K, bool HV>
+__global__ void k_g_start(DState* S, cudaGraphConditionalHandle h_round) {
+  count_launch(S);
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const DState& s = *S;
+  cudaGraphSetConditional(
+      h_round, s.e - s.b > static_cast<unsigned long long>(LeafCfg<K, HV>::TILE_L) ? 1u : 0u);
+}
+
 template <class K, bool HV>
 __global__ void k_g_end(DState* S, cudaGraphConditionalHandle h_round) {
   count_launch(S);

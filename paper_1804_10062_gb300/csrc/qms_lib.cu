@@ -551,7 +551,7 @@ class GraphRunner {
     cudaGraph_t g = nullptr;
     ck(cudaGraphCreate(&g, 0));
     cudaGraphConditionalHandle h_round, h_pass2, h_level, h_phase = 0, h_ovl = 0;
-    ck(cudaGraphConditionalHandleCreate(&h_round, g, 1, cudaGraphCondAssignDefault));
+    ck(cudaGraphConditionalHandleCreate(&h_round, g, 0, cudaGraphCondAssignDefault));
     ck(cudaGraphConditionalHandleCreate(&h_pass2, g, 0, cudaGraphCondAssignDefault));
     ck(cudaGraphConditionalHandleCreate(&h_level, g, 0, cudaGraphCondAssignDefault));
     if (half) {
@@ -566,7 +566,9 @@ class GraphRunner {
     void* a_side[] = {&S, &h_level, &h_phase, &h_ovl};
     void* a_phase[] = {&S, &h_phase, &h_level};
     cudaGraph_t body = nullptr;
-    cudaGraphNode_t w_round = add_cond(g, nullptr, h_round, cudaGraphCondTypeWhile, &body);
+    cudaGraphNode_t start = add_kernel(g, nullptr, reinterpret_cast<const void*>(k_g_start<K, HV>), 1,
+                                       32, 0, a_round);
+    cudaGraphNode_t w_round = add_cond(g, start, h_round, cudaGraphCondTypeWhile, &body);
     cudaGraphNode_t n = add_kernel(body, nullptr, reinterpret_cast<const void*>(k_g_begin<K, HV, CNT>),
                                    1, 32, 0, a_round);
     if (pivot == QMS_PIVOT_SQRTN) {
