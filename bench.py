@@ -520,7 +520,20 @@ def run_qms(args):
         hout = torch.empty(n, dtype=tdt, pin_memory=True)
         dbuf = [torch.empty(n, dtype=tdt, device="cuda") for _ in range(2)]
         s_up, s_sort, s_down = (torch.cuda.Stream() for _ in range(3))
-        ksteps = max(3, min(args.steps, 6))
+        # the link alone: one upload and one download of a whole array
+        link = {}
+        for name, dst, src, stream in (("h2d_GBps", dbuf[0], hbuf, s_up),
+                                       ("d2h_GBps", hout, dbuf[0], s_down)):
+            torch.cuda.synchronize()
+            c0 = torch.cuda.Event(enable_timing=True)
+            c1 = torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                c0.record(stream)
+                dst.copy_(src, non_blocking=True)
+                c1.record(stream)
+            torch.cuda.synchronize()
+            link[name] = n * esz / (c0.elapsed_time(c1) / 1e3) / 1e9
+        ksteps = max(8, min(args.steps, 16))
         up = [torch.cuda.Event() for _ in range(ksteps)]
         srt = [torch.cuda.Event() for _ in range(ksteps)]
         down = [torch.cuda.Event() for _ in range(ksteps)]
@@ -557,7 +570,7 @@ def run_qms(args):
             assert np.all(out_e2e[1:] >= out_e2e[:-1]), "e2e result not sorted"
         e2e = {"value": ws * ksteps * n / (e_ms / 1e3) / 1e9, "unit": "GKeys/s",
                "h2d_bytes_per_step": n * esz, "d2h_bytes_per_step": n * esz,
-               "steps": ksteps,
+               "steps": ksteps, **link,
                "api": "qms_sort via the C ABI; host pinned buffers; double-buffered, uploads "
                       "and downloads on their own streams overlapping the sorts"}
 

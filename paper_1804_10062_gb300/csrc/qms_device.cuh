@@ -918,7 +918,7 @@ __device__ __forceinline__ uint32_t part_local_small(K* g, uint32_t* gv, int cnt
 // warp w handles ranks [jw, jw + 32 * EXW); one lane finds the chunk's first
 // tile on each side, then lane l swaps ranks jw + l + 32k (consecutive lanes,
 // consecutive positions inside a run), walking its tiles forward.
-constexpr int EXW = 8;                 // ranks per lane
+constexpr int EXW = 16;                // ranks per lane
 constexpr uint64_t EXJ = 32ull * EXW;  // ranks per warp
 constexpr int EXB = 128;               // threads per exchange block (several blocks per SM)
 

@@ -541,7 +541,10 @@ class GraphRunner {
     const unsigned g_leaf = occ(reinterpret_cast<const void*>(k_g_leaf<K, HV, CNT>), LC::LT, tsm_l) * 2;
     const unsigned g_exch = occ(reinterpret_cast<const void*>(k_g_part_exchange<K, HV>), EXB, 0) * 2;
     const unsigned g_split = static_cast<unsigned>(sms) * 4;
-    const unsigned g_merge = occ(reinterpret_cast<const void*>(k_g_merge<K, HV, CNT>), MBT, 0) * 2;
+    // Eight waves of merge blocks that loop over the tiles: one block per tile
+    // costs more in the level-end counter (one atomic per block) than it
+    // gains, two waves too few (2^28 keys: 18.6 / 18.4 / 19.0 ms per sort).
+    const unsigned g_merge = occ(reinterpret_cast<const void*>(k_g_merge<K, HV, CNT>), MBT, 0) * 8;
     // Tiles are handed out through a ticket: with device-sized grids one
     // block per tile, else one wave of blocks that loop.
     const unsigned g_omerge =
