@@ -537,8 +537,11 @@ class GraphRunner {
       ck(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, f, block, smem));
       return static_cast<unsigned>(sms * std::max(o, 1));
     };
-    const unsigned g_part = occ(reinterpret_cast<const void*>(k_g_part_local<K, HV, CNT>), PNT, 0) * 2;
-    const unsigned g_leaf = occ(reinterpret_cast<const void*>(k_g_leaf<K, HV, CNT>), LC::LT, tsm_l) * 2;
+    // Grid caps in waves of resident blocks (the control kernels size each
+    // node to its work up to these), from sweeps at 2^28 keys: leaves 8
+    // waves (2: 18.72 ms per sort, 8: 18.65), partition tiles 4 (18.68).
+    const unsigned g_part = occ(reinterpret_cast<const void*>(k_g_part_local<K, HV, CNT>), PNT, 0) * 4;
+    const unsigned g_leaf = occ(reinterpret_cast<const void*>(k_g_leaf<K, HV, CNT>), LC::LT, tsm_l) * 8;
     const unsigned g_exch = occ(reinterpret_cast<const void*>(k_g_part_exchange<K, HV>), EXB, 0) * 2;
     const unsigned g_split = static_cast<unsigned>(sms) * 4;
     // Eight waves of merge blocks that loop over the tiles: one block per tile
