@@ -547,7 +547,10 @@ class GraphRunner {
     // Eight waves of merge blocks that loop over the tiles: one block per tile
     // costs more in the level-end counter (one atomic per block) than it
     // gains, two waves too few (2^28 keys: 18.6 / 18.4 / 19.0 ms per sort).
-    const unsigned g_merge = occ(reinterpret_cast<const void*>(k_g_merge<K, HV, CNT>), MBT, 0) * 8;
+    // With fixed grids every block of the node runs on every level, however
+    // small, so there it stays at two waves.
+    const unsigned g_merge =
+        occ(reinterpret_cast<const void*>(k_g_merge<K, HV, CNT>), MBT, 0) * (dyn ? 8 : 2);
     // Tiles are handed out through a ticket: with device-sized grids one
     // block per tile, else one wave of blocks that loop.
     const unsigned g_omerge =
