@@ -150,10 +150,18 @@ def source_sha(files=MERGE_SOURCES):
     return h.hexdigest()[:16]
 
 
-def ncu_traffic_per_byte(kernel):
-    """DRAM bytes per algorithmic byte of `kernel` from the committed ncu
-    summary, or None when the summary is missing or the sources changed."""
-    p = os.path.join(ROOT, "profiles", "%s_traffic.md" % kernel)
+# ncu DRAM-traffic summaries per (kernel class, log2 n, dtype, pivot rule)
+TRAFFIC_PROFILES = {("merge", 28, "u32", "m3"): "k_merge_level3_traffic_n2p28_u32_m3.md"}
+
+
+def ncu_traffic_per_byte(kernel, lgn, dtype, pivot):
+    """DRAM bytes per algorithmic byte of `kernel` on this workload from the
+    committed ncu summary, or None when there is none for the workload, or
+    the sources changed since it was taken."""
+    name = TRAFFIC_PROFILES.get((kernel, lgn, dtype, pivot))
+    if name is None:
+        return None
+    p = os.path.join(ROOT, "profiles", name)
     try:
         txt = open(p).read()
     except OSError:
@@ -494,7 +502,7 @@ def run_qms(args):
     dom = max(pd, key=lambda k: pd[k]["ms"])
     peak, peak_kind = measured_peak_hbm()
     achieved = pd[dom]["bytes"] / (pd[dom]["ms"] / 1e3) / 1e9 if pd[dom]["ms"] > 0 else 0.0
-    tpb = ncu_traffic_per_byte(dom)
+    tpb = ncu_traffic_per_byte(dom, args.lgn, args.dtype, args.pivot)
     per_launch_alg = pd[dom]["bytes"] / max(1, pd[dom]["launches"])
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                 "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
