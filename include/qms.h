@@ -105,7 +105,7 @@ typedef struct {
 
 typedef struct {
   uint64_t comparisons; /* element comparisons made (count_cmps only)          */
-  uint64_t aux_bytes;   /* device workspace used (about n/19 bytes + 18 KB)    */
+  uint64_t aux_bytes;   /* device workspace used (about n/27 bytes + 18 KB)    */
   uint64_t rounds;      /* partition rounds                                      */
   uint64_t mom_rounds;  /* rounds that used a median-of-medians pivot            */
   uint64_t launches;    /* kernels launched                                      */
