@@ -12,7 +12,12 @@ hybrid variants Sec. 4, comparison counter Sec. 5).
 Parity status: every exported function is pinned by the ``-m "not gpu"``
 tests (exhaustive permutations against the exact-average recurrence derived
 from the proof of Thm. 1, duplicates, Mergesort closed forms, the Cor. 1 band,
-the worst-case bound of Sec. 4, the Fig. 1 worked example and a library sort).
+the worst-case bound of Sec. 4, the Fig. 1 worked example and a library sort;
+for the median-of-medians machinery of Sec. 4: the median of five on every
+permutation and tied word, the selection against the order statistic and the
+BFPRT discard bound (tight on a constructed input), the 2 floor(n/6) pivot
+rank of every MoM round, the 2n/3 partition, the hybrid's switching rule; and
+for the move counter, closed forms of Fig. 3's moves on reverse input).
 """
 from __future__ import annotations
 
@@ -67,6 +72,27 @@ def lib():
             L.qms_ref_adversary_u32.argtypes = [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int,
                                                 ctypes.c_int, u64p]
             L.qms_ref_adversary_u32.restype = ctypes.c_int
+            L.qms_ref_sort2.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                                        ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                        ctypes.c_int, u64p, u64p]
+            L.qms_ref_sort2.restype = ctypes.c_int
+            L.qms_ref_moves_u32.argtypes = [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int,
+                                            ctypes.c_int, ctypes.c_int, ctypes.c_int, u64p, u64p]
+            L.qms_ref_moves_u32.restype = ctypes.c_int
+            L.qms_ref_out_moves_u32.argtypes = [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_size_t,
+                                                ctypes.c_size_t, ctypes.c_int, u64p, u64p]
+            L.qms_ref_out_moves_u32.restype = ctypes.c_int
+            L.qms_ref_median5_u32.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), u64p]
+            L.qms_ref_median5_u32.restype = ctypes.c_int
+            szp = ctypes.POINTER(ctypes.c_size_t)
+            L.qms_ref_select_u32.argtypes = [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_size_t,
+                                             ctypes.c_int, szp, u64p, ctypes.c_void_p,
+                                             ctypes.c_size_t, szp]
+            L.qms_ref_select_u32.restype = ctypes.c_int
+            L.qms_ref_rounds_u32.argtypes = [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int,
+                                             ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                             ctypes.c_void_p, ctypes.c_size_t, szp, u64p]
+            L.qms_ref_rounds_u32.restype = ctypes.c_int
             _lib = L
     return _lib
 
@@ -78,10 +104,15 @@ def _dtype_name(a: np.ndarray) -> str:
     raise TypeError("unsupported key dtype %s" % a.dtype)
 
 
+MOM_RULES = {"basic": 0, "faithful": 1}
+
+
 def sort(keys: np.ndarray, vals: np.ndarray | None = None, variant: str = "m3",
-         mode: str = "analysis", side: int = 0):
+         mode: str = "analysis", side: int = 0, mom: str = "basic"):
     """Sorts ``keys`` in place (and ``vals`` with them).
 
+    ``mom="faithful"`` adds the Sec. 4 details to median-of-medians rounds
+    (adaptive selection, partition of the 2n/3 non-medians only).
     Returns ``(comparisons, rounds)``.
     """
     assert keys.flags.c_contiguous
@@ -92,11 +123,92 @@ def sort(keys: np.ndarray, vals: np.ndarray | None = None, variant: str = "m3",
         vp = vals.ctypes.data
     c = ctypes.c_uint64(0)
     r = ctypes.c_uint64(0)
-    rc = lib().qms_ref_sort(keys.ctypes.data, vp, len(keys), DTYPES[d], VARIANTS[variant],
-                            MODES[mode], side, ctypes.byref(c), ctypes.byref(r))
+    rc = lib().qms_ref_sort2(keys.ctypes.data, vp, len(keys), DTYPES[d], VARIANTS[variant],
+                             MODES[mode], side, MOM_RULES[mom], ctypes.byref(c), ctypes.byref(r))
     if rc != 0:
         raise RuntimeError("qms_ref_sort failed: %d" % rc)
     return c.value, r.value
+
+
+def sort_moves_u32(keys: np.ndarray, variant: str = "m3", mode: str = "analysis", side: int = 0,
+                   mom: str = "basic"):
+    """Sorts uint32 ``keys`` in place counting element moves (Sec. 5: an
+    assignment of an input element is one move, a swap three).
+
+    Returns ``(comparisons, moves)``.
+    """
+    assert keys.dtype == np.uint32 and keys.flags.c_contiguous
+    c = ctypes.c_uint64(0)
+    m = ctypes.c_uint64(0)
+    rc = lib().qms_ref_moves_u32(keys.ctypes.data, len(keys), VARIANTS[variant], MODES[mode],
+                                 side, MOM_RULES[mom], ctypes.byref(c), ctypes.byref(m))
+    if rc != 0:
+        raise RuntimeError("qms_ref_moves_u32 failed: %d" % rc)
+    return c.value, m.value
+
+
+def out_moves_u32(a: np.ndarray, b: int, e: int, temp: int, mode: str = "analysis"):
+    """Fig. 3 ``out`` with moves counted; returns ``(comparisons, moves)``."""
+    assert a.dtype == np.uint32 and a.flags.c_contiguous
+    c = ctypes.c_uint64(0)
+    m = ctypes.c_uint64(0)
+    rc = lib().qms_ref_out_moves_u32(a.ctypes.data, b, e, temp, MODES[mode], ctypes.byref(c),
+                                     ctypes.byref(m))
+    if rc != 0:
+        raise RuntimeError("qms_ref_out_moves_u32 failed: %d" % rc)
+    return c.value, m.value
+
+
+def median5_u32(v) -> tuple:
+    """The selection's median of five: ``(index of the median in v, comparisons)``."""
+    a = np.ascontiguousarray(np.asarray(v, dtype=np.uint32))
+    assert a.size == 5
+    pos = ctypes.c_int(-1)
+    c = ctypes.c_uint64(0)
+    rc = lib().qms_ref_median5_u32(a.ctypes.data, ctypes.byref(pos), ctypes.byref(c))
+    if rc != 0:
+        raise RuntimeError("qms_ref_median5_u32 failed")
+    return pos.value, c.value
+
+
+def select_u32(a: np.ndarray, i: int, adaptive: bool = False, trace_cap: int = 4096):
+    """Groups-of-five selection of rank ``i`` in ``a`` (rearranged in place).
+
+    Returns ``(position, comparisons, trace)`` with ``trace`` an array of
+    (range size, size continued on) pairs, one per iteration.
+    """
+    assert a.dtype == np.uint32 and a.flags.c_contiguous
+    pos = ctypes.c_size_t(0)
+    c = ctypes.c_uint64(0)
+    ln = ctypes.c_size_t(0)
+    tr = np.zeros(2 * trace_cap, dtype=np.uint64)
+    rc = lib().qms_ref_select_u32(a.ctypes.data, len(a), i, 1 if adaptive else 0,
+                                  ctypes.byref(pos), ctypes.byref(c), tr.ctypes.data, trace_cap,
+                                  ctypes.byref(ln))
+    if rc != 0:
+        raise RuntimeError("qms_ref_select_u32 failed")
+    k = min(ln.value, trace_cap)
+    return pos.value, c.value, tr[: 2 * k].reshape(k, 2)
+
+
+ROUND_FIELDS = ("b", "e", "lt", "gt", "mom", "cmp_pivot", "cmp_part", "left")
+
+
+def rounds_u32(keys: np.ndarray, variant: str = "m3", mode: str = "analysis", side: int = 0,
+               mom: str = "basic", cap: int = 1 << 16):
+    """Sorts uint32 ``keys`` in place and returns ``(rounds, comparisons)``,
+    ``rounds`` an array of records with the fields ``ROUND_FIELDS``."""
+    assert keys.dtype == np.uint32 and keys.flags.c_contiguous
+    rec = np.zeros(8 * cap, dtype=np.uint64)
+    ln = ctypes.c_size_t(0)
+    c = ctypes.c_uint64(0)
+    rc = lib().qms_ref_rounds_u32(keys.ctypes.data, len(keys), VARIANTS[variant], MODES[mode],
+                                  side, MOM_RULES[mom], rec.ctypes.data, cap, ctypes.byref(ln),
+                                  ctypes.byref(c))
+    if rc != 0:
+        raise RuntimeError("qms_ref_rounds_u32 failed")
+    k = min(ln.value, cap)
+    return rec[: 8 * k].reshape(k, 8), c.value
 
 
 def out_u32(a: np.ndarray, b: int, e: int, temp: int, mode: str = "analysis") -> int:

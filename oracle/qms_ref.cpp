@@ -22,6 +22,13 @@
 //     [Sec. 4], HybridQuickMergesort with delta = 1/16 [Sec. 4].
 //   * An element-comparison counter [Sec. 5]: every call of the order
 //     predicate adds one.
+//   * An element-move counter [Sec. 5, the moves experiment]: the sort run on
+//     a key type whose construction and assignment from another element
+//     count one move each, so a swap counts three.
+//   * The MoM details of Sec. 4 as an option ("faithful" MoM): adaptive
+//     selection inside the median-of-medians routine, and a partition of
+//     only the 2n/3 elements that are not medians of triples (the medians
+//     are already on the correct side once the selection has run).
 //
 // Readings of points the paper leaves open (each also listed in the design
 // notes of the repository):
@@ -45,6 +52,15 @@
 //     median of five); all n - 1 other elements are compared with the pivot.
 //     MoM rounds Mergesort the larger side when its ceil(m/2) buffer fits
 //     in the smaller side, else the smaller side.
+//   * Faithful MoM (Sec. 4, last paragraphs): the selection looks for rank k
+//     among n elements; for k <= 0.3n it takes as pivot the group median of
+//     rank ceil((k+1)/3) - 1 (the smallest rank that still places at least
+//     k + 1 elements at or below the pivot, so the sought element stays on
+//     the kept side while about 0.3n elements or more are discarded), and
+//     mirrored for k >= 0.7n; otherwise the median of the group medians.
+//     After the selection the n/3 medians are split around the pivot, so
+//     only the other elements are compared with it; blocks are then put in
+//     place by rotations (moves, no comparisons).
 //   * HQMS: a median-of-3 pivot whose rank inside the current range lies
 //     outside [floor(n/16), n - 1 - floor(n/16)] makes the next round MoM;
 //     the round after that is median-of-3 again.
@@ -105,14 +121,46 @@ struct Split {
   bool mom;       // the round used a MoM pivot
 };
 
+// One partition round as seen by the tests: the range, the pivot block, the
+// rule, the comparisons spent choosing the pivot and partitioning, and the
+// side that was Mergesorted.
+struct RoundRec {
+  uint64_t b, e, lt, gt, mom, cmp_pivot, cmp_part, left;
+};
+
+// One iteration of the groups-of-five selection: the range size and the size
+// of the part it continues on (0 once the element is found).
+struct SelRec {
+  uint64_t n, kept;
+};
+
+// An element type whose moves are counted: every construction from, or
+// assignment of, another element adds one (so std::swap adds three).
+template <class K>
+struct Counted {
+  K v;
+  static thread_local uint64_t moves;
+  Counted() : v() {}
+  Counted(const Counted& o) : v(o.v) { ++moves; }
+  Counted& operator=(const Counted& o) {
+    v = o.v;
+    ++moves;
+    return *this;
+  }
+};
+template <class K>
+thread_local uint64_t Counted<K>::moves = 0;
+
 template <class E, class Less>
 class QuickMergesort {
  public:
-  QuickMergesort(E* a, Less less, int variant, int mode, int side)
-      : a_(a), less_(less), variant_(variant), mode_(mode), side_(side) {}
+  QuickMergesort(E* a, Less less, int variant, int mode, int side, int mom = 0)
+      : a_(a), less_(less), variant_(variant), mode_(mode), side_(side), mom_(mom) {}
 
   uint64_t comparisons() const { return cmps_; }
   uint64_t rounds() const { return rounds_; }
+  std::vector<RoundRec>* round_log = nullptr;  // filled when set
+  std::vector<SelRec>* select_log = nullptr;   // filled when set
 
   // Sorts a[b, e) ascending.
   void sort(size_t b, size_t e) {
@@ -123,6 +171,7 @@ class QuickMergesort {
       const size_t n = e - b;
       const bool mom_round =
           variant_ == MOM || (variant_ == HYBRID && mom_next);
+      const uint64_t c0 = cmps_;
       Split s;
       if (variant_ == SQRTN) {
         s = partition_sqrtn(b, e);
@@ -150,6 +199,11 @@ class QuickMergesort {
         left = s.lt < (b + e) / 2;
       } else {
         left = nl <= nr;  // three-way split: the smaller side
+      }
+      if (round_log) {
+        const uint64_t part = s.mom ? part_cmps_ : 0;
+        round_log->push_back(RoundRec{b, e, s.lt, s.gt, s.mom ? 1u : 0u,
+                                      cmps_ - c0 - part, part, left ? 1u : 0u});
       }
       if (left) {
         out(b, s.lt, s.gt);
@@ -303,7 +357,7 @@ class QuickMergesort {
     const size_t step = n / k;
     for (size_t i = 0; i < k; ++i) std::swap(a_[b + i], a_[b + i * step]);
     // Sort the sample with this same algorithm (counted).
-    QuickMergesort inner(a_, less_, variant_, mode_, side_);
+    QuickMergesort inner(a_, less_, variant_, mode_, side_, mom_);
     inner.sort(b, b + k);
     cmps_ += inner.comparisons();
     const size_t pm = b + k / 2;
@@ -315,6 +369,8 @@ class QuickMergesort {
     return two_way_front(b, e);
   }
 
+  // (Test hooks: the selection routines below are public.)
+ public:
   // Median of a[p0], a[p1], a[p2] with at most 3 comparisons; returns its
   // position.
   size_t median3_pos(size_t p0, size_t p1, size_t p2) {
@@ -345,33 +401,50 @@ class QuickMergesort {
     return L(4, 2) ? p[4] : p[2];  // p1 is the minimum of the four
   }
 
-  // Groups-of-five selection (median of medians): rearranges a[b, e) and
-  // returns the position of an element of rank i (0-based) in it.
+  // Groups-of-five selection (median of medians, [CLRS Sec. 9.3] as cited
+  // in Sec. 4): rearranges a[b, e) and returns the position of an element of
+  // rank i (0-based) in it.  Afterwards a[b, pos) <= a[pos] <= a[pos+1, e).
+  // With mom_ = 1 the pivot of an iteration adapts to i (Sec. 4, last
+  // paragraphs; the reading is in the header).
   size_t select(size_t b, size_t e, size_t i) {
     while (true) {
       const size_t n = e - b;
       if (n <= 5) {
         insertion_sort(b, e);
+        if (select_log) select_log->push_back(SelRec{n, 0});
         return b + i;
       }
       const size_t g = n / 5;
       for (size_t j = 0; j < g; ++j) {
         std::swap(a_[b + j], a_[median5_pos(b + 5 * j)]);
       }
-      const size_t mm = select(b, b + g, g / 2);
+      size_t rank = g / 2;
+      if (mom_ == 1) {
+        if (10 * i <= 3 * n) {
+          rank = (i + 1 + 2) / 3 - 1;  // ceil((i + 1) / 3) - 1
+        } else if (10 * i >= 7 * n) {
+          rank = g - 1 - ((n - i + 2) / 3 - 1);  // the mirror image
+        }
+        if (rank > g - 1) rank = g - 1;
+      }
+      const size_t mm = select(b, b + g, rank);
       std::swap(a_[b], a_[mm]);
       Split s = three_way(b, e, a_[b]);
       if (i < s.lt - b) {
+        if (select_log) select_log->push_back(SelRec{n, s.lt - b});
         e = s.lt;
       } else if (i < s.gt - b) {
+        if (select_log) select_log->push_back(SelRec{n, 0});
         return b + i;
       } else {
+        if (select_log) select_log->push_back(SelRec{n, e - s.gt});
         i -= s.gt - b;
         b = s.gt;
       }
     }
   }
 
+ private:
   Split partition_mom(size_t b, size_t e) {
     const size_t n = e - b, t = n / 3;
     for (size_t i = 0; i < t; ++i) {
@@ -379,34 +452,79 @@ class QuickMergesort {
       std::swap(a_[b + i], a_[p]);
     }
     const size_t mm = select(b, b + t, t / 2);
-    std::swap(a_[b], a_[mm]);
-    Split s = (mode_ == PAPER) ? three_way(b, e, a_[b]) : two_way_front(b, e);
+    const uint64_t c0 = cmps_;
+    Split s;
+    if (mom_ == 1 && t >= 1) {
+      s = partition_rest(b, e, t, mm);
+    } else {
+      std::swap(a_[b], a_[mm]);
+      s = (mode_ == PAPER) ? three_way(b, e, a_[b]) : two_way_front(b, e);
+    }
+    part_cmps_ = cmps_ - c0;
     s.mom = true;
     return s;
   }
 
+  // Sec. 4: once the selection has run, the medians a[b, b + t) are split
+  // around the pivot a[mm] (those before it are <= it, those after >= it),
+  // so only the n - t other elements are compared with the pivot: once each
+  // in analysis mode, three-way (at most twice) in paper mode.  Rotations
+  // then bring the blocks into partition order.
+  Split partition_rest(size_t b, size_t e, size_t t, size_t mm) {
+    const size_t m0 = b + t;  // first non-median
+    const E v = a_[mm];
+    size_t nl = m0, ne = m0, hi = e;
+    // a[m0, nl) < v, a[nl, ne) == v, a[ne, hi) unknown, a[hi, e) > v
+    while (ne < hi) {
+      if (lt(a_[ne], v)) {
+        std::swap(a_[nl++], a_[ne++]);
+      } else if (mode_ == PAPER && lt(v, a_[ne])) {
+        std::swap(a_[ne], a_[--hi]);
+      } else if (mode_ == PAPER) {
+        ++ne;
+      } else {
+        // analysis mode: two-way, ">= v" stays right
+        ++ne;
+      }
+    }
+    if (mode_ != PAPER) {  // no equal block: a[nl, e) >= v
+      hi = nl;
+      ne = nl;
+    }
+    // [b, mm) medians <= v, mm pivot, (mm, m0) medians >= v,
+    // [m0, nl) < v, [nl, ne) == v (paper mode), [ne, e) > v / >= v.
+    // 1. Move the left non-medians before the pivot.
+    std::rotate(a_ + mm, a_ + m0, a_ + nl);
+    const size_t p = mm + (nl - m0);  // the pivot's new index
+    // 2. Move the equal non-medians right after the pivot.
+    const size_t rm = m0 - mm - 1;  // medians right of the pivot
+    std::rotate(a_ + p + 1, a_ + p + 1 + rm, a_ + p + 1 + rm + (ne - nl));
+    return Split{p, p + 1 + (ne - nl), true};
+  }
+
   E* a_;
   Less less_;
-  int variant_, mode_, side_;
+  int variant_, mode_, side_, mom_;
   uint64_t cmps_ = 0;
   uint64_t rounds_ = 0;
+  uint64_t part_cmps_ = 0;  // comparisons of the last MoM round's partition
 };
 
 template <class K, class KLess>
 int sort_typed(void* keys, uint32_t* vals, size_t n, int variant, int mode,
-               int side, uint64_t* cmps, uint64_t* rounds) {
+               int side, int mom, uint64_t* cmps, uint64_t* rounds) {
   using Less = ByKey<K, KLess>;
   K* k = static_cast<K*>(keys);
   uint64_t c = 0, r = 0;
   if (vals == nullptr) {
-    QuickMergesort<K, Less> s(k, Less{}, variant, mode, side);
+    QuickMergesort<K, Less> s(k, Less{}, variant, mode, side, mom);
     if (n > 1) s.sort(0, n);
     c = s.comparisons();
     r = s.rounds();
   } else {
     std::vector<Pair<K>> e(n);
     for (size_t i = 0; i < n; ++i) e[i] = Pair<K>{k[i], vals[i]};
-    QuickMergesort<Pair<K>, Less> s(e.data(), Less{}, variant, mode, side);
+    QuickMergesort<Pair<K>, Less> s(e.data(), Less{}, variant, mode, side, mom);
     if (n > 1) s.sort(0, n);
     for (size_t i = 0; i < n; ++i) {
       k[i] = e[i].key;
@@ -454,6 +572,13 @@ struct AdversaryLess {
   }
 };
 
+struct LessCounted {
+  bool operator()(const Counted<uint32_t>& x, const Counted<uint32_t>& y) const {
+    return x.v < y.v;
+  }
+};
+using CountedU32 = Counted<uint32_t>;
+
 }  // namespace
 
 extern "C" {
@@ -464,22 +589,124 @@ extern "C" {
 // side: 0 = Fig. 3 (Mergesort the side left of the midpoint test),
 //       1 = larger side whenever its buffer fits.
 // vals: NULL for key-only sorts, else payloads moved with their keys.
-int qms_ref_sort(void* keys, uint32_t* vals, size_t n, int dtype, int variant,
-                 int mode, int side, uint64_t* cmps, uint64_t* rounds) {
+int qms_ref_sort2(void* keys, uint32_t* vals, size_t n, int dtype, int variant,
+                  int mode, int side, int mom, uint64_t* cmps, uint64_t* rounds) {
   if (keys == nullptr && n > 0) return -1;
-  if (variant < 0 || variant > 3 || mode < 0 || mode > 1) return -1;
+  if (variant < 0 || variant > 3 || mode < 0 || mode > 1 || mom < 0 || mom > 1) return -1;
   switch (dtype) {
     case 0:
-      return sort_typed<uint32_t, LessU32>(keys, vals, n, variant, mode, side, cmps, rounds);
+      return sort_typed<uint32_t, LessU32>(keys, vals, n, variant, mode, side, mom, cmps, rounds);
     case 1:
-      return sort_typed<uint64_t, LessU64>(keys, vals, n, variant, mode, side, cmps, rounds);
+      return sort_typed<uint64_t, LessU64>(keys, vals, n, variant, mode, side, mom, cmps, rounds);
     case 2:
-      return sort_typed<int64_t, LessI64>(keys, vals, n, variant, mode, side, cmps, rounds);
+      return sort_typed<int64_t, LessI64>(keys, vals, n, variant, mode, side, mom, cmps, rounds);
     case 3:
-      return sort_typed<float, LessF32>(keys, vals, n, variant, mode, side, cmps, rounds);
+      return sort_typed<float, LessF32>(keys, vals, n, variant, mode, side, mom, cmps, rounds);
     default:
       return -1;
   }
+}
+
+int qms_ref_sort(void* keys, uint32_t* vals, size_t n, int dtype, int variant,
+                 int mode, int side, uint64_t* cmps, uint64_t* rounds) {
+  return qms_ref_sort2(keys, vals, n, dtype, variant, mode, side, 0, cmps, rounds);
+}
+
+// The same sort on uint32 keys with element moves counted (Sec. 5: a move
+// is an assignment of an input element; a swap counts three).
+int qms_ref_moves_u32(uint32_t* keys, size_t n, int variant, int mode, int side, int mom,
+                      uint64_t* cmps, uint64_t* moves) {
+  if (keys == nullptr && n > 0) return -1;
+  if (variant < 0 || variant > 3 || mode < 0 || mode > 1 || mom < 0 || mom > 1) return -1;
+  std::vector<CountedU32> e(n);
+  for (size_t i = 0; i < n; ++i) e[i].v = keys[i];
+  CountedU32::moves = 0;
+  QuickMergesort<CountedU32, LessCounted> s(e.data(), LessCounted{}, variant, mode, side, mom);
+  if (n > 1) s.sort(0, n);
+  const uint64_t mv = CountedU32::moves;
+  for (size_t i = 0; i < n; ++i) keys[i] = e[i].v;
+  if (cmps) *cmps = s.comparisons();
+  if (moves) *moves = mv;
+  return 0;
+}
+
+// Fig. 3 "out" alone with moves counted (see qms_ref_out_u32).
+int qms_ref_out_moves_u32(uint32_t* a, size_t b, size_t e, size_t temp, int mode,
+                          uint64_t* cmps, uint64_t* moves) {
+  if (a == nullptr || e < b) return -1;
+  const size_t r = (e - b) - (e - b) / 2;
+  if (temp < e && temp + r > b) return -1;
+  const size_t len = std::max(e, temp + r);
+  std::vector<CountedU32> v(len);
+  for (size_t i = 0; i < len; ++i) v[i].v = a[i];
+  CountedU32::moves = 0;
+  QuickMergesort<CountedU32, LessCounted> s(v.data(), LessCounted{}, M3, mode, 0);
+  s.out(b, e, temp);
+  const uint64_t mv = CountedU32::moves;
+  for (size_t i = 0; i < len; ++i) a[i] = v[i].v;
+  if (cmps) *cmps = s.comparisons();
+  if (moves) *moves = mv;
+  return 0;
+}
+
+// Test hook: the 6-comparison median of five used by the selection.  *pos
+// receives the index (0..4) of the median within v[0..5) (v is not changed).
+int qms_ref_median5_u32(const uint32_t* v, int* pos, uint64_t* cmps) {
+  if (v == nullptr || pos == nullptr) return -1;
+  uint32_t a[5];
+  std::memcpy(a, v, sizeof(a));
+  using Less = ByKey<uint32_t, LessU32>;
+  QuickMergesort<uint32_t, Less> s(a, Less{}, MOM, ANALYSIS, 0);
+  *pos = static_cast<int>(s.median5_pos(0));
+  if (cmps) *cmps = s.comparisons();
+  return 0;
+}
+
+// Test hook: groups-of-five selection of rank i in a[0, n) (rearranged in
+// place); *pos receives the position of the selected element.  adaptive = 1
+// uses the Sec. 4 adaptation.  trace (may be NULL) receives up to cap
+// (n, kept) pairs, one per iteration at every recursion depth; *len their
+// number.
+int qms_ref_select_u32(uint32_t* a, size_t n, size_t i, int adaptive, size_t* pos,
+                       uint64_t* cmps, uint64_t* trace, size_t cap, size_t* len) {
+  if (a == nullptr || pos == nullptr || i >= n || adaptive < 0 || adaptive > 1) return -1;
+  using Less = ByKey<uint32_t, LessU32>;
+  QuickMergesort<uint32_t, Less> s(a, Less{}, MOM, PAPER, 0, adaptive);
+  std::vector<SelRec> log;
+  s.select_log = &log;
+  *pos = s.select(0, n, i);
+  if (cmps) *cmps = s.comparisons();
+  if (len) *len = log.size();
+  for (size_t j = 0; trace != nullptr && j < log.size() && j < cap; ++j) {
+    trace[2 * j] = log[j].n;
+    trace[2 * j + 1] = log[j].kept;
+  }
+  return 0;
+}
+
+// Test hook: sorts uint32 keys and records every partition round as eight
+// words (b, e, lt, gt, mom, cmp_pivot, cmp_part, left): the range, the
+// pivot block, whether the pivot was a median of medians, the comparisons
+// spent choosing the pivot (everything but the partition of a MoM round),
+// the partition comparisons of a MoM round, and whether the left side was
+// Mergesorted.  Up to cap rounds are written; *len receives their number.
+int qms_ref_rounds_u32(uint32_t* keys, size_t n, int variant, int mode, int side, int mom,
+                       uint64_t* rec, size_t cap, size_t* len, uint64_t* cmps) {
+  if (keys == nullptr && n > 0) return -1;
+  if (variant < 0 || variant > 3 || mode < 0 || mode > 1 || mom < 0 || mom > 1) return -1;
+  using Less = ByKey<uint32_t, LessU32>;
+  QuickMergesort<uint32_t, Less> s(keys, Less{}, variant, mode, side, mom);
+  std::vector<RoundRec> log;
+  s.round_log = &log;
+  if (n > 1) s.sort(0, n);
+  if (len) *len = log.size();
+  if (cmps) *cmps = s.comparisons();
+  for (size_t j = 0; rec != nullptr && j < log.size() && j < cap; ++j) {
+    const RoundRec& r = log[j];
+    const uint64_t w[8] = {r.b, r.e, r.lt, r.gt, r.mom, r.cmp_pivot, r.cmp_part, r.left};
+    std::memcpy(rec + 8 * j, w, sizeof(w));
+  }
+  return 0;
 }
 
 // Mergesort alone (Fig. 3 "out"): sorts a[b, e) using the ceil((e-b)/2)
