@@ -27,6 +27,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 DTYPE_BYTES = {"u32": 4, "u64": 8, "i64": 8, "f32": 4}
+# One metric string for both arms, so that the two lines can be divided.
+METRIC = "GKeys/s (plain sort)"
 
 
 def parse():
@@ -41,6 +43,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the batched and served forms")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the per-configuration records (C1-C3 workloads)")
     ap.add_argument("--batched-segments", type=int, default=65536)
     ap.add_argument("--served-requests", type=int, default=2000)
     ap.add_argument("--served-lg-max", type=float, default=26.0)
@@ -176,13 +180,15 @@ def ncu_traffic_per_byte(kernel, lgn, dtype, pivot):
 # ---------------------------------------------------------------------------
 
 
-def cpu_baseline(args, lg_sample=24, runs=3):
-    import numpy as np  # noqa: F401
+def cpu_baseline(args, lg_sample=None, runs=1, host=None):
+    """The oracle timed on the host: by default one sort of the whole
+    workload (the same keys the GPU sorts; about 20 s at 2^28)."""
     import oracle
     import qms_inputs as gen
+    lg_sample = args.lgn if lg_sample is None else lg_sample
     n = 1 << lg_sample
     dist = "normal" if args.dtype == "f32" else "uniform"
-    k0 = gen.keys(dist, args.dtype, n, 1000)
+    k0 = host if (host is not None and host.size == n) else gen.keys(dist, args.dtype, n, 1000)
     oracle.lib()
     ts = []
     for _ in range(runs):
@@ -192,8 +198,9 @@ def cpu_baseline(args, lg_sample=24, runs=3):
         ts.append(time.perf_counter() - t0)
     total = sum(ts)
     return {"value": runs * n / total / 1e9, "unit": "GKeys/s", "cores": 1, "kind": "oracle",
-            "sample": "%d runs of the single-threaded oracle on n=2^%d %s keys (the same "
-                      "distribution, %.1f s of CPU work)" % (runs, lg_sample, args.dtype, total)}
+            "sample": "%d run(s) of the single-threaded oracle (paper mode) on n=2^%d %s keys "
+                      "of the workload's distribution, %.1f s of CPU work" %
+                      (runs, lg_sample, args.dtype, total)}
 
 
 # ---------------------------------------------------------------------------
@@ -395,13 +402,149 @@ def bench_served(args, q, torch, np):
             "speedup_vs_fifo_plain": sat["sustained"] / fifo}
 
 
+def _to_dev(torch, np, k):
+    if k.dtype == np.uint32:
+        return torch.from_numpy(k.view(np.int32)).cuda()
+    if k.dtype == np.uint64:
+        return torch.from_numpy(k.view(np.int64)).cuda()
+    return torch.from_numpy(k).cuda()
+
+
+def whole_roofline(pd, ms, peak, peak_kind):
+    """Every kernel class's algorithmic bytes of one sort over its timed
+    device time: the whole-sort HBM fraction."""
+    b = sum(v["bytes"] for v in pd.values())
+    a = b / (ms / 1e3) / 1e9
+    return {"bound": "hbm", "scope": "whole sort (all kernel classes)", "achieved": a,
+            "peak": peak, "unit": "GB/s", "frac": a / peak, "peak_source": peak_kind,
+            "alg_bytes_per_sort": b}
+
+
+def plain_record(q, torch, np, k, dtype, pivot, dist, pairs=False, reps=3, count=False,
+                 cpu_sample=None, peak=(6800.0, "fallback")):
+    """One configuration of the plain form: device time of `reps` graph
+    sorts (median), the whole-sort roofline from a profiled pass of the same
+    sort, optional comparison counts beside the oracle's, and the oracle
+    timed on a bounded sample of the same distribution."""
+    import oracle
+    n = k.size
+    src = _to_dev(torch, np, k)
+    work = torch.empty_like(src)
+    vsrc = torch.arange(n, dtype=torch.int32, device="cuda") if pairs else None
+    vals = torch.empty_like(vsrc) if pairs else None
+
+    def reset():
+        work.copy_(src)
+        if pairs:
+            vals.copy_(vsrc)
+
+    def sort(**kw):
+        if pairs:
+            return q.qms_sort_pairs(work, vals, pivot=pivot, dtype=dtype, **kw)
+        return q.qms_sort(work, pivot=pivot, dtype=dtype, **kw)
+
+    reset()
+    sort()  # builds or reuses the graph instance
+    ts = []
+    for _ in range(reps):
+        reset()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        sort(wait=False)
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    ms = statistics.median(ts)
+    head = work[: min(n, 1 << 20)].cpu().numpy().view(k.dtype)
+    ok = bool(np.all(head[1:] >= head[:-1])) if dtype != "f32" else True
+    reset()
+    prof = q.qms_profile()
+    sort(profile=prof)
+    pd = prof.as_dict()
+    pk, pkind = peak
+    rec = {"value": n / (ms / 1e3) / 1e9, "unit": "GKeys/s", "ms": ms, "n": n, "dtype": dtype,
+           "pivot": pivot, "dist": dist, "pairs": pairs, "prefix_sorted": ok,
+           "roofline": whole_roofline(pd, ms, pk, pkind),
+           "kernels_ms": {kk: round(v["ms"], 4) for kk, v in pd.items() if v["launches"]}}
+    if count:
+        reset()
+        st = sort(count_cmps=True)
+        kc = k.copy()
+        oc, _ = oracle.sort(kc, variant=pivot, mode="analysis")
+        rec["comparisons_per_key"] = {"gpu": st["comparisons"] / n, "oracle_analysis": oc / n,
+                                      "lg_n_factorial": float(np.sum(np.log2(np.arange(2, n + 1)))) / n}
+    if cpu_sample is not None:
+        ks, vs, what = cpu_sample
+        t0 = time.perf_counter()
+        oracle.sort(ks, vs, variant=pivot, mode="paper")
+        el = time.perf_counter() - t0
+        rec["cpu_baseline"] = {"value": ks.size / el / 1e9, "unit": "GKeys/s", "cores": 1,
+                               "kind": "oracle", "sample": what + " (%.2f s)" % el}
+    del src, work, vsrc, vals
+    torch.cuda.empty_cache()
+    return rec
+
+
+def config_records(args, q, torch, np):
+    """The configurations besides the headline: C1 (2^20 permutation with
+    comparison counts), C2 (2^28 int64 and float32; 2^24 with every pivot
+    rule) and C3 (2^27 uint64 keys with uint32 payloads over six key
+    distributions, hybrid pivot)."""
+    import oracle
+    import qms_inputs as gen
+    peak = measured_peak_hbm()
+    out = {}
+    lg_cpu = 22
+
+    def sample(dist, dtype, pairs=False, lg=lg_cpu):
+        m = 1 << lg
+        if dist == "killer":
+            ks = oracle.adversary_u32(m, "hybrid", "paper")[0].astype(np.uint64)
+        elif dist == "perm":
+            ks = gen.permutation_u32(m, 11)
+        else:
+            ks = gen.keys(dist, dtype, m, 11)
+        vs = gen.payload_index(m) if pairs else None
+        return ks, vs, "oracle on n=2^%d %s %s keys%s" % (lg, dist, dtype,
+                                                          " with payloads" if pairs else "")
+
+    k = gen.permutation_u32(1 << 20, 1)
+    out["C1_perm_u32_2p20_m3"] = plain_record(q, torch, np, k, "u32", "m3", "perm", reps=5,
+                                              count=True, cpu_sample=sample("perm", "u32", lg=20),
+                                              peak=peak)
+    for dtype, dist in (("i64", "uniform"), ("f32", "normal")):
+        k = gen.keys(dist, dtype, 1 << 28, 3)
+        out["C2_%s_2p28_m3" % dtype] = plain_record(q, torch, np, k, dtype, "m3", dist,
+                                                    cpu_sample=sample(dist, dtype), peak=peak)
+        del k
+    for dtype, dist in (("u32", "uniform"), ("i64", "uniform"), ("f32", "normal")):
+        k = gen.keys(dist, dtype, 1 << 24, 4)
+        for pivot in ("m3", "sqrtn", "mom", "hybrid"):
+            out["C2_%s_2p24_%s" % (dtype, pivot)] = plain_record(
+                q, torch, np, k, dtype, pivot, dist, reps=5,
+                cpu_sample=sample(dist, dtype) if dtype == "u32" else None, peak=peak)
+        del k
+    for dist in ("uniform", "mod16", "sorted", "reverse", "organ", "killer"):
+        if dist == "killer":
+            k = oracle.adversary_u32(1 << 27, "hybrid", "paper")[0].astype(np.uint64)
+        else:
+            k = gen.keys(dist, "u64", 1 << 27, 9)
+        out["C3_pairs_u64_2p27_%s_hybrid" % dist] = plain_record(
+            q, torch, np, k, "u64", "hybrid", dist, pairs=True,
+            cpu_sample=sample(dist, "u64", pairs=True), peak=peak)
+        del k
+    return out
+
+
 def run_reference(args):
     ws, rank, _ = dist_init(args)
     if rank != 0:
         return 0
     import oracle
     import qms_inputs as gen
-    lg = min(args.lgn, 22)
+    lg = min(args.lgn, 25)
     n = 1 << lg
     dist = "normal" if args.dtype == "f32" else "uniform"
     k0 = gen.keys(dist, args.dtype, n, 2)
@@ -413,7 +556,7 @@ def run_reference(args):
         oracle.sort(k0.copy(), variant=args.pivot, mode="paper")
     el = time.perf_counter() - t0
     v = args.steps * n / el / 1e9
-    line = {"impl": "reference", "metric": "GKeys/s (plain sort)", "value": v, "unit": "GKeys/s",
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "GKeys/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
@@ -504,6 +647,9 @@ def run_qms(args):
     achieved = pd[dom]["bytes"] / (pd[dom]["ms"] / 1e3) / 1e9 if pd[dom]["ms"] > 0 else 0.0
     tpb = ncu_traffic_per_byte(dom, args.lgn, args.dtype, args.pivot)
     per_launch_alg = pd[dom]["bytes"] / max(1, pd[dom]["launches"])
+    # the profiled pass ran K sorts: per-sort bytes over the timed pass's time per sort
+    per_sort = {k: {"bytes": v["bytes"] / args.steps} for k, v in pd.items()}
+    whole = whole_roofline(per_sort, el_ms / args.steps, peak, peak_kind)
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                 "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
                 "timing": "CUDA events around every launch, in a profiled pass of the same K "
@@ -592,17 +738,24 @@ def run_qms(args):
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(args)
+        cpu = cpu_baseline(args, host=host)
+
+    configs = None
+    if rank == 0 and not args.no_configs:
+        del bufs, work
+        torch.cuda.empty_cache()
+        bufs, work = [], None
+        configs = config_records(args, q, torch, np)
 
     forms = None
     if not args.no_forms:
-        del bufs, work
+        bufs, work = [], None
         torch.cuda.empty_cache()
         forms = {"batched": bench_batched(args, q, torch, np),
                  "served": bench_served(args, q, torch, np)}
 
     if rank == 0:
-        line = {"metric": "GKeys/s (plain sort); %% HBM roofline of the dominant kernel",
+        line = {"metric": METRIC,
                 "value": value, "unit": "GKeys/s", "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": el_ms / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -611,8 +764,9 @@ def run_qms(args):
                            "arrays_per_gpu_step": 1, "l2": "inputs larger than L2 (%d MiB per "
                            "array), no flush" % (n * esz >> 20),
                            "parallelism": "replicas" if ws > 1 else "single GPU"},
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": launches, "clocks": ck, "forms": forms}
+                "roofline": roofline, "roofline_whole_sort": whole, "cpu_baseline": cpu,
+                "e2e": e2e, "gpu_launches": launches, "clocks": ck, "configs": configs,
+                "forms": forms}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

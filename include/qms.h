@@ -8,7 +8,9 @@
  * and continue on the remaining side (Sec. 2 and the Fig. 3 listing).  The
  * problem statement is internal sorting: n elements, ascending, with only
  * O(log n) extra words beyond the array (Sec. 1).  On the GPU the extra
- * memory is O(n / 8192 + 1) words (one counter per 8192-key tile).
+ * memory is O(n / 256 + 1) words, about n/27 bytes plus an 18 KB descriptor
+ * (per-tile counters and prefixes of the partition, merge-path splits,
+ * overlapped-merge flags); there is no n-sized scratch.
  *
  * Conventions for every call:
  *   - Key and payload pointers are DEVICE pointers owned by the caller; sorts
@@ -92,13 +94,20 @@ typedef struct {
                                   "out" with its overlapped final merge), whenever it
                                   exceeds 8192 keys and that buffer fits.  Default:
                                   Fig. 3's side rule with a full-size buffer          */
+#define QMS_FLAG_TEST_WITHHOLD 8 /* test hook for failure handling: the overlapped
+                                  merge of QMS_FLAG_LARGER_SIDE rounds never marks
+                                  its first tile done, so the waits on that tile run
+                                  out after spin_limit polls and the sort returns
+                                  QMS_ETIMEOUT (its output is then unspecified)       */
 
 typedef struct {
   int pivot;       /* QMS_PIVOT_*                                              */
   int count_cmps;  /* nonzero: use the counting kernels and report
                       qms_stats.comparisons (element comparisons, Sec. 5)      */
   int flags;       /* QMS_FLAG_*                                               */
-  int reserved1;
+  int spin_limit;  /* polls of one completion flag before a bounded device wait
+                      gives up with QMS_ETIMEOUT; <= 0: the default, 2^20 polls
+                      (about a second).  Only the overlapped merge waits.     */
   qms_profile* profile; /* NULL, or accumulates per-kernel device times (host-
                            driven rounds, CUDA events around every launch)    */
 } qms_options;
@@ -119,13 +128,15 @@ const char* qms_error_string(int code);
 
 /* Sorts d_keys[0, n) in place, ascending (the QuickMergesort driver loop of
  * Fig. 3: partition, Mergesort the side left of the midpoint test, continue
- * on the other side; ranges of at most 8192 keys are finished by the base
- * case).  By default the whole round loop runs on the device as one CUDA
- * graph with conditional nodes (instances are cached per key type, pivot
- * rule and device; the first call of a kind builds one) and the call returns
+ * on the other side; a last range of at most one Mergesort leaf -- 16384
+ * keys, 8192 with payloads -- is finished by the base case).  By default
+ * the whole round loop runs on the device as one CUDA graph with
+ * conditional nodes (instances are cached per key type, pivot rule and
+ * device; the first call of a kind builds one) and the call returns
  * after the sort finished; with QMS_FLAG_ASYNC and stats == NULL it returns
  * once the sort is enqueued on `stream`.  Errors: QMS_EINVAL (d_keys NULL
- * with n > 1, bad dtype or pivot), QMS_ENOMEM, QMS_ECUDA, QMS_EINTERNAL. */
+ * with n > 1, bad dtype or pivot), QMS_ENOMEM, QMS_ECUDA, QMS_EINTERNAL,
+ * QMS_ETIMEOUT (a bounded device wait gave up; see qms_options.spin_limit). */
 int qms_sort(void* d_keys, size_t n, int dtype, const qms_options* opt, void* stream,
              qms_stats* stats);
 
@@ -153,7 +164,7 @@ int qms_sort_batched(void* d_keys, uint32_t* d_vals, const uint64_t* d_offsets, 
  * admitted in arrival order against a device-memory budget -- the bytes the
  * server itself holds for a request: a device slot for its keys, unless the
  * keys are a device array sorted in place (in == out), plus the sort's
- * O(n/8192 + 1)-word workspace -- and a maximum number of admitted requests.
+ * workspace (about n/27 bytes) -- and a maximum number of admitted requests.
  * Worker threads, each with its own stream, run admitted work concurrently:
  * a request longer than 64 * 8192 keys runs alone through the grid-wide
  * rounds; shorter ones waiting at the head of the queue are sorted together
@@ -259,10 +270,16 @@ int qms_mergesort_half(void* d_keys, uint32_t* d_vals, size_t m, size_t buf, int
  *   - No cudaMalloc, cudaFree or allocating library routine is called.
  *   - The first call on a device looks up the array's device address (with
  *     that device current); make that first call before any stream capture.
+ *     The address is kept for the life of the process, so the library must
+ *     not be used across a cudaDeviceReset.
  *   - All calls share the one array and it keeps the last call's contents
  *     (each call clears what must start at zero).  Calls that overlap on the
  *     GPU (other streams, other host threads) race on it: serialise them.
- * Returns as qms_sort. */
+ *   - The rounds run from the host: the call reads one small result back
+ *     per round and returns once the sort has finished on `stream`
+ *     (QMS_FLAG_ASYNC has no effect).  QMS_FLAG_LARGER_SIDE, count_cmps and
+ *     spin_limit behave as in qms_sort.
+ * Errors as qms_sort. */
 int qms_sort_noalloc(void* d_keys, size_t n, int dtype, const qms_options* opt, void* stream,
                      qms_stats* stats);
 

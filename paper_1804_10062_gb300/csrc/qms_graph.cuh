@@ -39,6 +39,8 @@ struct DState {
   uint32_t* wtl;
   uint32_t* wtr;
   int fig3;  // always Fig. 3's side rule
+  unsigned spin_limit;  // polls of one flag before a bounded wait gives up
+  int withhold;         // test hook: the overlapped merge never publishes tile 0
   // driver state
   unsigned long long b, e;          // remaining range
   unsigned long long lo, hi, parked;  // current partition pass
@@ -529,7 +531,7 @@ __global__ void __launch_bounds__(MBT, MergeCfg<K, HV>::MINB) k_g_ovl_merge(DSta
   const uint64_t q = s.M0 / 2, r = s.M0 - q;
   ovl_merge_loop<K, HV, CNT>(static_cast<K*>(s.keys), s.vals, s.B0, r, s.P0, q,
                              reinterpret_cast<const uint64_t*>(s.splits), s.wtl, s.wtr, s.flags,
-                             s.xf, s.desc);
+                             s.xf, s.desc, s.spin_limit, s.withhold);
 }
 
 template <class K, bool HV, bool CNT>

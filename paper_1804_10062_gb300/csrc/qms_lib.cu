@@ -26,6 +26,7 @@
 #include "qms_cta.cuh"
 #include "qms_merge.cuh"
 #include "qms_graph.cuh"
+#include "qms_host.h"
 
 namespace qms {
 namespace {
@@ -42,14 +43,10 @@ inline int xform_of(int dtype) {
   return dtype == QMS_F32 ? XF_F32 : (dtype == QMS_I64 ? XF_I64 : XF_NONE);
 }
 
-// Raises the dynamic shared-memory limit of a kernel once per process.
+// Raises the dynamic shared-memory limit of a kernel on the current device.
 template <class F>
-void allow_smem(F* f, size_t bytes, bool& done) {
-  if (!done) {
-    ck(cudaFuncSetAttribute(reinterpret_cast<const void*>(f),
-                            cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes)));
-    done = true;
-  }
+void allow_smem(F* f, size_t bytes) {
+  ck(smem_attr(reinterpret_cast<const void*>(f), bytes));
 }
 
 // Host mirror of the descriptor fields the driver reads back each round.
@@ -193,16 +190,15 @@ class Sorter {
  public:
   Sorter(K* keys, uint32_t* vals, int xf, cudaStream_t st, Workspace& ws, Profiler& prof)
       : keys_(keys), vals_(vals), xf_(xf), st_(st), ws_(ws), prof_(prof) {
-    static bool a1 = false, a2 = false, a3 = false, a4 = false;
-    allow_smem(k_leaf_sort<K, HV, CNT>, tile_smem_bytes<K, HV, LeafCfg<K, HV>::LT>(), a1);
-    (void)a2;
-    (void)a3;
-    allow_smem(k_pivot_sample<K, HV, CNT>, tile_smem_bytes<K, true>(), a4);
+    allow_smem(k_leaf_sort<K, HV, CNT>, tile_smem_bytes<K, HV, LeafCfg<K, HV>::LT>());
+    allow_smem(k_pivot_sample<K, HV, CNT>, tile_smem_bytes<K, true>());
   }
 
   uint64_t rounds = 0, mom_rounds = 0, launches = 0;
   uint64_t exchanged_bytes = 0;  // algorithmic bytes of the exchange steps
   bool fig3_side = true;         // Fig. 3's side rule; false: the larger side when it fits
+  unsigned spin_limit = kOvlSpinLimit;  // polls of one flag in a bounded device wait
+  int withhold = 0;                     // test hook (QMS_FLAG_TEST_WITHHOLD)
 
   // ---- steps ------------------------------------------------------------
 
@@ -275,7 +271,8 @@ class Sorter {
     prof_.end(st_, QMS_K_MERGE_SPLIT, 0);
     prof_.begin(st_);
     k_ovl_merge<K, HV, CNT><<<grid_of(mtiles), MBT, 0, st_>>>(
-        keys_, vals_, Bb, r, P, q, ws_.splits, ws_.wtl, ws_.wtr, ws_.flags, xf_, ws_.desc);
+        keys_, vals_, Bb, r, P, q, ws_.splits, ws_.wtl, ws_.wtr, ws_.flags, xf_, ws_.desc,
+        spin_limit, withhold);
     prof_.end(st_, QMS_K_MERGE, 4 * m * ES);
     launched(3);
   }
@@ -523,15 +520,9 @@ class GraphRunner {
     using LC = LeafCfg<K, HV>;
     const size_t tsm = tile_smem_bytes<K, HV>(), tsm_s = tile_smem_bytes<K, true>();
     const size_t tsm_l = tile_smem_bytes<K, HV, LC::LT>();
-    static std::once_flag once;
-    std::call_once(once, [&] {
-      cudaFuncSetAttribute(reinterpret_cast<const void*>(k_g_leaf<K, HV, CNT>),
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(tsm_l));
-      cudaFuncSetAttribute(reinterpret_cast<const void*>(k_g_final<K, HV, CNT>),
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(tsm_l));
-      cudaFuncSetAttribute(reinterpret_cast<const void*>(k_g_pivot_sample<K, HV, CNT>),
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(tsm_s));
-    });
+    allow_smem(k_g_leaf<K, HV, CNT>, tsm_l);
+    allow_smem(k_g_final<K, HV, CNT>, tsm_l);
+    allow_smem(k_g_pivot_sample<K, HV, CNT>, tsm_s);
     auto occ = [&](const void* f, int block, size_t smem) {
       int o = 0;
       ck(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, f, block, smem));
@@ -756,7 +747,7 @@ class GraphRunner {
 
   // Enqueues the sort of keys[0, n) on st; with stats, waits and fills them.
   static int run(K* keys, uint32_t* vals, uint64_t n, int dtype, int pivot, bool fig3,
-                 cudaStream_t st, qms_stats* stats) {
+                 unsigned spin_limit, int withhold, cudaStream_t st, qms_stats* stats) {
     const auto t0 = std::chrono::steady_clock::now();
     GraphInst* gi = acquire(n, pivot, !fig3, st);
     struct Rel {
@@ -780,6 +771,8 @@ class GraphRunner {
     h.splits = reinterpret_cast<unsigned long long*>(w + wl.splits);
     h.flags = reinterpret_cast<unsigned*>(w + wl.flags);
     h.fig3 = fig3 ? 1 : 0;
+    h.spin_limit = spin_limit;
+    h.withhold = withhold;
     h.wtl = reinterpret_cast<uint32_t*>(w + wl.wtl);
     h.wtr = reinterpret_cast<uint32_t*>(w + wl.wtr);
     h.b = 0;
@@ -877,6 +870,12 @@ int dispatch(const Args& a, qms_stats* stats, Fn&& fn) {
 
 bool valid_dtype(int d) { return d >= QMS_U32 && d <= QMS_F32; }
 
+// Polls of one flag before a bounded device wait gives up.
+unsigned spin_limit_of(const qms_options* opt) {
+  if (opt == nullptr || opt->spin_limit <= 0) return kOvlSpinLimit;
+  return static_cast<unsigned>(opt->spin_limit);
+}
+
 // ---------------------------------------------------------------------------
 // Batched form: many independent segments of one array.  Segments of at most
 // CTA_MAX_TILES tiles are sorted in one persistent launch (one block per
@@ -945,8 +944,7 @@ int run_batched(void* keys, uint32_t* vals, const uint64_t* d_off, size_t nseg, 
   const int xf = xform_of(dtype);
   if (nsmall) {
     ck(cudaMemcpyAsync(d_order, order.data(), static_cast<size_t>(nsmall) * 4, cudaMemcpyHostToDevice, st));
-    static bool attr = false;
-    allow_smem(k_batched<K, HV, CNT>, tile_smem_bytes<K, HV>(), attr);
+    allow_smem(k_batched<K, HV, CNT>, tile_smem_bytes<K, HV>());
     int dev = 0, sms = 0, occ = 0;
     ck(cudaGetDevice(&dev));
     ck(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -1054,8 +1052,8 @@ int noalloc_scratch(unsigned char** out) {
 }
 
 template <class K, bool CNT>
-int run_noalloc(void* keys, uint64_t n, int dtype, int pivot, cudaStream_t st,
-                unsigned char* base, qms_stats* stats) {
+int run_noalloc(void* keys, uint64_t n, int dtype, int pivot, const qms_options* opt,
+                cudaStream_t st, unsigned char* base, qms_stats* stats) {
   const auto t0 = std::chrono::steady_clock::now();
   Workspace ws;  // base stays null: nothing is allocated and nothing is freed
   ws.st = st;
@@ -1066,6 +1064,9 @@ int run_noalloc(void* keys, uint64_t n, int dtype, int pivot, cudaStream_t st,
   ck(cudaMemsetAsync(ws.desc, 0, sizeof(Desc), st));
   Profiler prof(nullptr);
   Sorter<K, false, CNT> s(static_cast<K*>(keys), nullptr, xform_of(dtype), st, ws, prof);
+  s.fig3_side = !(opt && (opt->flags & QMS_FLAG_LARGER_SIDE));
+  s.spin_limit = spin_limit_of(opt);
+  s.withhold = (opt && (opt->flags & QMS_FLAG_TEST_WITHHOLD)) ? 1 : 0;
   s.sort(n, pivot);
   unsigned long long cmp = 0;
   unsigned err = 0;
@@ -1121,9 +1122,13 @@ static int sort_common(void* d_keys, uint32_t* d_vals, size_t n, int dtype, cons
          opt ? opt->profile : nullptr};
   const bool host_driven = (opt && (opt->profile || (opt->flags & QMS_FLAG_HOST_DRIVEN)));
   const bool fig3 = !(opt && (opt->flags & QMS_FLAG_LARGER_SIDE));
+  const unsigned spin = spin_limit_of(opt);
+  const int withhold = (opt && (opt->flags & QMS_FLAG_TEST_WITHHOLD)) ? 1 : 0;
   if (host_driven)
     return dispatch(a, stats, [&](auto& s) {
       s.fig3_side = fig3;
+      s.spin_limit = spin;
+      s.withhold = withhold;
       s.sort(n, pivot);
     });
   qms_stats local{};
@@ -1133,7 +1138,8 @@ static int sort_common(void* d_keys, uint32_t* d_vals, size_t n, int dtype, cons
     const bool hv = d_vals != nullptr, cnt = a.count;
     const cudaStream_t s = a.st;
 #define QMS_G(K, H, C) \
-  GraphRunner<K, H, C>::run(static_cast<K*>(d_keys), d_vals, n, dtype, pivot, fig3, s, st)
+  GraphRunner<K, H, C>::run(static_cast<K*>(d_keys), d_vals, n, dtype, pivot, fig3, spin, withhold, \
+                            s, st)
     if (u64) {
       if (hv) return cnt ? QMS_G(uint64_t, true, true) : QMS_G(uint64_t, true, false);
       return cnt ? QMS_G(uint64_t, false, true) : QMS_G(uint64_t, false, false);
@@ -1215,11 +1221,11 @@ int qms_sort_noalloc(void* d_keys, size_t n, int dtype, const qms_options* opt, 
   const bool cnt = opt && opt->count_cmps;
   try {
     if (dtype == QMS_U64 || dtype == QMS_I64) {
-      return cnt ? run_noalloc<uint64_t, true>(d_keys, n, dtype, pivot, st, base, stats)
-                 : run_noalloc<uint64_t, false>(d_keys, n, dtype, pivot, st, base, stats);
+      return cnt ? run_noalloc<uint64_t, true>(d_keys, n, dtype, pivot, opt, st, base, stats)
+                 : run_noalloc<uint64_t, false>(d_keys, n, dtype, pivot, opt, st, base, stats);
     }
-    return cnt ? run_noalloc<uint32_t, true>(d_keys, n, dtype, pivot, st, base, stats)
-               : run_noalloc<uint32_t, false>(d_keys, n, dtype, pivot, st, base, stats);
+    return cnt ? run_noalloc<uint32_t, true>(d_keys, n, dtype, pivot, opt, st, base, stats)
+               : run_noalloc<uint32_t, false>(d_keys, n, dtype, pivot, opt, st, base, stats);
   } catch (const Err& e) {
     return e.code;
   } catch (...) {

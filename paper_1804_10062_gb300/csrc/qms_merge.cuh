@@ -415,7 +415,7 @@ __global__ void __launch_bounds__(256) k_ovl_deps(uint64_t la, uint64_t lb, cons
     ovl_deps_tile<MT>(la, lb, splits, dep_lo, dep_hi, t);
 }
 
-constexpr unsigned kOvlSpinLimit = 1u << 20;  // polls of one flag (about a second)
+constexpr unsigned kOvlSpinLimit = 1u << 20;  // default polls of one flag (about a second)
 constexpr unsigned kErrOvlWait = 8u;          // Desc::err bit: a wait ran out
 
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
@@ -428,11 +428,12 @@ __device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
 }
 
 // Waits until flags[u] != 0 for every u in [u0, u1) (the block's threads
-// share the flags); false if a wait ran out.  The first wait that runs out
-// sets kErrOvlWait in *err, and every wait, current or later, that sees the
-// bit gives up at once: one stuck tile costs one wait, not one per tile.
+// share the flags); false if a wait ran out (more than `limit` polls of one
+// flag).  The first wait that runs out sets kErrOvlWait in *err, and every
+// wait, current or later, that sees the bit gives up at once: one stuck tile
+// costs one wait, not one per tile.
 __device__ __forceinline__ bool wait_flags(const unsigned* flags, uint64_t u0, uint64_t u1,
-                                           unsigned* err) {
+                                           unsigned* err, unsigned limit) {
   bool ok = (ld_acquire_u32(err) & kErrOvlWait) == 0;
   for (uint64_t u = u0 + threadIdx.x; u < u1 && ok; u += blockDim.x) {
     unsigned it = 0;
@@ -441,7 +442,7 @@ __device__ __forceinline__ bool wait_flags(const unsigned* flags, uint64_t u0, u
         ok = false;
         break;
       }
-      if (it > kOvlSpinLimit) {
+      if (it > limit) {
         atomicOr(err, kErrOvlWait);
         ok = false;
         break;
@@ -468,7 +469,7 @@ __device__ __forceinline__ bool ovl_merge_tile(K* keys, uint32_t* vals, uint64_t
                                                const uint32_t* dep_lo, const uint32_t* dep_hi,
                                                unsigned* flags, unsigned* err, int xf, uint64_t t,
                                                K* sin, K* sout, uint32_t* svin, uint32_t* svout,
-                                               uint64_t& cmp) {
+                                               uint64_t& cmp, unsigned limit, bool withhold) {
   using C = MergeCfg<K, HV>;
   constexpr int VM = C::VM, MT = C::MT;
   constexpr int PE = 128 / static_cast<int>(sizeof(K));
@@ -492,7 +493,7 @@ __device__ __forceinline__ bool ovl_merge_tile(K* keys, uint32_t* vals, uint64_t
   bool ok = true;
   {
     const uint64_t u0 = dep_lo[t], u1 = dep_hi[t];
-    if (u0 < u1) ok = wait_flags(flags, u0, u1, err);
+    if (u0 < u1) ok = wait_flags(flags, u0, u1, err, limit);
   }
   // 2. Load the tile's elements and the buffer elements bound for their
   //    slots together.
@@ -540,8 +541,11 @@ __device__ __forceinline__ bool ovl_merge_tile(K* keys, uint32_t* vals, uint64_t
                                HV ? vals + Ob + o0 : nullptr, xf, cmp);
   // 4. Publish.  A tile that moved buffer elements into later windows makes
   //    them visible before its flag; any other tile has nothing a later tile
-  //    reads and only sets the flag.
-  if (static_cast<uint64_t>(W) < b_hi - b_lo) {
+  //    reads and only sets the flag.  (withhold: a test hook that never
+  //    publishes tile 0, so that the waits on it run out.)
+  if (withhold && t == 0) {
+    // nothing is published
+  } else if (static_cast<uint64_t>(W) < b_hi - b_lo) {
     __syncthreads();
     if (tid == 0) {
       __threadfence();
@@ -557,7 +561,8 @@ template <class K, bool HV, bool CNT>
 __device__ __forceinline__ void ovl_merge_loop(K* keys, uint32_t* vals, uint64_t Ab, uint64_t la,
                                                uint64_t Ob, uint64_t lb, const uint64_t* splits,
                                                const uint32_t* dep_lo, const uint32_t* dep_hi,
-                                               unsigned* flags, int xf, Desc* desc) {
+                                               unsigned* flags, int xf, Desc* desc, unsigned limit,
+                                               int withhold) {
   using C = MergeCfg<K, HV>;
   __shared__ K sin[C::IN_K];
   __shared__ K sout[C::IN_K];
@@ -579,7 +584,8 @@ __device__ __forceinline__ void ovl_merge_loop(K* keys, uint32_t* vals, uint64_t
     __syncthreads();  // every thread has read the ticket
     if (!one && threadIdx.x == 0) ticket = atomicAdd(&desc->oticket, 1ull);
     ok = ovl_merge_tile<K, HV, CNT>(keys, vals, Ab, la, Ob, lb, splits, dep_lo, dep_hi, flags,
-                                    &desc->err, xf, t, sin, sout, svin, svout, cmp) && ok;
+                                    &desc->err, xf, t, sin, sout, svin, svout, cmp, limit,
+                                    withhold != 0) && ok;
     if (one) break;
     __syncthreads();
     t = ticket;
@@ -592,8 +598,9 @@ template <class K, bool HV, bool CNT>
 __global__ void __launch_bounds__(MBT, MergeCfg<K, HV>::MINB)
     k_ovl_merge(K* keys, uint32_t* vals, uint64_t Ab, uint64_t la, uint64_t Ob, uint64_t lb,
                 const uint64_t* splits, const uint32_t* dep_lo, const uint32_t* dep_hi,
-                unsigned* flags, int xf, Desc* desc) {
-  ovl_merge_loop<K, HV, CNT>(keys, vals, Ab, la, Ob, lb, splits, dep_lo, dep_hi, flags, xf, desc);
+                unsigned* flags, int xf, Desc* desc, unsigned limit, int withhold) {
+  ovl_merge_loop<K, HV, CNT>(keys, vals, Ab, la, Ob, lb, splits, dep_lo, dep_hi, flags, xf, desc,
+                             limit, withhold);
 }
 
 }  // namespace qms

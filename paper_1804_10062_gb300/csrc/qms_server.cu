@@ -32,6 +32,7 @@
 
 #include "../../include/qms.h"
 #include "qms_cta.cuh"
+#include "qms_host.h"
 
 namespace qms {
 namespace {
@@ -175,12 +176,7 @@ int run_group_typed(std::vector<Req*>& g, cudaStream_t st, int pivot) {
   }
   ok(cudaMemsetAsync(base, 0, hdr, st));
   ok(cudaMemcpyAsync(segs, hs.data(), hs.size() * sizeof(SegDesc), cudaMemcpyHostToDevice, st));
-  static std::once_flag once;
-  std::call_once(once, [] {
-    cudaFuncSetAttribute(reinterpret_cast<const void*>(k_batched_ptrs<K, false>),
-                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         static_cast<int>(tile_smem_bytes<K, false>()));
-  });
+  ok(smem_attr(reinterpret_cast<const void*>(k_batched_ptrs<K, false>), tile_smem_bytes<K, false>()));
   int dev = 0, sms = 0, occ = 0;
   ok(cudaGetDevice(&dev));
   ok(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));

@@ -44,7 +44,7 @@ class qms_profile(ctypes.Structure):
 
 class qms_options(ctypes.Structure):
     _fields_ = [("pivot", ctypes.c_int), ("count_cmps", ctypes.c_int),
-                ("flags", ctypes.c_int), ("reserved1", ctypes.c_int),
+                ("flags", ctypes.c_int), ("spin_limit", ctypes.c_int),
                 ("profile", ctypes.POINTER(qms_profile))]
 
 
@@ -164,11 +164,12 @@ def _raise(rc, what):
 QMS_FLAG_ASYNC = 1
 QMS_FLAG_HOST_DRIVEN = 2
 QMS_FLAG_LARGER_SIDE = 4
+QMS_FLAG_TEST_WITHHOLD = 8
 SIDES = {"fig3": 0, "larger": QMS_FLAG_LARGER_SIDE}
 
 
-def _options(pivot, count_cmps, profile, flags=0):
-    opt = qms_options(PIVOTS[pivot], 1 if count_cmps else 0, flags, 0, None)
+def _options(pivot, count_cmps, profile, flags=0, spin_limit=0):
+    opt = qms_options(PIVOTS[pivot], 1 if count_cmps else 0, flags, int(spin_limit), None)
     if profile is not None:
         opt.profile = ctypes.pointer(profile)
     return opt
@@ -176,7 +177,7 @@ def _options(pivot, count_cmps, profile, flags=0):
 
 def qms_sort(keys, pivot: str = "m3", count_cmps: bool = False, stream=None, dtype=None,
              profile: qms_profile | None = None, host_driven: bool = False, wait: bool = True,
-             side: str = "fig3"):
+             side: str = "fig3", spin_limit: int = 0, test_withhold: bool = False):
     """Sorts ``keys`` in place; returns the qms_stats fields as a dict (or
     None with ``wait=False``: the sort is only enqueued on the stream).
 
@@ -184,11 +185,13 @@ def qms_sort(keys, pivot: str = "m3", count_cmps: bool = False, stream=None, dty
     runs the rounds from the host); ``host_driven`` selects that driver
     without profiling.  ``side``: "fig3" (Fig. 3's rule, full-size buffer) or
     "larger" (Mergesort the larger side with a half-size buffer when it
-    fits)."""
+    fits).  ``spin_limit`` bounds the device waits of the overlapped merge
+    (polls of one flag; 0 = default); ``test_withhold`` is the failure-test
+    hook QMS_FLAG_TEST_WITHHOLD."""
     code = _check_keys(keys, dtype)
     flags = ((QMS_FLAG_HOST_DRIVEN if host_driven else 0) | (0 if wait else QMS_FLAG_ASYNC)
-             | SIDES[side])
-    opt = _options(pivot, count_cmps, profile, flags)
+             | SIDES[side] | (QMS_FLAG_TEST_WITHHOLD if test_withhold else 0))
+    opt = _options(pivot, count_cmps, profile, flags, spin_limit)
     st = qms_stats()
     rc = lib().qms_sort(ctypes.c_void_p(keys.data_ptr()), keys.numel(), code, ctypes.byref(opt),
                         _stream(stream), ctypes.byref(st) if wait else None)
@@ -198,17 +201,19 @@ def qms_sort(keys, pivot: str = "m3", count_cmps: bool = False, stream=None, dty
 
 def qms_sort_pairs(keys, vals, pivot: str = "m3", count_cmps: bool = False, stream=None, dtype=None,
                    profile: qms_profile | None = None, host_driven: bool = False,
-                   side: str = "fig3"):
-    """Sorts ``keys`` in place, moving ``vals`` with them; returns stats."""
+                   side: str = "fig3", wait: bool = True):
+    """Sorts ``keys`` in place, moving ``vals`` with them; returns stats (or
+    None with ``wait=False``: the sort is only enqueued on the stream)."""
     code = _check_keys(keys, dtype)
     vp = _check_vals(vals, keys.numel())
     opt = _options(pivot, count_cmps, profile,
-                   (QMS_FLAG_HOST_DRIVEN if host_driven else 0) | SIDES[side])
+                   (QMS_FLAG_HOST_DRIVEN if host_driven else 0) | SIDES[side]
+                   | (0 if wait else QMS_FLAG_ASYNC))
     st = qms_stats()
     rc = lib().qms_sort_pairs(ctypes.c_void_p(keys.data_ptr()), vp, keys.numel(), code,
-                              ctypes.byref(opt), _stream(stream), ctypes.byref(st))
+                              ctypes.byref(opt), _stream(stream), ctypes.byref(st) if wait else None)
     _raise(rc, "qms_sort_pairs")
-    return st.as_dict()
+    return st.as_dict() if wait else None
 
 
 def qms_sort_batched(keys, offsets, vals=None, pivot: str = "m3", count_cmps: bool = False,
