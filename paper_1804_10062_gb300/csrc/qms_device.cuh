@@ -86,25 +86,25 @@ __device__ __forceinline__ int sk_i(int i) {
 }
 __device__ __forceinline__ int sv_i(int i) { return i + (i >> 5); }
 
-// Shared-memory tiles hold LT * V keys: LT = NT (8192 keys) everywhere but
-// in the Mergesort leaves of some key types (LeafCfg).
-template <class K, int LT = NT>
+// Shared-memory tiles hold LT * VV keys: LT = NT threads of VV = V keys
+// (8192 keys) everywhere but in the Mergesort leaves (LeafCfg).
+template <class K, int LT = NT, int VV = V>
 __host__ __device__ constexpr int sk_len() {
-  return LT * V + LT * V / (128 / static_cast<int>(sizeof(K))) + 4;
+  return LT * VV + LT * VV / (128 / static_cast<int>(sizeof(K))) + 4;
 }
-template <int LT = NT>
-__host__ __device__ constexpr int sv_len() { return LT * V + LT * V / 32 + 4; }
+template <int LT = NT, int VV = V>
+__host__ __device__ constexpr int sv_len() { return LT * VV + LT * VV / 32 + 4; }
 
 // Scratch words used by block scans and small per-block tables.
 constexpr int SCRATCH_WORDS = 64;
 
-template <class K, bool HV, int LT = NT>
+template <class K, bool HV, int LT = NT, int VV = V>
 __host__ __device__ constexpr size_t tile_smem_bytes() {
-  return static_cast<size_t>(sk_len<K, LT>()) * sizeof(K) +
-         (HV ? static_cast<size_t>(sv_len<LT>()) * 4 : 0) + SCRATCH_WORDS * 8;
+  return static_cast<size_t>(sk_len<K, LT, VV>()) * sizeof(K) +
+         (HV ? static_cast<size_t>(sv_len<LT, VV>()) * 4 : 0) + SCRATCH_WORDS * 8;
 }
 
-template <class K, bool HV, int LT = NT>
+template <class K, bool HV, int LT = NT, int VV = V>
 struct TileSmem {
   K* k;
   uint32_t* v;
@@ -112,26 +112,35 @@ struct TileSmem {
   __device__ __forceinline__ static TileSmem carve(unsigned char* base) {
     TileSmem s;
     s.k = reinterpret_cast<K*>(base);
-    size_t off = static_cast<size_t>(sk_len<K, LT>()) * sizeof(K);
+    size_t off = static_cast<size_t>(sk_len<K, LT, VV>()) * sizeof(K);
     s.v = HV ? reinterpret_cast<uint32_t*>(base + off) : nullptr;
-    if (HV) off += static_cast<size_t>(sv_len<LT>()) * 4;
+    if (HV) off += static_cast<size_t>(sv_len<LT, VV>()) * 4;
     s.scratch = reinterpret_cast<uint32_t*>(base + off);
     return s;
   }
 };
 
-// Mergesort leaves: LT threads of V keys each.  Keys without payloads use
-// 16384-key leaves (1024 threads; the tile sort needs 32 registers for
-// 4-byte keys, two blocks per SM, and about 53 for 8-byte keys, one block of
-// 139 KB shared memory per SM: the same warps as two 512-thread blocks), which
-// saves one merge level per Mergesort.  With payloads the leaves stay at
-// 8192 keys and are built for two 512-thread blocks per SM (64 registers;
-// for 8-byte keys a few spills, still faster than one block per SM).
+// Mergesort leaves: LT threads of VL keys each.
+//   - 4-byte keys without payloads: 16384-key leaves of 512 threads x 32
+//     keys, two blocks per SM.  Each thread's 32 keys are sorted by a
+//     network in registers, so a leaf needs 9 shared-memory merge rounds
+//     instead of 10, and every merge-path search serves 32 outputs.
+//   - 8-byte keys without payloads: 16384-key leaves of 1024 threads x 16
+//     keys (about 53 registers), one block of 139 KB shared memory per SM.
+//   - With payloads: 8192-key leaves of 512 threads x 16, two blocks per SM
+//     (64 registers; for 8-byte keys a few spills, still faster than one
+//     block per SM).
+// 16384-key leaves save one HBM merge level per Mergesort against 8192.
+#ifndef QMS_LEAF_U32
+#define QMS_LEAF_U32 0  // 0: 512 x 32 keys; 1: 1024 x 32 (32768-key leaves); 2: 1024 x 16
+#endif
 template <class K, bool HV>
 struct LeafCfg {
-  static constexpr int LT = !HV ? 2 * NT : NT;
-  static constexpr int TILE_L = LT * V;
-  static constexpr int MINB = (sizeof(K) == 4 && LT == 2 * NT) || HV ? 2 : 1;  // blocks per SM built for
+  static constexpr bool W32 = sizeof(K) == 4 && !HV;
+  static constexpr int LT = HV ? NT : (W32 && QMS_LEAF_U32 == 0 ? NT : 2 * NT);
+  static constexpr int VL = W32 && QMS_LEAF_U32 != 2 ? 2 * V : V;
+  static constexpr int TILE_L = LT * VL;
+  static constexpr int MINB = (W32 && QMS_LEAF_U32 == 1) ? 1 : ((W32 || HV) ? 2 : 1);  // blocks per SM built for
 };
 
 // ---------------------------------------------------------------------------
@@ -199,22 +208,22 @@ __device__ __forceinline__ void cp_async_wait_all() {
 // ---------------------------------------------------------------------------
 // Tile load / store (striped: item j of thread t is element j*NT + t)
 
-template <class K, bool HV, int LT = NT>
-__device__ __forceinline__ void load_tile_enc(TileSmem<K, HV, LT> s, const K* g, const uint32_t* gv,
+template <class K, bool HV, int LT = NT, int VV = V>
+__device__ __forceinline__ void load_tile_enc(TileSmem<K, HV, LT, VV> s, const K* g, const uint32_t* gv,
                                               int cnt, int xf) {
 #pragma unroll 8
-  for (int j = 0; j < V; ++j) {
+  for (int j = 0; j < VV; ++j) {
     const int i = j * LT + threadIdx.x;
     s.k[sk_i<K>(i)] = (i < cnt) ? enc_key(g[i], xf) : key_max<K>();
     if (HV) s.v[sv_i(i)] = (i < cnt) ? gv[i] : 0xffffffffu;
   }
 }
 
-template <class K, bool HV, int LT = NT>
-__device__ __forceinline__ void store_tile_dec(TileSmem<K, HV, LT> s, K* g, uint32_t* gv, int cnt,
+template <class K, bool HV, int LT = NT, int VV = V>
+__device__ __forceinline__ void store_tile_dec(TileSmem<K, HV, LT, VV> s, K* g, uint32_t* gv, int cnt,
                                                int xf) {
 #pragma unroll
-  for (int j = 0; j < V; ++j) {
+  for (int j = 0; j < VV; ++j) {
     const int i = j * LT + threadIdx.x;
     if (i < cnt) {
       g[i] = dec_key(s.k[sk_i<K>(i)], xf);
@@ -224,14 +233,14 @@ __device__ __forceinline__ void store_tile_dec(TileSmem<K, HV, LT> s, K* g, uint
 }
 
 // Copies cnt elements src -> dst (global to global, no overlap), striped.
-// cnt <= LT * V: each thread issues its loads in batches of V/4 before the
+// cnt <= LT * VV: each thread issues its loads in batches of VV/4 before the
 // matching stores (four round trips, few registers).
-template <class K, bool HV, int LT = NT>
+template <class K, bool HV, int LT = NT, int VV = V>
 __device__ __forceinline__ void copy_elems(K* dst, uint32_t* dv, const K* src, const uint32_t* sv,
                                            int cnt) {
-  constexpr int B = V / 4;
+  constexpr int B = VV / 4;
 #pragma unroll
-  for (int jb = 0; jb < V; jb += B) {
+  for (int jb = 0; jb < VV; jb += B) {
     K t[B];
     uint32_t tv[B];
 #pragma unroll
@@ -302,14 +311,14 @@ __device__ __forceinline__ void serial_merge(const K* sk, int ai, int ae, int bi
 }
 
 // The same merge, with the payloads read along (no source indices kept).
-template <class K, bool HV, bool CNT>
+template <class K, bool HV, bool CNT, int VV = V>
 __device__ __forceinline__ void serial_merge_kv(const K* sk, const uint32_t* sv, int ai, int ae,
-                                                int bi, int be, K (&k)[V], uint32_t (&v)[V],
+                                                int bi, int be, K (&k)[VV], uint32_t (&v)[VV],
                                                 uint64_t& cmp) {
   K ka = sk[sk_i<K>(ai)];
   K kb = sk[sk_i<K>(bi)];
 #pragma unroll
-  for (int j = 0; j < V; ++j) {
+  for (int j = 0; j < VV; ++j) {
     const bool a_ok = ai < ae, b_ok = bi < be;
     if (CNT && a_ok && b_ok) ++cmp;
     const bool tb = b_ok && (!a_ok || kb < ka);
@@ -351,12 +360,12 @@ struct MergeExchangeNet {
 template <int N>
 inline constexpr MergeExchangeNet<N> kNet{};
 
-// Sorts the V register items of one thread with the network (comparator I
+// Sorts the VV register items of one thread with the network (comparator I
 // onwards).
-template <class K, bool HV, int I = 0>
-__device__ __forceinline__ void net_sort(K (&k)[V], uint32_t (&v)[V]) {
-  if constexpr (I < kNet<V>.len) {
-    constexpr int a = kNet<V>.c[I].a, b = kNet<V>.c[I].b;
+template <class K, bool HV, int VV = V, int I = 0>
+__device__ __forceinline__ void net_sort(K (&k)[VV], uint32_t (&v)[VV]) {
+  if constexpr (I < kNet<VV>.len) {
+    constexpr int a = kNet<VV>.c[I].a, b = kNet<VV>.c[I].b;
     if (!HV && sizeof(K) == 4) {
       const K lo = min(k[a], k[b]);
       k[b] = max(k[a], k[b]);
@@ -374,7 +383,7 @@ __device__ __forceinline__ void net_sort(K (&k)[V], uint32_t (&v)[V]) {
         v[b] = y;
       }
     }
-    net_sort<K, HV, I + 1>(k, v);
+    net_sort<K, HV, VV, I + 1>(k, v);
   }
 }
 
@@ -399,42 +408,42 @@ __device__ __forceinline__ void tile_sync(int threads) {
 // 63 comparators for V = 16), then log2(NT) rounds of merge-path merges in
 // shared memory.
 
-template <class K, bool HV, bool CNT, int LT = NT>
-__device__ void block_sort_tile(TileSmem<K, HV, LT> s, uint64_t& cmp, int P = LT) {
+template <class K, bool HV, bool CNT, int LT = NT, int VV = V>
+__device__ void block_sort_tile(TileSmem<K, HV, LT, VV> s, uint64_t& cmp, int P = LT) {
   // P (a power of two <= LT): threads holding data; items beyond the data
-  // are padding keys, so the first P*V items end up sorted.
+  // are padding keys, so the first P*VV items end up sorted.
   const int tid = threadIdx.x;
-  K k[V];
-  uint32_t v[V];
+  K k[VV];
+  uint32_t v[VV];
   __syncthreads();
-  if (tid < P) {  // each thread reads, sorts and writes back its own V keys
+  if (tid < P) {  // each thread reads, sorts and writes back its own VV keys
 #pragma unroll
-    for (int j = 0; j < V; ++j) {
-      k[j] = s.k[sk_i<K>(tid * V + j)];
-      if (HV) v[j] = s.v[sv_i(tid * V + j)];
+    for (int j = 0; j < VV; ++j) {
+      k[j] = s.k[sk_i<K>(tid * VV + j)];
+      if (HV) v[j] = s.v[sv_i(tid * VV + j)];
     }
-    net_sort<K, HV>(k, v);
-    if (CNT) cmp += kNet<V>.len;
+    net_sort<K, HV, VV>(k, v);
+    if (CNT) cmp += kNet<VV>.len;
 #pragma unroll
-    for (int j = 0; j < V; ++j) {
-      s.k[sk_i<K>(tid * V + j)] = k[j];
-      if (HV) s.v[sv_i(tid * V + j)] = v[j];
+    for (int j = 0; j < VV; ++j) {
+      s.k[sk_i<K>(tid * VV + j)] = k[j];
+      if (HV) s.v[sv_i(tid * VV + j)] = v[j];
     }
   }
   tile_sync<LT>(2);
   for (int sp = 1; sp < P; sp <<= 1) {
-    const int L = sp * V;
+    const int L = sp * VV;
     const int g = tid / (2 * sp), r = tid - g * 2 * sp;
     const int a0 = g * 2 * L, b0 = a0 + L;
-    const int d = r * V;
+    const int d = r * VV;
     if (tid < P) {
       const int ia = merge_path_smem<K, CNT>(s.k, a0, L, b0, L, d, cmp);
-      serial_merge_kv<K, HV, CNT>(s.k, s.v, a0 + ia, a0 + L, b0 + d - ia, b0 + L, k, v, cmp);
+      serial_merge_kv<K, HV, CNT, VV>(s.k, s.v, a0 + ia, a0 + L, b0 + d - ia, b0 + L, k, v, cmp);
     }
     tile_sync<LT>(2 * sp);  // the pair's reads are done before its writes
     if (tid < P) {
 #pragma unroll
-      for (int j = 0; j < V; ++j) {
+      for (int j = 0; j < VV; ++j) {
         s.k[sk_i<K>(a0 + d + j)] = k[j];
         if (HV) s.v[sv_i(a0 + d + j)] = v[j];
       }
@@ -444,10 +453,11 @@ __device__ void block_sort_tile(TileSmem<K, HV, LT> s, uint64_t& cmp, int P = LT
   __syncthreads();  // the whole sorted tile is visible to the block
 }
 
-// Smallest power of two P with P * V >= cnt (cnt <= TILE).
+// Smallest power of two P with P * VV >= cnt.
+template <int VV = V>
 __device__ __forceinline__ int threads_for(int cnt) {
   int P = 1;
-  while (P * V < cnt) P <<= 1;
+  while (P * VV < cnt) P <<= 1;
   return P;
 }
 
@@ -455,26 +465,26 @@ __device__ __forceinline__ int threads_for(int cnt) {
 // are written to buf[0, cnt) and buf's old contents move to g[0, cnt) (the
 // Mergesort leaf "X then swap into the target", Fig. 3 msort); otherwise the
 // tile is sorted in place.
-template <class K, bool HV, bool CNT, int LT = NT>
-__device__ __forceinline__ void leaf_sort_tile(TileSmem<K, HV, LT> s, K* g, uint32_t* gv, K* buf, uint32_t* bufv,
+template <class K, bool HV, bool CNT, int LT = NT, int VV = V>
+__device__ __forceinline__ void leaf_sort_tile(TileSmem<K, HV, LT, VV> s, K* g, uint32_t* gv, K* buf, uint32_t* bufv,
                                int cnt, int xf, uint64_t& cmp) {
-  const int P = threads_for(cnt);
+  const int P = threads_for<VV>(cnt);
   __syncthreads();
   if (P == LT) {
-    load_tile_enc<K, HV, LT>(s, g, gv, cnt, xf);
+    load_tile_enc<K, HV, LT, VV>(s, g, gv, cnt, xf);
   } else {
-    for (int i = threadIdx.x; i < P * V; i += LT) {
+    for (int i = threadIdx.x; i < P * VV; i += LT) {
       s.k[sk_i<K>(i)] = (i < cnt) ? enc_key(g[i], xf) : key_max<K>();
       if (HV) s.v[sv_i(i)] = (i < cnt) ? gv[i] : 0xffffffffu;
     }
   }
   __syncthreads();
-  if (buf != nullptr) copy_elems<K, HV, LT>(g, gv, buf, bufv, cnt);
-  block_sort_tile<K, HV, CNT, LT>(s, cmp, P);
+  if (buf != nullptr) copy_elems<K, HV, LT, VV>(g, gv, buf, bufv, cnt);
+  block_sort_tile<K, HV, CNT, LT, VV>(s, cmp, P);
   if (buf != nullptr) {
-    store_tile_dec<K, HV, LT>(s, buf, bufv, cnt, xf);
+    store_tile_dec<K, HV, LT, VV>(s, buf, bufv, cnt, xf);
   } else {
-    store_tile_dec<K, HV, LT>(s, g, gv, cnt, xf);
+    store_tile_dec<K, HV, LT, VV>(s, g, gv, cnt, xf);
   }
 }
 

@@ -536,12 +536,12 @@ __global__ void __launch_bounds__(MBT, MergeCfg<K, HV>::MINB) k_g_ovl_merge(DSta
 
 template <class K, bool HV, bool CNT>
 __global__ void __launch_bounds__(LeafCfg<K, HV>::LT, LeafCfg<K, HV>::MINB) k_g_leaf(DState* S) {
-  constexpr int LT = LeafCfg<K, HV>::LT, TL = LeafCfg<K, HV>::TILE_L;
+  constexpr int LT = LeafCfg<K, HV>::LT, TL = LeafCfg<K, HV>::TILE_L, VL = LeafCfg<K, HV>::VL;
   count_launch(S);
   DState& s = *S;
   if (!s.active || s.m <= 1) return;
   extern __shared__ __align__(16) unsigned char smem[];
-  const auto sm = TileSmem<K, HV, LT>::carve(smem);
+  const auto sm = TileSmem<K, HV, LT, VL>::carve(smem);
   uint64_t cmp = 0;
   const uint64_t m = s.m, P = s.P, Bb = s.Bb;
   const bool to_buf = s.to_buf != 0;
@@ -550,7 +550,7 @@ __global__ void __launch_bounds__(LeafCfg<K, HV>::LT, LeafCfg<K, HV>::MINB) k_g_
   for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const uint64_t off = t * TL;
     const int cnt = static_cast<int>((m - off) < static_cast<uint64_t>(TL) ? (m - off) : TL);
-    leaf_sort_tile<K, HV, CNT, LT>(sm, keys + P + off, HV ? s.vals + P + off : nullptr,
+    leaf_sort_tile<K, HV, CNT, LT, VL>(sm, keys + P + off, HV ? s.vals + P + off : nullptr,
                                    to_buf ? keys + Bb + off : nullptr,
                                    (HV && to_buf) ? s.vals + Bb + off : nullptr, cnt, s.xf, cmp);
   }
@@ -624,16 +624,16 @@ __global__ void k_g_end(DState* S, cudaGraphConditionalHandle h_round) {
 
 template <class K, bool HV, bool CNT>
 __global__ void __launch_bounds__(LeafCfg<K, HV>::LT) k_g_final(DState* S) {
-  constexpr int LT = LeafCfg<K, HV>::LT;
+  constexpr int LT = LeafCfg<K, HV>::LT, VL = LeafCfg<K, HV>::VL;
   count_launch(S);
   DState& s = *S;
   if (s.desc->err || s.e - s.b <= 1) return;
   extern __shared__ __align__(16) unsigned char smem[];
-  const auto sm = TileSmem<K, HV, LT>::carve(smem);
+  const auto sm = TileSmem<K, HV, LT, VL>::carve(smem);
   uint64_t cmp = 0;
   const uint64_t b = s.b;
   K* keys = static_cast<K*>(s.keys);
-  leaf_sort_tile<K, HV, CNT, LT>(sm, keys + b, HV ? s.vals + b : nullptr, nullptr, nullptr,
+  leaf_sort_tile<K, HV, CNT, LT, VL>(sm, keys + b, HV ? s.vals + b : nullptr, nullptr, nullptr,
                                  static_cast<int>(s.e - b), s.xf, cmp);
   if (CNT) flush_count(cmp, &s.desc->cmp);
 }

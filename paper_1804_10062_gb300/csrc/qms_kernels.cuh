@@ -67,9 +67,9 @@ template <class K, bool HV, bool CNT>
 __global__ void __launch_bounds__(LeafCfg<K, HV>::LT, LeafCfg<K, HV>::MINB) k_leaf_sort(K* keys, uint32_t* vals, uint64_t P,
                                                                   uint64_t m, uint64_t Bb, int to_buf,
                                                                   int xf, Desc* desc) {
-  constexpr int LT = LeafCfg<K, HV>::LT, TL = LeafCfg<K, HV>::TILE_L;
+  constexpr int LT = LeafCfg<K, HV>::LT, TL = LeafCfg<K, HV>::TILE_L, VL = LeafCfg<K, HV>::VL;
   extern __shared__ __align__(16) unsigned char smem[];
-  const auto s = TileSmem<K, HV, LT>::carve(smem);
+  const auto s = TileSmem<K, HV, LT, VL>::carve(smem);
   uint64_t cmp = 0;
   const uint64_t ntiles = (m + TL - 1) / TL;
   for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(LeafCfg<K, HV>::LT, LeafCfg<K, HV>::MINB) k_le
     uint32_t* gv = HV ? vals + P + off : nullptr;
     K* b = to_buf ? keys + Bb + off : nullptr;
     uint32_t* bv = (HV && to_buf) ? vals + Bb + off : nullptr;
-    leaf_sort_tile<K, HV, CNT, LT>(s, g, gv, b, bv, cnt, xf, cmp);
+    leaf_sort_tile<K, HV, CNT, LT, VL>(s, g, gv, b, bv, cnt, xf, cmp);
   }
   if (CNT) flush_count(cmp, &desc->cmp);
 }

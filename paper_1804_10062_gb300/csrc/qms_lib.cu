@@ -190,7 +190,8 @@ class Sorter {
  public:
   Sorter(K* keys, uint32_t* vals, int xf, cudaStream_t st, Workspace& ws, Profiler& prof)
       : keys_(keys), vals_(vals), xf_(xf), st_(st), ws_(ws), prof_(prof) {
-    allow_smem(k_leaf_sort<K, HV, CNT>, tile_smem_bytes<K, HV, LeafCfg<K, HV>::LT>());
+    allow_smem(k_leaf_sort<K, HV, CNT>,
+               tile_smem_bytes<K, HV, LeafCfg<K, HV>::LT, LeafCfg<K, HV>::VL>());
     allow_smem(k_pivot_sample<K, HV, CNT>, tile_smem_bytes<K, true>());
   }
 
@@ -209,7 +210,7 @@ class Sorter {
     using LC = LeafCfg<K, HV>;
     const uint64_t nt = (m + LC::TILE_L - 1) / LC::TILE_L;
     prof_.begin(st_);
-    k_leaf_sort<K, HV, CNT><<<grid_of(nt), LC::LT, tile_smem_bytes<K, HV, LC::LT>(), st_>>>(
+    k_leaf_sort<K, HV, CNT><<<grid_of(nt), LC::LT, tile_smem_bytes<K, HV, LC::LT, LC::VL>(), st_>>>(
         keys_, vals_, P, m, Bb, to_buf ? 1 : 0, xf_, ws_.desc);
     prof_.end(st_, QMS_K_LEAF, (to_buf ? 4 : 2) * m * ES);
     launched();
@@ -519,7 +520,7 @@ class GraphRunner {
     ck(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     using LC = LeafCfg<K, HV>;
     const size_t tsm = tile_smem_bytes<K, HV>(), tsm_s = tile_smem_bytes<K, true>();
-    const size_t tsm_l = tile_smem_bytes<K, HV, LC::LT>();
+    const size_t tsm_l = tile_smem_bytes<K, HV, LC::LT, LC::VL>();
     allow_smem(k_g_leaf<K, HV, CNT>, tsm_l);
     allow_smem(k_g_final<K, HV, CNT>, tsm_l);
     allow_smem(k_g_pivot_sample<K, HV, CNT>, tsm_s);
