@@ -260,6 +260,15 @@ def bench_batched(args, q, torch, np):
     doff = torch.from_numpy(off.view(np.int64)).cuda()
     out = {"segments": nseg, "keys": n, "lengths": "floor(exp(U(ln 16, ln 65536)))"}
     peak, _ = measured_peak_hbm()
+    # Autotune the per-bin kernel configurations on this GPU (4-byte keys
+    # without payloads: uint32 and float32 share the plan), untimed.
+    t0 = time.perf_counter()
+    report = q.qms_batched_autotune("u32")
+    plan, tuned = q.qms_batched_get_plan("u32")
+    out["autotune"] = {"seconds": time.perf_counter() - t0, "tuned": tuned,
+                       "plan": {"bin_%d_(%d..%d keys)" % (b, (1 << (b - 1)) + 1 if b else 1, 1 << b): c
+                                for b, c in enumerate(plan)},
+                       "report": report.strip().splitlines()}
     for dt in ("u32", "f32"):
         k = gen.keys("uniform", dt, n, 1)
         src = torch.from_numpy(k.view(np.int32)).cuda()

@@ -158,6 +158,60 @@ int qms_sort_pairs(void* d_keys, uint32_t* d_vals, size_t n, int dtype, const qm
 int qms_sort_batched(void* d_keys, uint32_t* d_vals, const uint64_t* d_offsets, size_t nseg,
                      int dtype, const qms_options* opt, void* stream, qms_stats* stats);
 
+/* ---- Batched form: plan and autotuner ------------------------------------
+ * qms_sort_batched maps every segment length bin b (segments of
+ * (2^(b-1), 2^b] keys, b < QMS_BATCH_BINS; b = 0 holds single keys) to a
+ * kernel configuration.  Configurations QMS_BCFG_G32 .. QMS_BCFG_G512W sort
+ * a segment that fits their tile with the base case (Fig. 3's driver never
+ * partitions a range of one tile or less) inside one group of threads --
+ * a warp, or a block-sized group -- several groups per block;
+ * QMS_BCFG_QMS runs the QuickMergesort rounds of a segment in one block.
+ * Segments longer than 2^(QMS_BATCH_BINS-1) keys always take the rounds.
+ * The default plan takes, per bin, the smallest group whose tile holds it.
+ * The autotuner times every admissible configuration per bin on the
+ * current GPU and keeps the fastest; the plan is stored per key width,
+ * payload and SM count in the JSON file
+ *   $QMS_AUTOTUNE_DIR/batched_k<4|8>_v<0|1>_sm<count>.json
+ * (default directory $HOME/.cache/qms_gb300), which later processes read on
+ * their first batched call.  The paper has no batched form. */
+#define QMS_BATCH_BINS 15
+#define QMS_BCFG_G32 0    /* one warp, 16 keys per thread: up to 512 keys   */
+#define QMS_BCFG_G64 1    /* 64 threads x 16: up to 1024                    */
+#define QMS_BCFG_G128 2   /* 128 x 16: up to 2048                           */
+#define QMS_BCFG_G256 3   /* 256 x 16: up to 4096                           */
+#define QMS_BCFG_G512 4   /* 512 x 16: up to 8192                           */
+#define QMS_BCFG_G256W 5  /* 256 x 32: up to 8192 (4-byte keys, no payload) */
+#define QMS_BCFG_G512W 6  /* 512 x 32: up to 16384 (4-byte keys, no payload)*/
+#define QMS_BCFG_QMS 7    /* one block per segment, QuickMergesort rounds   */
+
+/* Times every configuration per length bin on the current device (about a
+ * second of GPU work), installs the fastest plan for (dtype's key width,
+ * with_payload) on this device and writes the plan file.  report (may be
+ * NULL) receives a text table of the timings, truncated to report_len.
+ * Errors: QMS_EINVAL, QMS_ENOMEM, QMS_ECUDA, QMS_EINTERNAL. */
+int qms_batched_autotune(int dtype, int with_payload, void* stream, char* report,
+                         size_t report_len);
+
+/* The plan in use on the current device (loading the plan file on first
+ * use): cfg[b] for b < nbins (bins beyond QMS_BATCH_BINS read as
+ * QMS_BCFG_QMS); *tuned = 1 when it came from the autotuner or its file. */
+int qms_batched_get_plan(int dtype, int with_payload, int* cfg, int nbins, int* tuned);
+
+/* Installs a plan for the current device (nbins == QMS_BATCH_BINS); every
+ * entry must exist for these keys and hold its bin.  QMS_EINVAL otherwise. */
+int qms_batched_set_plan(int dtype, int with_payload, const int* cfg, int nbins);
+
+/* Host-only helpers (no GPU): read a plan file written for sm_count SMs
+ * into cfg (QMS_EAGAIN, with the default plan in cfg, when the file is
+ * missing or was written for other keys or another SM count), and write
+ * one (ns_per_key may be NULL). */
+int qms_batched_plan_read(const char* path, int dtype, int with_payload, int sm_count, int* cfg,
+                          int nbins);
+int qms_batched_plan_write(const char* path, int dtype, int with_payload, int sm_count,
+                           const int* cfg, const double* ns_per_key, int nbins);
+/* Static name of a configuration ("group32x16", ..., "block_qms"). */
+const char* qms_batched_config_name(int cfg);
+
 /* ---- Served form --------------------------------------------------------
  * A request server with continuous batching (no counterpart in the paper,
  * which sorts one array; each request is one QuickMergesort).  Requests are

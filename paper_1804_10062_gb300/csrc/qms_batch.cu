@@ -1,0 +1,83 @@
+// Group kernels of the batched form (see qms_batch.cuh), in a translation
+// unit of their own so that they compile beside the rest of the library.
+
+#include "qms_batch.cuh"
+#include "qms_batch.h"
+#include "qms_host.h"
+
+namespace qms {
+
+int batch_cfg_threads(int c) {
+  static const int t[BC_COUNT] = {32, 64, 128, 256, 512, 256, 512, NT};
+  return (c >= 0 && c < BC_COUNT) ? t[c] : 0;
+}
+int batch_cfg_keys_per_thread(int c) {
+  static const int v[BC_COUNT] = {V, V, V, V, V, 2 * V, 2 * V, V};
+  return (c >= 0 && c < BC_COUNT) ? v[c] : 0;
+}
+const char* batch_cfg_name(int c) {
+  static const char* n[BC_COUNT] = {"group32x16", "group64x16", "group128x16", "group256x16",
+                                    "group512x16", "group256x32", "group512x32", "block_qms"};
+  return (c >= 0 && c < BC_COUNT) ? n[c] : "invalid";
+}
+
+namespace {
+
+template <class K, bool HV, bool CNT, int GT, int VV>
+cudaError_t launch_one(void* keys, uint32_t* vals, const uint64_t* offsets, const uint32_t* order,
+                       uint32_t nseg, unsigned int* ticket, int xf, Desc* desc, cudaStream_t st) {
+  constexpr size_t smem = group_smem_bytes<K, HV, GT, VV>() * (NT / GT);
+  auto f = k_batched_group<K, HV, CNT, GT, VV>;
+  cudaError_t e = smem_attr(reinterpret_cast<const void*>(f), smem);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0, occ = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, f, NT, smem)) != cudaSuccess) return e;
+  const uint64_t groups = (nseg + (NT / GT) - 1) / (NT / GT);
+  const uint64_t resident = static_cast<uint64_t>(sms) * (occ > 0 ? occ : 1);
+  const unsigned grid = static_cast<unsigned>(groups < resident ? (groups > 0 ? groups : 1) : resident);
+  f<<<grid, NT, smem, st>>>(static_cast<K*>(keys), vals, offsets, order, nseg, ticket, xf, desc);
+  return cudaGetLastError();
+}
+
+template <class K, bool HV, bool CNT>
+cudaError_t launch_typed(int c, void* keys, uint32_t* vals, const uint64_t* offsets,
+                         const uint32_t* order, uint32_t nseg, unsigned int* ticket, int xf,
+                         Desc* desc, cudaStream_t st) {
+  switch (c) {
+    case BC_G32: return launch_one<K, HV, CNT, 32, V>(keys, vals, offsets, order, nseg, ticket, xf, desc, st);
+    case BC_G64: return launch_one<K, HV, CNT, 64, V>(keys, vals, offsets, order, nseg, ticket, xf, desc, st);
+    case BC_G128: return launch_one<K, HV, CNT, 128, V>(keys, vals, offsets, order, nseg, ticket, xf, desc, st);
+    case BC_G256: return launch_one<K, HV, CNT, 256, V>(keys, vals, offsets, order, nseg, ticket, xf, desc, st);
+    case BC_G512: return launch_one<K, HV, CNT, 512, V>(keys, vals, offsets, order, nseg, ticket, xf, desc, st);
+    default: break;
+  }
+  if constexpr (sizeof(K) == 4 && !HV) {
+    if (c == BC_G256W)
+      return launch_one<K, HV, CNT, 256, 2 * V>(keys, vals, offsets, order, nseg, ticket, xf, desc, st);
+    if (c == BC_G512W)
+      return launch_one<K, HV, CNT, 512, 2 * V>(keys, vals, offsets, order, nseg, ticket, xf, desc, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+cudaError_t launch_group_cfg(int c, int ksize, bool hv, bool cnt, void* keys, uint32_t* vals,
+                             const uint64_t* offsets, const uint32_t* order, uint32_t nseg,
+                             unsigned int* ticket, int xf, Desc* desc, cudaStream_t st) {
+  if (nseg == 0) return cudaSuccess;
+  if (ksize == 8) {
+    if (hv) return cnt ? launch_typed<uint64_t, true, true>(c, keys, vals, offsets, order, nseg, ticket, xf, desc, st)
+                       : launch_typed<uint64_t, true, false>(c, keys, vals, offsets, order, nseg, ticket, xf, desc, st);
+    return cnt ? launch_typed<uint64_t, false, true>(c, keys, vals, offsets, order, nseg, ticket, xf, desc, st)
+               : launch_typed<uint64_t, false, false>(c, keys, vals, offsets, order, nseg, ticket, xf, desc, st);
+  }
+  if (hv) return cnt ? launch_typed<uint32_t, true, true>(c, keys, vals, offsets, order, nseg, ticket, xf, desc, st)
+                     : launch_typed<uint32_t, true, false>(c, keys, vals, offsets, order, nseg, ticket, xf, desc, st);
+  return cnt ? launch_typed<uint32_t, false, true>(c, keys, vals, offsets, order, nseg, ticket, xf, desc, st)
+             : launch_typed<uint32_t, false, false>(c, keys, vals, offsets, order, nseg, ticket, xf, desc, st);
+}
+
+}  // namespace qms

@@ -14,6 +14,9 @@
 namespace qms {
 
 constexpr int CTA_MAX_TILES = 64;  // segments up to 64 * 8192 keys
+#ifndef QMS_CTA_MINB
+#define QMS_CTA_MINB 2  // blocks per SM the block-per-segment kernel is built for
+#endif
 
 // Out-of-line copies of the tile routines for the block-scoped path: the
 // whole QuickMergesort of a segment lives in one kernel, and separate
@@ -23,10 +26,27 @@ __device__ __noinline__ uint32_t part_local_tile_call(TileSmem<K, HV> s, K* g, u
                                                       K piv, bool le, int xf, uint64_t& cmp) {
   return part_local_tile<K, HV, CNT>(s, g, gv, cnt, piv, le, xf, cmp);
 }
+// Leaves of the block-scoped path: 512 threads of CtaLeaf::VL keys, so
+// 4-byte keys without payloads sort 16384-key leaves (one merge level and
+// about one round fewer per segment than 8192-key leaves); the tile shares
+// the block's shared memory with the 8192-key partition and merge tiles.
+template <class K, bool HV>
+struct CtaLeaf {
+  static constexpr int VL = (sizeof(K) == 4 && !HV) ? 2 * V : V;
+  static constexpr int TL = NT * VL;
+};
+template <class K, bool HV>
+__host__ __device__ constexpr size_t cta_smem_bytes() {
+  return tile_smem_bytes<K, HV, NT, CtaLeaf<K, HV>::VL>() > tile_smem_bytes<K, HV>()
+             ? tile_smem_bytes<K, HV, NT, CtaLeaf<K, HV>::VL>()
+             : tile_smem_bytes<K, HV>();
+}
+
 template <class K, bool HV, bool CNT>
-__device__ __noinline__ void leaf_sort_tile_call(TileSmem<K, HV> s, K* g, uint32_t* gv, K* buf,
+__device__ __noinline__ void leaf_sort_tile_call(unsigned char* smem, K* g, uint32_t* gv, K* buf,
                                                  uint32_t* bufv, int cnt, int xf, uint64_t& cmp) {
-  leaf_sort_tile<K, HV, CNT>(s, g, gv, buf, bufv, cnt, xf, cmp);
+  constexpr int VL = CtaLeaf<K, HV>::VL;
+  leaf_sort_tile<K, HV, CNT, NT, VL>(TileSmem<K, HV, NT, VL>::carve(smem), g, gv, buf, bufv, cnt, xf, cmp);
 }
 template <class K, bool HV, bool CNT>
 __device__ __noinline__ void merge_tile_call(TileSmem<K, HV> s, K* keys, uint32_t* vals, uint64_t X,
@@ -92,36 +112,39 @@ __device__ __noinline__ uint64_t cta_partition(TileSmem<K, HV> s, CtaState& cs, 
 
 // Mergesort of P[0, m) with the disjoint buffer Bb[0, m) (full-buffer form).
 template <class K, bool HV, bool CNT>
-__device__ __noinline__ void cta_mergesort(TileSmem<K, HV> s, CtaState& cs, K* keys, uint32_t* vals, uint64_t P,
-                              uint64_t m, uint64_t Bb, int xf, uint64_t& cmp) {
+__device__ __noinline__ void cta_mergesort(TileSmem<K, HV> s, unsigned char* smem, CtaState& cs, K* keys,
+                                           uint32_t* vals, uint64_t P, uint64_t m, uint64_t Bb, int xf,
+                                           uint64_t& cmp) {
   constexpr uint64_t ES = sizeof(K) + (HV ? 4 : 0);
+  constexpr uint64_t TL = CtaLeaf<K, HV>::TL;
   if (m <= 1) return;
-  if (m <= static_cast<uint64_t>(TILE)) {
-    leaf_sort_tile_call<K, HV, CNT>(s, keys + P, HV ? vals + P : nullptr, nullptr, nullptr,
+  if (m <= TL) {
+    leaf_sort_tile_call<K, HV, CNT>(smem, keys + P, HV ? vals + P : nullptr, nullptr, nullptr,
                                static_cast<int>(m), xf, cmp);
     if (threadIdx.x == 0) cs.bytes += 2 * m * ES;
     __syncthreads();
     return;
   }
-  const uint32_t leaves = static_cast<uint32_t>((m + TILE - 1) / TILE);
+  const uint32_t leaves = static_cast<uint32_t>((m + TL - 1) / TL);
   int levels = 0;
   while ((1u << levels) < leaves) ++levels;
   const bool to_buf = (levels & 1) != 0;
   for (uint32_t t = 0; t < leaves; ++t) {
-    const uint64_t off = static_cast<uint64_t>(t) * TILE;
-    const int cnt = static_cast<int>((m - off) < static_cast<uint64_t>(TILE) ? (m - off) : TILE);
-    leaf_sort_tile_call<K, HV, CNT>(s, keys + P + off, HV ? vals + P + off : nullptr,
+    const uint64_t off = static_cast<uint64_t>(t) * TL;
+    const int cnt = static_cast<int>((m - off) < TL ? (m - off) : TL);
+    leaf_sort_tile_call<K, HV, CNT>(smem, keys + P + off, HV ? vals + P + off : nullptr,
                                to_buf ? keys + Bb + off : nullptr,
                                (HV && to_buf) ? vals + Bb + off : nullptr, cnt, xf, cmp);
   }
   uint64_t X = to_buf ? Bb : P, Y = to_buf ? P : Bb;
+  const uint32_t mtiles = static_cast<uint32_t>((m + TILE - 1) / TILE);  // merge tiles of 8192 outputs
   for (int l = 0; l < levels; ++l) {
-    const uint64_t L = static_cast<uint64_t>(TILE) << l;
+    const uint64_t L = TL << l;
     __syncthreads();
-    for (uint32_t t = threadIdx.x >> 5; t < leaves; t += NWARP)
+    for (uint32_t t = threadIdx.x >> 5; t < mtiles; t += NWARP)
       merge_split_warp<K, CNT>(keys, X, m, L, t, xf, cs.splits, cmp);
     __syncthreads();
-    for (uint32_t t = 0; t < leaves; ++t)
+    for (uint32_t t = 0; t < mtiles; ++t)
       merge_tile_call<K, HV, CNT>(s, keys, vals, X, Y, m, L, t, cs.splits, xf, cmp);
     const uint64_t x = X;
     X = Y;
@@ -273,10 +296,10 @@ __device__ __noinline__ void cta_pivot_mom(CtaState& cs, K* keys, uint32_t* vals
 
 // QuickMergesort of keys[b, e) by one block (pivot: QMS_PIVOT_* code).
 template <class K, bool HV, bool CNT>
-__device__ void cta_qms(TileSmem<K, HV> s, CtaState& cs, K* keys, uint32_t* vals, uint64_t b,
-                        uint64_t e, int pivot, int xf, uint64_t& cmp) {
+__device__ void cta_qms(TileSmem<K, HV> s, unsigned char* smem, CtaState& cs, K* keys, uint32_t* vals,
+                        uint64_t b, uint64_t e, int pivot, int xf, uint64_t& cmp) {
   bool mom_next = false;
-  while (e - b > static_cast<uint64_t>(TILE)) {
+  while (e - b > static_cast<uint64_t>(CtaLeaf<K, HV>::TL)) {
     if (cs.err) return;
     const uint64_t nn = e - b;
     const bool mom = pivot == 2 || (pivot == 3 && mom_next);
@@ -304,15 +327,15 @@ __device__ void cta_qms(TileSmem<K, HV> s, CtaState& cs, K* keys, uint32_t* vals
     const uint64_t nl = k - b, nr = e - rb;
     const bool left = (eq == 0) ? (k < b + nn / 2) : (nl <= nr);
     if (left) {
-      cta_mergesort<K, HV, CNT>(s, cs, keys, vals, b, nl, rb, xf, cmp);
+      cta_mergesort<K, HV, CNT>(s, smem, cs, keys, vals, b, nl, rb, xf, cmp);
       b = rb;
     } else {
-      cta_mergesort<K, HV, CNT>(s, cs, keys, vals, rb, nr, b, xf, cmp);
+      cta_mergesort<K, HV, CNT>(s, smem, cs, keys, vals, rb, nr, b, xf, cmp);
       e = k;
     }
   }
   if (e - b > 1) {
-    leaf_sort_tile_call<K, HV, CNT>(s, keys + b, HV ? vals + b : nullptr, nullptr, nullptr,
+    leaf_sort_tile_call<K, HV, CNT>(smem, keys + b, HV ? vals + b : nullptr, nullptr, nullptr,
                                static_cast<int>(e - b), xf, cmp);
     if (threadIdx.x == 0) cs.bytes += 2 * (e - b) * (sizeof(K) + (HV ? 4 : 0));
   }
@@ -323,7 +346,7 @@ __device__ void cta_qms(TileSmem<K, HV> s, CtaState& cs, K* keys, uint32_t* vals
 // segment (in the host's longest-first order) from an atomic ticket and sorts
 // it alone.
 template <class K, bool HV, bool CNT>
-__global__ void __launch_bounds__(NT) k_batched(K* keys, uint32_t* vals, const uint64_t* offsets,
+__global__ void __launch_bounds__(NT, QMS_CTA_MINB) k_batched(K* keys, uint32_t* vals, const uint64_t* offsets,
                                                 const uint32_t* order, uint32_t nseg,
                                                 unsigned int* ticket, int pivot, int xf,
                                                 Desc* desc) {
@@ -342,7 +365,7 @@ __global__ void __launch_bounds__(NT) k_batched(K* keys, uint32_t* vals, const u
     const uint32_t t = cs.seg;
     if (t >= nseg || cs.err) break;
     const uint32_t sg = order[t];
-    cta_qms<K, HV, CNT>(s, cs, keys, vals, offsets[sg], offsets[sg + 1], pivot, xf, cmp);
+    cta_qms<K, HV, CNT>(s, smem, cs, keys, vals, offsets[sg], offsets[sg + 1], pivot, xf, cmp);
   }
   if (CNT) flush_count(cmp, &desc->cmp);
   if (threadIdx.x == 0) {
@@ -361,7 +384,7 @@ struct SegDesc {
 };
 
 template <class K, bool CNT>
-__global__ void __launch_bounds__(NT) k_batched_ptrs(const SegDesc* segs, uint32_t nseg,
+__global__ void __launch_bounds__(NT, QMS_CTA_MINB) k_batched_ptrs(const SegDesc* segs, uint32_t nseg,
                                                      unsigned int* ticket, int pivot, Desc* desc) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ CtaState cs;
@@ -378,7 +401,7 @@ __global__ void __launch_bounds__(NT) k_batched_ptrs(const SegDesc* segs, uint32
     const uint32_t t = cs.seg;
     if (t >= nseg || cs.err) break;
     const SegDesc sd = segs[t];
-    cta_qms<K, false, CNT>(s, cs, static_cast<K*>(sd.keys), nullptr, 0, sd.n, pivot, sd.xf, cmp);
+    cta_qms<K, false, CNT>(s, smem, cs, static_cast<K*>(sd.keys), nullptr, 0, sd.n, pivot, sd.xf, cmp);
   }
   if (CNT) flush_count(cmp, &desc->cmp);
   if (threadIdx.x == 0) {

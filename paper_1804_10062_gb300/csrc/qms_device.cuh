@@ -932,65 +932,76 @@ constexpr int EXW = 16;                // ranks per lane
 constexpr uint64_t EXJ = 32ull * EXW;  // ranks per warp
 constexpr int EXB = 128;               // threads per exchange block (several blocks per SM)
 
+
 // Swaps the misplaced pairs of ranks [jw, jw + EXJ) (jw a multiple of EXJ).
 // wtl/wtr give, per warp, the tile holding its first left / right rank.
-template <class K, bool HV>
+// Positions are kept relative to lo in type P: 32 bits whenever the range
+// is shorter than 2^32 (half the registers of 64-bit positions, so more
+// warps stay resident), 64 bits otherwise.
+template <class K, bool HV, class P = uint32_t>
 __device__ __forceinline__ void exchange_warp(K* keys, uint32_t* vals, uint64_t lo, uint64_t s,
                                               const uint32_t* counts, const uint64_t* pml,
                                               const uint64_t* pmr, const uint32_t* wtl,
                                               const uint32_t* wtr, uint64_t jw, uint64_t mis) {
   const unsigned lane = threadIdx.x & 31u;
+  K* kb = keys + lo;
+  uint32_t* vb = HV ? vals + lo : nullptr;
+  const P sr = static_cast<P>(s - lo);
   uint32_t tl = wtl[jw / EXJ], tr = wtr[jw / EXJ];
   // Positions first (walking the tiles with their bounds kept in registers),
   // then all loads, then all stores: a lane keeps 2 * EXW loads in flight.
-  uint64_t l_lo = pml[tl], l_hi = pml[tl + 1], l_base = lo + static_cast<uint64_t>(tl) * PT + counts[tl];
+  uint64_t l_lo = pml[tl], l_hi = pml[tl + 1];
+  P l_base = static_cast<P>(tl) * PT + counts[tl];
   uint64_t r_lo = pmr[tr], r_hi = pmr[tr + 1];
-  uint64_t r_base = lo + static_cast<uint64_t>(tr) * PT;
-  if (r_base < s) r_base = s;
-  uint64_t lp[EXW], rp[EXW];
+  P r_base = static_cast<P>(tr) * PT;
+  if (r_base < sr) r_base = sr;
+  // this lane's ranks jw + lane + 32 q exist for q < nq
+  const uint64_t left = mis - jw;
+  const uint64_t nq64 = left > lane ? (left - lane + 31) / 32 : 0;
+  const int nq = nq64 < static_cast<uint64_t>(EXW) ? static_cast<int>(nq64) : EXW;
+  P lp[EXW], rp[EXW];
 #pragma unroll
   for (int q = 0; q < EXW; ++q) {
     const uint64_t j = jw + lane + 32u * q;
-    lp[q] = rp[q] = ~0ull;
-    if (j < mis) {
+    if (q < nq) {
       while (j >= l_hi) {
         ++tl;
         l_lo = l_hi;
         l_hi = pml[tl + 1];
-        l_base = lo + static_cast<uint64_t>(tl) * PT + counts[tl];
+        l_base = static_cast<P>(tl) * PT + counts[tl];
       }
       while (j >= r_hi) {
         ++tr;
         r_lo = r_hi;
         r_hi = pmr[tr + 1];
-        r_base = lo + static_cast<uint64_t>(tr) * PT;
-        if (r_base < s) r_base = s;
+        r_base = static_cast<P>(tr) * PT;
+        if (r_base < sr) r_base = sr;
       }
-      lp[q] = l_base + (j - l_lo);
-      rp[q] = r_base + (j - r_lo);
+      lp[q] = l_base + static_cast<P>(j - l_lo);
+      rp[q] = r_base + static_cast<P>(j - r_lo);
     }
   }
   K a[EXW], b[EXW];
-  uint32_t va[EXW], vb[EXW];
+  uint32_t va[EXW], vb2[EXW];
 #pragma unroll
   for (int q = 0; q < EXW; ++q) {
-    if (lp[q] != ~0ull) {
-      a[q] = keys[lp[q]];
-      b[q] = keys[rp[q]];
+    if (q < nq) {
+      a[q] = kb[lp[q]];
+      b[q] = kb[rp[q]];
       if (HV) {
-        va[q] = vals[lp[q]];
-        vb[q] = vals[rp[q]];
+        va[q] = vb[lp[q]];
+        vb2[q] = vb[rp[q]];
       }
     }
   }
 #pragma unroll
   for (int q = 0; q < EXW; ++q) {
-    if (lp[q] != ~0ull) {
-      keys[lp[q]] = b[q];
-      keys[rp[q]] = a[q];
+    if (q < nq) {
+      kb[lp[q]] = b[q];
+      kb[rp[q]] = a[q];
       if (HV) {
-        vals[lp[q]] = vb[q];
-        vals[rp[q]] = va[q];
+        vb[lp[q]] = vb2[q];
+        vb[rp[q]] = va[q];
       }
     }
   }

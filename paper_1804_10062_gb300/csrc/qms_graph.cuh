@@ -339,19 +339,26 @@ __global__ static void __launch_bounds__(NT) k_g_part_prefix(DState* S) {
   }
 }
 
-template <class K, bool HV>
+// P: uint32_t positions (graphs for arrays shorter than 2^32 keys), else uint64_t.
+template <class K, bool HV, class P>
 __global__ void __launch_bounds__(EXB) k_g_part_exchange(DState* S) {
   count_launch(S);
-  DState& s = *S;
+  const DState& s = *S;
   if (!s.active) return;
+  // the state, read once (the stores to the keys could alias it otherwise)
+  K* const keys = static_cast<K*>(s.keys);
+  uint32_t* const vals = s.vals;
+  const uint32_t* const counts = s.counts;
+  const uint64_t* const pml = reinterpret_cast<const uint64_t*>(s.pml);
+  const uint64_t* const pmr = reinterpret_cast<const uint64_t*>(s.pmr);
+  const uint32_t* const wtl = s.wtl;
+  const uint32_t* const wtr = s.wtr;
   const uint64_t mis = s.desc->mis, lo = s.lo;
   const uint64_t sb = lo + s.desc->L;
   const uint64_t w0 = (blockIdx.x * static_cast<uint64_t>(EXB) + threadIdx.x) >> 5;
   const uint64_t nw = (static_cast<uint64_t>(gridDim.x) * EXB) >> 5;
   for (uint64_t jw = w0 * EXJ; jw < mis; jw += nw * EXJ)
-    exchange_warp<K, HV>(static_cast<K*>(s.keys), s.vals, lo, sb, s.counts,
-                         reinterpret_cast<const uint64_t*>(s.pml), reinterpret_cast<const uint64_t*>(s.pmr),
-                         s.wtl, s.wtr, jw, mis);
+    exchange_warp<K, HV, P>(keys, vals, lo, sb, counts, pml, pmr, wtl, wtr, jw, mis);
 }
 
 template <class K, bool HV>
@@ -559,6 +566,7 @@ __global__ void __launch_bounds__(LeafCfg<K, HV>::LT, LeafCfg<K, HV>::MINB) k_g_
 
 template <class K, bool HV, bool CNT>
 __global__ void __launch_bounds__(256) k_g_split(DState* S) {
+  grid_dep_trigger();  // the merge node may start and load its buffer tiles
   count_launch(S);
   const DState& s = *S;
   uint64_t cmp = 0;
@@ -585,8 +593,10 @@ __global__ void __launch_bounds__(MBT, MergeCfg<K, HV>::MINB)
   for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     __syncthreads();
     merge_level_tile<K, HV, CNT>(static_cast<K*>(s.keys), s.vals, X, Y, m, L,
-                                 reinterpret_cast<const uint64_t*>(s.splits), s.xf, s.desc, t);
+                                 reinterpret_cast<const uint64_t*>(s.splits), s.xf, s.desc, t,
+                                 t == blockIdx.x);
   }
+  grid_dep_wait();  // (blocks without a tile) the split step has finished
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();

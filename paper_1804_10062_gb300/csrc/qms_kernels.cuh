@@ -405,8 +405,11 @@ static __global__ void __launch_bounds__(NT) k_part_prefix(uint64_t lo, uint64_t
 
 // Step 3: exchange the misplaced elements by rank (one warp per chunk of
 // EXJ ranks).
-template <class K, bool HV>
-__global__ void __launch_bounds__(EXB) k_part_exchange(K* keys, uint32_t* vals, uint64_t lo,
+// P: uint32_t positions for ranges shorter than 2^32 keys, else uint64_t.
+// For 4-byte keys without payloads the kernel is built for five blocks per
+// SM (95 registers, no spills; 126 registers and four blocks before).
+template <class K, bool HV, class P>
+__global__ void __launch_bounds__(EXB, (sizeof(K) == 4 && !HV) ? 5 : 1) k_part_exchange(K* keys, uint32_t* vals, uint64_t lo,
                                                        const uint32_t* counts, const uint64_t* pml,
                                                        const uint64_t* pmr, const uint32_t* wtl,
                                                        const uint32_t* wtr, const Desc* desc) {
@@ -415,7 +418,7 @@ __global__ void __launch_bounds__(EXB) k_part_exchange(K* keys, uint32_t* vals, 
   const uint64_t w0 = (blockIdx.x * static_cast<uint64_t>(EXB) + threadIdx.x) >> 5;
   const uint64_t nw = (static_cast<uint64_t>(gridDim.x) * EXB) >> 5;
   for (uint64_t jw = w0 * EXJ; jw < mis; jw += nw * EXJ)
-    exchange_warp<K, HV>(keys, vals, lo, s, counts, pml, pmr, wtl, wtr, jw, mis);
+    exchange_warp<K, HV, P>(keys, vals, lo, s, counts, pml, pmr, wtl, wtr, jw, mis);
 }
 
 // Step 4: the pivot parked at position `parked` moves to its final index

@@ -10,6 +10,7 @@
 // round) to size the Mergesort launches.
 
 #include <cuda_runtime.h>
+#include <sys/stat.h>
 
 #include <algorithm>
 #include <chrono>
@@ -18,6 +19,8 @@
 #include <cstdlib>
 #include <cstring>
 #include <map>
+#include <random>
+#include <string>
 #include <mutex>
 #include <tuple>
 #include <vector>
@@ -26,6 +29,7 @@
 #include "qms_cta.cuh"
 #include "qms_merge.cuh"
 #include "qms_graph.cuh"
+#include "qms_batch.h"
 #include "qms_host.h"
 
 namespace qms {
@@ -139,6 +143,7 @@ struct Workspace {
 class Profiler {
  public:
   explicit Profiler(qms_profile* out) : out_(out) {}
+  bool active() const { return out_ != nullptr; }
   ~Profiler() {
     for (auto& r : recs_) {
       cudaEventDestroy(r.a);
@@ -243,8 +248,7 @@ class Sorter {
           keys_, X, m, L, xf_, ws_.splits, ws_.desc);
       prof_.end(st_, QMS_K_MERGE_SPLIT, 0);
       prof_.begin(st_);
-      k_merge_level3<K, HV, CNT><<<grid_of(mtiles), MBT, 0, st_>>>(keys_, vals_, X, Y, m, L,
-                                                                    ws_.splits, xf_, ws_.desc);
+      launch_merge(X, Y, m, L, mtiles);
       prof_.end(st_, QMS_K_MERGE, 4 * m * ES);
       launched(2);
       std::swap(X, Y);
@@ -343,8 +347,13 @@ class Sorter {
       const uint64_t maxmis = n / 2 + 1;
       const uint64_t per = static_cast<uint64_t>(EXB) * EXW;
       prof_.begin(st_);
-      k_part_exchange<K, HV><<<grid_of((maxmis + per - 1) / per), EXB, 0, st_>>>(
-          keys_, vals_, lo, ws_.counts, ws_.pml, ws_.pmr, ws_.wtl, ws_.wtr, ws_.desc);
+      if (n < (1ull << 32)) {
+        k_part_exchange<K, HV, uint32_t><<<grid_of((maxmis + per - 1) / per), EXB, 0, st_>>>(
+            keys_, vals_, lo, ws_.counts, ws_.pml, ws_.pmr, ws_.wtl, ws_.wtr, ws_.desc);
+      } else {
+        k_part_exchange<K, HV, uint64_t><<<grid_of((maxmis + per - 1) / per), EXB, 0, st_>>>(
+            keys_, vals_, lo, ws_.counts, ws_.pml, ws_.pmr, ws_.wtl, ws_.wtr, ws_.desc);
+      }
       prof_.end(st_, QMS_K_PART_EXCHANGE, 0);  // bytes added once mis is known
       launched(3);
     } else {
@@ -416,6 +425,24 @@ class Sorter {
 
   void launched(int c = 1) { launches += c; }
 
+  // One swap-merge level; unless its time is being profiled, with a
+  // programmatic dependency on the split step before it (the merge blocks
+  // start early and load their buffer tiles while the split runs).
+  void launch_merge(uint64_t X, uint64_t Y, uint64_t m, uint64_t L, uint64_t mtiles) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(grid_of(mtiles));
+    cfg.blockDim = dim3(MBT);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st_;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = (prof_.active() || std::getenv("QMS_NO_PDL")) ? 0 : 1;
+    ck(cudaLaunchKernelEx(&cfg, k_merge_level3<K, HV, CNT>, keys_, vals_, X, Y, m, L,
+                          static_cast<const uint64_t*>(ws_.splits), xf_, ws_.desc));
+  }
+
  private:
   static unsigned grid_of(uint64_t blocks) {
     if (blocks < 1) blocks = 1;
@@ -452,6 +479,7 @@ struct GraphInst {
   cudaEvent_t done = nullptr;    // recorded after the instance's last launch
   cudaStream_t last = nullptr;   // stream of that launch
   bool used = false;             // launched at least once
+  bool wide = false;             // built for arrays of 2^32 keys or more
   bool busy = false;             // a call is setting it up on the host
 };
 
@@ -460,9 +488,13 @@ inline size_t graph_ws_bytes(uint64_t cap) { return WsLayout(cap).total; }
 std::mutex g_graph_mu;
 std::map<std::tuple<int, int, int, int, int, int>, std::vector<GraphInst*>> g_graphs;
 
+// Adds a kernel node after `dep`.  programmatic: the edge is a programmatic
+// dependency (the kernel may start once every block of `dep` has called
+// griddepcontrol.launch_dependents, and waits for dep's completion with
+// griddepcontrol.wait); if the runtime refuses that edge, an ordinary one.
 cudaGraphNode_t add_kernel(cudaGraph_t g, cudaGraphNode_t dep, const void* func, unsigned grid,
                            unsigned block, size_t smem, void** args,
-                           cudaGraphDeviceNode_t* devnode = nullptr) {
+                           cudaGraphDeviceNode_t* devnode = nullptr, bool programmatic = false) {
   cudaKernelNodeParams p{};
   p.func = const_cast<void*>(func);
   p.gridDim = dim3(grid);
@@ -471,7 +503,18 @@ cudaGraphNode_t add_kernel(cudaGraph_t g, cudaGraphNode_t dep, const void* func,
   p.kernelParams = args;
   p.extra = nullptr;
   cudaGraphNode_t n = nullptr;
-  ck(cudaGraphAddKernelNode(&n, g, dep ? &dep : nullptr, dep ? 1 : 0, &p));
+  if (programmatic && dep) {
+    ck(cudaGraphAddKernelNode(&n, g, nullptr, 0, &p));
+    cudaGraphEdgeData e{};
+    e.from_port = cudaGraphKernelNodePortProgrammatic;
+    e.type = cudaGraphDependencyTypeProgrammatic;
+    if (cudaGraphAddDependencies(g, &dep, &n, &e, 1) != cudaSuccess) {
+      (void)cudaGetLastError();
+      ck(cudaGraphAddDependencies(g, &dep, &n, nullptr, 1));
+    }
+  } else {
+    ck(cudaGraphAddKernelNode(&n, g, dep ? &dep : nullptr, dep ? 1 : 0, &p));
+  }
   if (devnode) {
     // Device-updatable: the control kernels size its grid to the work.
     cudaKernelNodeAttrValue v{};
@@ -508,13 +551,22 @@ class GraphRunner {
   // Builds the graph of one instance (kernel arguments: the instance's
   // device state and the three condition handles).
   static void build(GraphInst* gi, int pivot, bool half) {
-    build_impl(gi, pivot, true, half);
+    build_impl(gi, pivot, true, half, std::getenv("QMS_NO_PDL") == nullptr);
+  }
+
+  // The exchange kernel of this graph: 32-bit positions unless the graph
+  // serves arrays of 2^32 keys or more.
+  static const void* exchange_kernel(bool wide) {
+    return wide ? reinterpret_cast<const void*>(k_g_part_exchange<K, HV, uint64_t>)
+                : reinterpret_cast<const void*>(k_g_part_exchange<K, HV, uint32_t>);
   }
 
   // half: the round body also holds the larger-side machinery (two Mergesort
   // phases and the overlapped merge); without it a round runs Fig. 3's rule
-  // with no extra conditional nodes.
-  static void build_impl(GraphInst* gi, int pivot, bool dyn, bool half) {
+  // with no extra conditional nodes.  pdl: the merge node depends on the
+  // split node programmatically (it starts while the split runs and loads
+  // its buffer tiles first).
+  static void build_impl(GraphInst* gi, int pivot, bool dyn, bool half, bool pdl) {
     int dev = 0, sms = 0;
     ck(cudaGetDevice(&dev));
     ck(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -532,17 +584,27 @@ class GraphRunner {
     // Grid caps in waves of resident blocks (the control kernels size each
     // node to its work up to these), from sweeps at 2^28 keys: leaves 8
     // waves (2: 18.72 ms per sort, 8: 18.65), partition tiles 4 (18.68).
-    const unsigned g_part = occ(reinterpret_cast<const void*>(k_g_part_local<K, HV, CNT>), PNT, 0) * 4;
-    const unsigned g_leaf = occ(reinterpret_cast<const void*>(k_g_leaf<K, HV, CNT>), LC::LT, tsm_l) * 8;
-    const unsigned g_exch = occ(reinterpret_cast<const void*>(k_g_part_exchange<K, HV>), EXB, 0) * 2;
+    // (QMS_*_WAVES environment variables override the caps for experiments.)
+    auto waves = [&](const char* env, unsigned dflt, unsigned per_wave) {
+      const char* v = std::getenv(env);
+      const unsigned w = (v && dyn) ? static_cast<unsigned>(std::max(1, std::atoi(v))) : dflt;
+      return per_wave * w;
+    };
+    const unsigned g_part =
+        waves("QMS_PART_WAVES", 4, occ(reinterpret_cast<const void*>(k_g_part_local<K, HV, CNT>), PNT, 0));
+    const unsigned g_leaf =
+        waves("QMS_LEAF_WAVES", 8, occ(reinterpret_cast<const void*>(k_g_leaf<K, HV, CNT>), LC::LT, tsm_l));
+    const unsigned g_exch =
+        waves("QMS_EXCH_WAVES", 2, occ(exchange_kernel(gi->wide), EXB, 0));
     const unsigned g_split = static_cast<unsigned>(sms) * 4;
     // Eight waves of merge blocks that loop over the tiles: one block per tile
     // costs more in the level-end counter (one atomic per block) than it
     // gains, two waves too few (2^28 keys: 18.6 / 18.4 / 19.0 ms per sort).
     // With fixed grids every block of the node runs on every level, however
     // small, so there it stays at two waves.
-    const unsigned g_merge =
-        occ(reinterpret_cast<const void*>(k_g_merge<K, HV, CNT>), MBT, 0) * (dyn ? 8 : 2);
+    const unsigned g_merge = dyn ? waves("QMS_MERGE_WAVES", 8,
+                                         occ(reinterpret_cast<const void*>(k_g_merge<K, HV, CNT>), MBT, 0))
+                                 : occ(reinterpret_cast<const void*>(k_g_merge<K, HV, CNT>), MBT, 0) * 2;
     // Tiles are handed out through a ticket: with device-sized grids one
     // block per tile, else one wave of blocks that loop.
     const unsigned g_omerge =
@@ -607,8 +669,7 @@ class GraphRunner {
                      dn ? dn + ic : nullptr);
       d = add_kernel(gr, d, reinterpret_cast<const void*>(k_g_part_prefix), g_scan, NT, 0, a_s,
                      dn ? dn + ipf : nullptr);
-      d = add_kernel(gr, d, reinterpret_cast<const void*>(k_g_part_exchange<K, HV>), g_exch, EXB, 0, a_s,
-                     dn ? dn + ie : nullptr);
+      d = add_kernel(gr, d, exchange_kernel(gi->wide), g_exch, EXB, 0, a_s, dn ? dn + ie : nullptr);
       return d;
     };
     n = add_pass(body, n, DN_PART1, DN_EXCH1);
@@ -624,7 +685,7 @@ class GraphRunner {
       cudaGraphNode_t q = add_kernel(lv, nullptr, reinterpret_cast<const void*>(k_g_split<K, HV, CNT>),
                                      g_split, 256, 0, a_s, dn ? dn + DN_SPLIT : nullptr);
       add_kernel(lv, q, reinterpret_cast<const void*>(k_g_merge<K, HV, CNT>), g_merge, MBT, 0, a_level,
-                 dn ? dn + DN_MERGE : nullptr);
+                 dn ? dn + DN_MERGE : nullptr, pdl);
       return d;
     };
     if (!half) {
@@ -658,16 +719,20 @@ class GraphRunner {
     if (dyn && !all) {  // some node is not device-updatable: fixed grids throughout
       cudaGraphDestroy(g);
       for (int i = 0; i < DN_COUNT; ++i) gi->dn[i] = nullptr;
-      build_impl(gi, pivot, false, half);
+      build_impl(gi, pivot, false, half, pdl);
       return;
     }
     gi->dyn = all ? 1u : 0u;
     if (cudaGraphInstantiate(&gi->exec, g, 0) != cudaSuccess) {
       (void)cudaGetLastError();
       cudaGraphDestroy(g);
+      for (int i = 0; i < DN_COUNT; ++i) gi->dn[i] = nullptr;
+      if (pdl) {  // programmatic edges not accepted here: ordinary edges
+        build_impl(gi, pivot, dyn, half, false);
+        return;
+      }
       if (dyn) {  // device-updatable nodes not accepted here: fixed grids
-        for (int i = 0; i < DN_COUNT; ++i) gi->dn[i] = nullptr;
-        build_impl(gi, pivot, false, half);
+        build_impl(gi, pivot, false, half, false);
         return;
       }
       throw Err{QMS_ECUDA};
@@ -677,13 +742,14 @@ class GraphRunner {
       cudaGraphExecDestroy(gi->exec);
       cudaGraphDestroy(g);
       for (int i = 0; i < DN_COUNT; ++i) gi->dn[i] = nullptr;
-      build_impl(gi, pivot, false, half);
+      build_impl(gi, pivot, false, half, false);
       return;
     }
     gi->graph = g;
     if (std::getenv("QMS_VERBOSE"))
-      std::fprintf(stderr, "qms: graph built (K=%zu HV=%d CNT=%d pivot=%d): %s grids\n", sizeof(K),
-                   HV ? 1 : 0, CNT ? 1 : 0, pivot, gi->dyn ? "device-sized" : "fixed");
+      std::fprintf(stderr, "qms: graph built (K=%zu HV=%d CNT=%d pivot=%d): %s grids%s\n", sizeof(K),
+                   HV ? 1 : 0, CNT ? 1 : 0, pivot, gi->dyn ? "device-sized" : "fixed",
+                   pdl ? ", programmatic split-merge edge" : "");
   }
 
   // Takes a free instance able to hold n keys (creating or growing one).
@@ -695,8 +761,9 @@ class GraphRunner {
   static GraphInst* acquire(uint64_t n, int pivot, bool half, cudaStream_t st) {
     int dev = 0;
     ck(cudaGetDevice(&dev));
-    const auto key =
-        std::make_tuple(static_cast<int>(sizeof(K)), HV ? 1 : 0, CNT ? 1 : 0, pivot, half ? 1 : 0, dev);
+    const bool wide = n >= (1ull << 32);
+    const auto key = std::make_tuple(static_cast<int>(sizeof(K)), HV ? 1 : 0, CNT ? 1 : 0, pivot,
+                                     (half ? 1 : 0) | (wide ? 2 : 0), dev);
     std::lock_guard<std::mutex> lk(g_graph_mu);
     auto& pool = g_graphs[key];
     GraphInst* gi = nullptr;
@@ -721,6 +788,7 @@ class GraphRunner {
       ck(cudaMalloc(reinterpret_cast<void**>(&gi->d_state), sizeof(DState)));
       ck(cudaMallocHost(reinterpret_cast<void**>(&gi->h_state), sizeof(DState)));
       ck(cudaEventCreateWithFlags(&gi->done, cudaEventDisableTiming));
+      gi->wide = wide;
       build(gi, pivot, half);
       pool.push_back(gi);
     }
@@ -878,27 +946,187 @@ unsigned spin_limit_of(const qms_options* opt) {
 }
 
 // ---------------------------------------------------------------------------
-// Batched form: many independent segments of one array.  Segments of at most
-// CTA_MAX_TILES tiles are sorted in one persistent launch (one block per
-// segment, longest first, taken from an atomic ticket); longer segments run
-// through the grid-wide driver one after the other on the same stream.
+// Batched-form plan: for each length bin (segments of (2^(b-1), 2^b] keys)
+// the kernel configuration that sorts it (qms_batch.h).  The default takes
+// the smallest thread group whose tile holds the bin; the autotuner
+// (qms_batched_autotune) times every configuration per bin on this GPU and
+// stores the fastest in a JSON file per key type, payload and SM count,
+// which later processes load.
+
+struct BatchPlan {
+  int cfg[BATCH_BINS];
+  bool tuned;
+};
+
+BatchPlan default_plan(int ksize, bool hv) {
+  BatchPlan p{};
+  for (int b = 0; b < BATCH_BINS; ++b) {
+    int best = BC_QMS;
+    for (int c = 0; c < BC_QMS; ++c) {
+      if (!batch_cfg_valid(c, ksize, hv) || batch_cfg_capacity(c) < (1 << b)) continue;
+      if (best == BC_QMS || batch_cfg_capacity(c) < batch_cfg_capacity(best)) best = c;
+    }
+    p.cfg[b] = best;
+  }
+  p.tuned = false;
+  return p;
+}
+
+void mkdir_one(const char* d) { (void)::mkdir(d, 0755); }
+
+std::string plan_dir() {
+  if (const char* d = std::getenv("QMS_AUTOTUNE_DIR")) return d;
+  const char* h = std::getenv("HOME");
+  return std::string(h ? h : "/tmp") + "/.cache/qms_gb300";
+}
+
+std::string plan_path(int ksize, bool hv, int sms) {
+  char buf[96];
+  std::snprintf(buf, sizeof(buf), "/batched_k%d_v%d_sm%d.json", ksize, hv ? 1 : 0, sms);
+  return plan_dir() + buf;
+}
+
+int cfg_by_name(const char* name) {
+  for (int c = 0; c < BC_COUNT; ++c)
+    if (std::strcmp(name, batch_cfg_name(c)) == 0) return c;
+  return -1;
+}
+
+// Reads a plan file written by write_plan: one bin per line,
+//   {"bin": B, "max_len": N, "config": "NAME", "ns_per_key": X}
+// Lines that do not parse, or name a configuration that does not exist for
+// these keys, leave the default for their bin.  Returns false when the
+// file cannot be read or holds another key type or SM count.
+bool read_plan(const std::string& path, int ksize, bool hv, int sms, BatchPlan* p) {
+  FILE* f = std::fopen(path.c_str(), "r");
+  if (!f) return false;
+  char line[512];
+  bool header = false;
+  while (std::fgets(line, sizeof(line), f)) {
+    int k = 0, v = 0, sm = 0;
+    if (std::sscanf(line, " {\"key_bytes\": %d, \"payload\": %d, \"sm_count\": %d", &k, &v, &sm) == 3) {
+      header = (k == ksize && v == (hv ? 1 : 0) && sm == sms);
+      continue;
+    }
+    int b = -1;
+    char name[64] = {0};
+    if (std::sscanf(line, " {\"bin\": %d, \"max_len\": %*d, \"config\": \"%63[^\"]\"", &b, name) == 2 &&
+        b >= 0 && b < BATCH_BINS) {
+      const int c = cfg_by_name(name);
+      if (c >= 0 && batch_cfg_valid(c, ksize, hv) && batch_cfg_capacity(c) >= (1 << b)) p->cfg[b] = c;
+    }
+  }
+  std::fclose(f);
+  p->tuned = header;
+  return header;
+}
+
+bool write_plan(const std::string& path, int ksize, bool hv, int sms, const BatchPlan& p,
+                const double* ns_per_key) {
+  FILE* f = std::fopen(path.c_str(), "w");
+  if (!f) return false;
+  std::fprintf(f, "{\"key_bytes\": %d, \"payload\": %d, \"sm_count\": %d,\n \"bins\": [\n", ksize,
+               hv ? 1 : 0, sms);
+  for (int b = 0; b < BATCH_BINS; ++b)
+    std::fprintf(f, "  {\"bin\": %d, \"max_len\": %d, \"config\": \"%s\", \"ns_per_key\": %.6f}%s\n", b,
+                 1 << b, batch_cfg_name(p.cfg[b]), ns_per_key ? ns_per_key[b] : 0.0,
+                 b + 1 < BATCH_BINS ? "," : "");
+  std::fprintf(f, " ]}\n");
+  return std::fclose(f) == 0;
+}
+
+std::mutex g_plan_mu;
+std::map<std::tuple<int, int, int>, BatchPlan> g_plans;  // (key bytes, payload, device)
+
+BatchPlan plan_for(int ksize, bool hv) {
+  int dev = 0, sms = 0;
+  ck(cudaGetDevice(&dev));
+  ck(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  std::lock_guard<std::mutex> lk(g_plan_mu);
+  const auto key = std::make_tuple(ksize, hv ? 1 : 0, dev);
+  auto it = g_plans.find(key);
+  if (it != g_plans.end()) return it->second;
+  BatchPlan p = default_plan(ksize, hv);
+  BatchPlan q = p;
+  if (read_plan(plan_path(ksize, hv, sms), ksize, hv, sms, &q)) p = q;
+  g_plans[key] = p;
+  return p;
+}
+
+void set_plan(int ksize, bool hv, const BatchPlan& p) {
+  int dev = 0;
+  ck(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(g_plan_mu);
+  g_plans[std::make_tuple(ksize, hv ? 1 : 0, dev)] = p;
+}
+
+// Streams of the batched form's concurrent bins (per device, created once).
+constexpr int kBatchStreams = BC_COUNT;
+cudaStream_t batch_stream(int i) {
+  static std::mutex mu;
+  static std::map<int, std::vector<cudaStream_t>> streams;
+  int dev = 0;
+  ck(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(mu);
+  auto& v = streams[dev];
+  if (v.empty()) {
+    v.resize(kBatchStreams);
+    for (auto& x : v) ck(cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking));
+  }
+  return v[i];
+}
+
+// ---------------------------------------------------------------------------
+// Batched form: many independent segments of one array.  Every segment is
+// one QuickMergesort.  The plan maps each length bin to a kernel
+// configuration: segments that fit one group's tile are finished by the
+// base case inside a warp or block-sized group (several groups per block);
+// longer segments of at most CTA_MAX_TILES tiles are sorted by one block
+// each running the rounds (longest first, from an atomic ticket); still
+// longer ones run through the grid-wide driver.  The configurations' lists
+// run concurrently on separate streams.
+
+// Launches the block-per-segment QuickMergesort over order[0, n).
+template <class K, bool HV, bool CNT>
+void launch_cta_qms(K* keys, uint32_t* vals, const uint64_t* d_off, const uint32_t* d_order,
+                    uint32_t n, unsigned int* ticket, int pivot, int xf, Desc* desc, cudaStream_t st) {
+  constexpr size_t smem = cta_smem_bytes<K, HV>();
+  allow_smem(k_batched<K, HV, CNT>, smem);
+  int dev = 0, sms = 0, occ = 0;
+  ck(cudaGetDevice(&dev));
+  ck(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  ck(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batched<K, HV, CNT>, NT, smem));
+  const unsigned grid = static_cast<unsigned>(
+      std::max<uint64_t>(1, std::min<uint64_t>(n, static_cast<uint64_t>(sms) * std::max(occ, 1))));
+  k_batched<K, HV, CNT><<<grid, NT, smem, st>>>(keys, vals, d_off, d_order, n, ticket, pivot, xf, desc);
+  ck(cudaGetLastError());
+}
+
+inline int ceil_log2(uint64_t x) {
+  int b = 0;
+  while ((1ull << b) < x) ++b;
+  return b;
+}
 
 template <class K, bool HV, bool CNT>
 int run_batched(void* keys, uint32_t* vals, const uint64_t* d_off, size_t nseg, int dtype,
                 int pivot, cudaStream_t st, qms_profile* profile, qms_stats* stats) {
   const auto t0 = std::chrono::steady_clock::now();
+  constexpr uint64_t ES = sizeof(K) + (HV ? 4 : 0);
   std::vector<uint64_t> off(nseg + 1);
   ck(cudaMemcpyAsync(off.data(), d_off, (nseg + 1) * sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
   ck(cudaStreamSynchronize(st));
   for (size_t i = 0; i < nseg; ++i)
     if (off[i + 1] < off[i]) throw Err{QMS_EINVAL};
   if (HV && off[nseg] >= (1ull << 32)) throw Err{QMS_EINVAL};
-  // Longest first: bucket by floor(log2(length)), buckets in descending order.
+  const BatchPlan plan = plan_for(sizeof(K), HV);
   const uint64_t cta_max = static_cast<uint64_t>(CTA_MAX_TILES) * TILE;
-  std::vector<uint32_t> bucket_cnt(65, 0);
+  // Each configuration's segments, longest first: counting sort by length
+  // bin (ceil(log2 length), at most 64), bins in descending order.
+  std::vector<uint32_t> cnt_cb(static_cast<size_t>(BC_COUNT) * 65, 0);
   std::vector<uint32_t> big;
-  uint64_t big_max = 0;
-  auto lg = [](uint64_t x) { int l = 0; while ((2ull << l) <= x) ++l; return l; };
+  uint64_t big_max = 0, group_keys = 0;
+  auto cfg_of = [&](uint64_t len, int b) { return b < BATCH_BINS ? plan.cfg[b] : BC_QMS; };
   for (size_t i = 0; i < nseg; ++i) {
     const uint64_t len = off[i + 1] - off[i];
     if (len <= 1) continue;
@@ -907,25 +1135,35 @@ int run_batched(void* keys, uint32_t* vals, const uint64_t* d_off, size_t nseg, 
       big_max = std::max(big_max, len);
       continue;
     }
-    ++bucket_cnt[lg(len)];
+    const int b = ceil_log2(len);
+    const int c = cfg_of(len, b);
+    ++cnt_cb[static_cast<size_t>(c) * 65 + b];
+    if (c != BC_QMS) group_keys += len;
   }
-  std::vector<uint32_t> start(65, 0);
+  std::vector<uint32_t> cfg_start(BC_COUNT + 1, 0), pos(static_cast<size_t>(BC_COUNT) * 65, 0);
   uint32_t acc = 0;
-  for (int b = 64; b >= 0; --b) {
-    start[b] = acc;
-    acc += bucket_cnt[b];
+  for (int c = 0; c < BC_COUNT; ++c) {
+    cfg_start[c] = acc;
+    for (int b = 64; b >= 0; --b) {
+      pos[static_cast<size_t>(c) * 65 + b] = acc;
+      acc += cnt_cb[static_cast<size_t>(c) * 65 + b];
+    }
   }
-  const uint32_t nsmall = acc;
-  std::vector<uint32_t> order(nsmall ? nsmall : 1);
+  cfg_start[BC_COUNT] = acc;
+  const uint32_t nlisted = acc;
+  std::vector<uint32_t> order(nlisted ? nlisted : 1);
   for (size_t i = 0; i < nseg; ++i) {
     const uint64_t len = off[i + 1] - off[i];
     if (len <= 1 || len > cta_max) continue;
-    order[start[lg(len)]++] = static_cast<uint32_t>(i);
+    const int b = ceil_log2(len);
+    order[pos[static_cast<size_t>(cfg_of(len, b)) * 65 + b]++] = static_cast<uint32_t>(i);
   }
-  // Workspace: descriptor, ticket and order (O(segments) words), plus the
-  // grid driver's workspace for the longest large segment.
-  const size_t hdr = 256 * ((sizeof(Desc) + 255) / 256) + 256;
-  const size_t bbytes = hdr + static_cast<size_t>(nsmall) * 4;
+  // Workspace: descriptor, one ticket per configuration and the lists
+  // (O(segments) words), plus the grid driver's workspace for the longest
+  // large segment.
+  const size_t desc_b = 256 * ((sizeof(Desc) + 255) / 256);
+  const size_t hdr = desc_b + 256;
+  const size_t bbytes = hdr + static_cast<size_t>(nlisted) * 4;
   unsigned char* bws = nullptr;
   if (cudaMallocAsync(reinterpret_cast<void**>(&bws), bbytes, st) != cudaSuccess) {
     (void)cudaGetLastError();
@@ -937,28 +1175,48 @@ int run_batched(void* keys, uint32_t* vals, const uint64_t* d_off, size_t nseg, 
     ~Free() { cudaFreeAsync(p, s); }
   } free_bws{bws, st};
   Desc* desc = reinterpret_cast<Desc*>(bws);
-  unsigned int* ticket = reinterpret_cast<unsigned int*>(bws + 256 * ((sizeof(Desc) + 255) / 256));
+  unsigned int* tickets = reinterpret_cast<unsigned int*>(bws + desc_b);
   uint32_t* d_order = reinterpret_cast<uint32_t*>(bws + hdr);
   ck(cudaMemsetAsync(bws, 0, hdr, st));
   uint64_t launches = 0;
   Profiler prof(profile);
   const int xf = xform_of(dtype);
-  if (nsmall) {
-    ck(cudaMemcpyAsync(d_order, order.data(), static_cast<size_t>(nsmall) * 4, cudaMemcpyHostToDevice, st));
-    allow_smem(k_batched<K, HV, CNT>, tile_smem_bytes<K, HV>());
-    int dev = 0, sms = 0, occ = 0;
-    ck(cudaGetDevice(&dev));
-    ck(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    ck(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batched<K, HV, CNT>, NT,
-                                                     tile_smem_bytes<K, HV>()));
-    const unsigned grid = static_cast<unsigned>(
-        std::max<uint64_t>(1, std::min<uint64_t>(nsmall, static_cast<uint64_t>(sms) * std::max(occ, 1))));
+  if (nlisted) {
+    ck(cudaMemcpyAsync(d_order, order.data(), static_cast<size_t>(nlisted) * 4, cudaMemcpyHostToDevice, st));
     prof.begin(st);
-    k_batched<K, HV, CNT><<<grid, NT, tile_smem_bytes<K, HV>(), st>>>(
-        static_cast<K*>(keys), vals, d_off, d_order, nsmall, ticket, pivot, xf, desc);
+    // fork: every non-empty list on its own stream, joined back into st
+    cudaEvent_t fork = nullptr;
+    ck(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+    std::vector<cudaEvent_t> joins;
+    struct Ev {
+      cudaEvent_t& f;
+      std::vector<cudaEvent_t>& j;
+      ~Ev() {
+        if (f) cudaEventDestroy(f);
+        for (auto e : j) cudaEventDestroy(e);
+      }
+    } ev{fork, joins};
+    ck(cudaEventRecord(fork, st));
+    for (int c = 0; c < BC_COUNT; ++c) {
+      const uint32_t n = cfg_start[c + 1] - cfg_start[c];
+      if (n == 0) continue;
+      cudaStream_t bs = batch_stream(c);
+      ck(cudaStreamWaitEvent(bs, fork, 0));
+      const uint32_t* lst = d_order + cfg_start[c];
+      if (c == BC_QMS) {
+        launch_cta_qms<K, HV, CNT>(static_cast<K*>(keys), vals, d_off, lst, n, tickets + c, pivot, xf,
+                                   desc, bs);
+      } else {
+        ck(launch_group_cfg(c, sizeof(K), HV, CNT, keys, vals, d_off, lst, n, tickets + c, xf, desc, bs));
+      }
+      ++launches;
+      cudaEvent_t j = nullptr;
+      ck(cudaEventCreateWithFlags(&j, cudaEventDisableTiming));
+      joins.push_back(j);
+      ck(cudaEventRecord(j, bs));
+      ck(cudaStreamWaitEvent(st, j, 0));
+    }
     prof.end(st, QMS_K_BATCH, 0);
-    ck(cudaGetLastError());
-    ++launches;
   }
   uint64_t rounds = 0, mom_rounds = 0, big_cmp = 0;
   if (!big.empty()) {
@@ -990,7 +1248,8 @@ int run_batched(void* keys, uint32_t* vals, const uint64_t* d_off, size_t nseg, 
   ck(cudaStreamSynchronize(st));
   ck(cudaGetLastError());
   prof.flush();
-  if (profile) profile->bytes[QMS_K_BATCH] += h.bytes;
+  // group-sorted segments move 2 * ES bytes per key (read once, written once)
+  if (profile) profile->bytes[QMS_K_BATCH] += h.bytes + 2 * ES * group_keys;
   if (h.err) throw Err{QMS_EINTERNAL};
   if (stats) {
     stats->comparisons = h.cmp + big_cmp;
@@ -999,6 +1258,139 @@ int run_batched(void* keys, uint32_t* vals, const uint64_t* d_off, size_t nseg, 
     stats->mom_rounds = mom_rounds;
     stats->launches = launches;
     stats->ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  }
+  return QMS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner of the batched form.  For every length bin it sorts a synthetic
+// batch of random keys (segment lengths uniform within the bin, enough
+// segments to fill the GPU several times) with every configuration whose
+// tile holds the bin, times each with CUDA events (median of three, keys
+// refilled before every run), keeps the fastest per key, installs the plan
+// for this device and writes it to the plan file.
+
+template <class K>
+__global__ void k_fill_random(K* a, uint64_t n, uint64_t seed) {
+  for (uint64_t i = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
+    uint64_t z = seed + (i + 1) * 0x9E3779B97F4A7C15ull;  // SplitMix64 (Steele, Lea, Flood)
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    a[i] = static_cast<K>(z ^ (z >> 31));
+  }
+}
+
+template <class K, bool HV>
+int autotune_typed(cudaStream_t st, char* report, size_t report_len) {
+  int dev = 0, sms = 0;
+  ck(cudaGetDevice(&dev));
+  ck(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  constexpr uint64_t kMaxKeys = 1ull << 24;
+  const uint64_t cap_keys = kMaxKeys + (1ull << 15);
+  const uint64_t max_seg = kMaxKeys / 2 + 2;
+  // one allocation: keys, payloads, offsets, order, descriptor and tickets
+  const size_t kb = cap_keys * sizeof(K), vb = HV ? cap_keys * 4 : 0;
+  const size_t ob = (max_seg + 1) * 8, rb = max_seg * 4, db = 256 * ((sizeof(Desc) + 255) / 256) + 256;
+  unsigned char* mem = nullptr;
+  if (cudaMalloc(reinterpret_cast<void**>(&mem), kb + vb + ob + rb + db) != cudaSuccess) {
+    (void)cudaGetLastError();
+    throw Err{QMS_ENOMEM};
+  }
+  struct Free {
+    unsigned char* p;
+    ~Free() { cudaFree(p); }
+  } fr{mem};
+  K* keys = reinterpret_cast<K*>(mem);
+  uint32_t* vals = HV ? reinterpret_cast<uint32_t*>(mem + kb) : nullptr;
+  uint64_t* d_off = reinterpret_cast<uint64_t*>(mem + kb + vb);
+  uint32_t* d_order = reinterpret_cast<uint32_t*>(mem + kb + vb + ob);
+  Desc* desc = reinterpret_cast<Desc*>(mem + kb + vb + ob + rb);
+  unsigned int* ticket = reinterpret_cast<unsigned int*>(reinterpret_cast<unsigned char*>(desc) +
+                                                         256 * ((sizeof(Desc) + 255) / 256));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  ck(cudaEventCreate(&e0));
+  ck(cudaEventCreate(&e1));
+  struct Evs {
+    cudaEvent_t a, b;
+    ~Evs() {
+      cudaEventDestroy(a);
+      cudaEventDestroy(b);
+    }
+  } evs{e0, e1};
+  BatchPlan plan = default_plan(sizeof(K), HV);
+  double ns[BATCH_BINS] = {0};
+  std::mt19937_64 rng(0x5eedull);
+  std::string rep;
+  for (int b = 1; b < BATCH_BINS; ++b) {
+    const uint64_t lo = (1ull << (b - 1)) + 1, hi = 1ull << b;
+    const uint64_t target = std::min<uint64_t>(kMaxKeys, 1ull << (b + 13));
+    std::vector<uint64_t> off(1, 0);
+    std::uniform_int_distribution<uint64_t> len(std::max<uint64_t>(lo, 2), hi);
+    while (off.back() < target && off.size() < max_seg) off.push_back(off.back() + len(rng));
+    const uint32_t nseg = static_cast<uint32_t>(off.size() - 1);
+    const uint64_t n = off.back();
+    std::vector<uint32_t> order(nseg);
+    for (uint32_t i = 0; i < nseg; ++i) order[i] = i;
+    std::sort(order.begin(), order.end(), [&](uint32_t x, uint32_t y) {
+      return off[x + 1] - off[x] > off[y + 1] - off[y];
+    });
+    ck(cudaMemcpyAsync(d_off, off.data(), off.size() * 8, cudaMemcpyHostToDevice, st));
+    ck(cudaMemcpyAsync(d_order, order.data(), order.size() * 4, cudaMemcpyHostToDevice, st));
+    double best = -1.0;
+    int best_c = plan.cfg[b];
+    for (int c = 0; c < BC_COUNT; ++c) {
+      if (!batch_cfg_valid(c, sizeof(K), HV)) continue;
+      if (c != BC_QMS && batch_cfg_capacity(c) < static_cast<int>(hi)) continue;
+      if (c == BC_QMS && hi <= static_cast<uint64_t>(TILE)) continue;  // a single tile there
+      float t[3] = {0, 0, 0};
+      for (int r = -1; r < 3; ++r) {  // one warm-up run
+        k_fill_random<K><<<1024, 256, 0, st>>>(keys, n, 77 + r);
+        ck(cudaMemsetAsync(desc, 0, 256 * ((sizeof(Desc) + 255) / 256) + 256, st));
+        ck(cudaEventRecord(e0, st));
+        if (c == BC_QMS)
+          launch_cta_qms<K, HV, false>(keys, vals, d_off, d_order, nseg, ticket, QMS_PIVOT_M3, XF_NONE,
+                                       desc, st);
+        else
+          ck(launch_group_cfg(c, sizeof(K), HV, false, keys, vals, d_off, d_order, nseg, ticket,
+                              XF_NONE, desc, st));
+        ck(cudaEventRecord(e1, st));
+        ck(cudaEventSynchronize(e1));
+        if (r >= 0) ck(cudaEventElapsedTime(&t[r], e0, e1));
+      }
+      unsigned err = 0;
+      ck(cudaMemcpy(&err, &desc->err, sizeof(err), cudaMemcpyDeviceToHost));
+      if (err) throw Err{QMS_EINTERNAL};
+      std::sort(t, t + 3);
+      const double per = static_cast<double>(t[1]) * 1e6 / static_cast<double>(n);
+      char line[160];
+      std::snprintf(line, sizeof(line), "bin %2d (%llu..%llu keys, %u segments): %-12s %.4f ns/key\n", b,
+                    static_cast<unsigned long long>(lo), static_cast<unsigned long long>(hi), nseg,
+                    batch_cfg_name(c), per);
+      rep += line;
+      if (best < 0 || per < best) {
+        best = per;
+        best_c = c;
+      }
+    }
+    plan.cfg[b] = best_c;
+    ns[b] = best;
+  }
+  plan.tuned = true;
+  set_plan(sizeof(K), HV, plan);
+  const std::string path = plan_path(sizeof(K), HV, sms);
+  std::string dir = plan_dir();
+  // create the directory (one level below an existing one is enough here)
+  for (size_t p = 1; p <= dir.size(); ++p) {
+    if (p == dir.size() || dir[p] == '/') {
+      const std::string d = dir.substr(0, p);
+      mkdir_one(d.c_str());
+    }
+  }
+  const bool saved = write_plan(path, sizeof(K), HV, sms, plan, ns);
+  rep += saved ? ("plan written to " + path + "\n") : ("plan not written (" + path + ")\n");
+  if (report && report_len) {
+    std::snprintf(report, report_len, "%s", rep.c_str());
   }
   return QMS_OK;
 }
@@ -1233,6 +1625,83 @@ int qms_sort_noalloc(void* d_keys, size_t n, int dtype, const qms_options* opt, 
     return QMS_EINTERNAL;
   }
 }
+
+static int key_bytes_of(int dtype) { return (dtype == QMS_U64 || dtype == QMS_I64) ? 8 : 4; }
+
+int qms_batched_autotune(int dtype, int with_payload, void* stream, char* report, size_t report_len) {
+  if (!valid_dtype(dtype)) return QMS_EINVAL;
+  if (report && report_len) report[0] = 0;
+  const cudaStream_t st = static_cast<cudaStream_t>(stream);
+  try {
+    if (key_bytes_of(dtype) == 8)
+      return with_payload ? autotune_typed<uint64_t, true>(st, report, report_len)
+                          : autotune_typed<uint64_t, false>(st, report, report_len);
+    return with_payload ? autotune_typed<uint32_t, true>(st, report, report_len)
+                        : autotune_typed<uint32_t, false>(st, report, report_len);
+  } catch (const Err& e) {
+    return e.code;
+  } catch (...) {
+    return QMS_EINTERNAL;
+  }
+}
+
+int qms_batched_get_plan(int dtype, int with_payload, int* cfg, int nbins, int* tuned) {
+  if (!valid_dtype(dtype) || cfg == nullptr || nbins < 1) return QMS_EINVAL;
+  try {
+    const BatchPlan p = plan_for(key_bytes_of(dtype), with_payload != 0);
+    for (int b = 0; b < nbins; ++b) cfg[b] = b < BATCH_BINS ? p.cfg[b] : BC_QMS;
+    if (tuned) *tuned = p.tuned ? 1 : 0;
+    return QMS_OK;
+  } catch (const Err& e) {
+    return e.code;
+  } catch (...) {
+    return QMS_EINTERNAL;
+  }
+}
+
+int qms_batched_set_plan(int dtype, int with_payload, const int* cfg, int nbins) {
+  if (!valid_dtype(dtype) || cfg == nullptr || nbins != BATCH_BINS) return QMS_EINVAL;
+  const int ks = key_bytes_of(dtype);
+  BatchPlan p{};
+  for (int b = 0; b < BATCH_BINS; ++b) {
+    const int c = cfg[b];
+    if (!batch_cfg_valid(c, ks, with_payload != 0)) return QMS_EINVAL;
+    if (c != BC_QMS && batch_cfg_capacity(c) < (1 << b)) return QMS_EINVAL;
+    p.cfg[b] = c;
+  }
+  p.tuned = false;
+  try {
+    set_plan(ks, with_payload != 0, p);
+    return QMS_OK;
+  } catch (const Err& e) {
+    return e.code;
+  } catch (...) {
+    return QMS_EINTERNAL;
+  }
+}
+
+int qms_batched_plan_read(const char* path, int dtype, int with_payload, int sm_count, int* cfg,
+                          int nbins) {
+  if (path == nullptr || !valid_dtype(dtype) || cfg == nullptr || nbins != BATCH_BINS) return QMS_EINVAL;
+  BatchPlan p = default_plan(key_bytes_of(dtype), with_payload != 0);
+  const bool ok = read_plan(path, key_bytes_of(dtype), with_payload != 0, sm_count, &p);
+  for (int b = 0; b < BATCH_BINS; ++b) cfg[b] = p.cfg[b];
+  return ok ? QMS_OK : QMS_EAGAIN;
+}
+
+int qms_batched_plan_write(const char* path, int dtype, int with_payload, int sm_count, const int* cfg,
+                           const double* ns_per_key, int nbins) {
+  if (path == nullptr || !valid_dtype(dtype) || cfg == nullptr || nbins != BATCH_BINS) return QMS_EINVAL;
+  BatchPlan p{};
+  for (int b = 0; b < BATCH_BINS; ++b) {
+    if (!batch_cfg_valid(cfg[b], key_bytes_of(dtype), with_payload != 0)) return QMS_EINVAL;
+    p.cfg[b] = cfg[b];
+  }
+  return write_plan(path, key_bytes_of(dtype), with_payload != 0, sm_count, p, ns_per_key) ? QMS_OK
+                                                                                             : QMS_EINVAL;
+}
+
+const char* qms_batched_config_name(int cfg) { return batch_cfg_name(cfg); }
 
 int qms_sort_batched(void* d_keys, uint32_t* d_vals, const uint64_t* d_offsets, size_t nseg,
                      int dtype, const qms_options* opt, void* stream, qms_stats* stats) {

@@ -103,10 +103,26 @@ __device__ __forceinline__ void merge_staged_out(const K* sin, K* sout, const ui
   });
 }
 
+// Programmatic dependent launch.  A kernel launched with a programmatic
+// dependency on the one before it may start while that one still runs;
+// grid_dep_wait() returns once the earlier grid has finished and its writes
+// are visible (at once when there is no such dependency).
+// grid_dep_trigger() lets the next kernel start early.
+__device__ __forceinline__ void grid_dep_wait() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+__device__ __forceinline__ void grid_dep_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // One output tile per block.  Element i of the tile (i = j*MBT + thread) is
 // loaded from the A/B slices and from the buffer tile by the same thread,
 // which then stores its buffer value into that X slot: the tile's consumed
 // slots receive exactly its buffer elements.
+//
+// The buffer tile does not depend on the split step, so it is loaded first;
+// with `wait` the block then waits for the split step's grid (launched with
+// a programmatic dependency, the merge starts while the split still runs).
 //
 // Shared-memory indices carry one padding element per 128 bytes.  For the
 // striped element i = j*MBT + thread that is j*(MBT + MBT/PE) + pad(thread),
@@ -114,21 +130,39 @@ __device__ __forceinline__ void merge_staged_out(const K* sin, K* sout, const ui
 // PE a multiple of 2*VM) it is pad(d) + j: both a per-thread base plus a
 // compile-time offset.
 template <class K, bool HV, bool CNT>
-__device__ __forceinline__ void merge_level_tile_impl(K* keys, uint32_t* vals,
-                                                      const MGeom<MergeCfg<K, HV>::MT>& gm,
-                                                      uint64_t a_lo, uint64_t a_hi, K* gy,
-                                                      uint32_t* gyv, uint64_t X, int xf, Desc* desc,
-                                                      K* sin, K* sout, uint32_t* svin,
-                                                      uint32_t* svout) {
+__device__ __forceinline__ void merge_level_tile(K* keys, uint32_t* vals, uint64_t X, uint64_t Y,
+                                                 uint64_t m, uint64_t L, const uint64_t* splits,
+                                                 int xf, Desc* desc, uint64_t t, bool wait) {
   using C = MergeCfg<K, HV>;
+  constexpr int MT = C::MT;
   constexpr int VM = C::VM;
   constexpr int PE = 128 / static_cast<int>(sizeof(K));  // keys per padded row
   static_assert(PE % (2 * VM) == 0 || VM % PE == 0, "blocked rows must not straddle padding");
   constexpr int SK = MBT + MBT / PE;  // padded stride of one striped row of keys
   constexpr int SV = MBT + MBT / 32;
+  __shared__ K sin[C::IN_K];
+  __shared__ K sout[C::IN_K];
+  __shared__ uint32_t svin[HV ? C::IN_V : 1];
+  __shared__ uint32_t svout[HV ? C::IN_V : 1];
+  const MGeom<MT> gm(m, L, t);
+  K* gy = keys + Y + t * MT;
+  uint32_t* gyv = HV ? vals + Y + t * MT : nullptr;
   uint64_t cmp = 0;
   const int tid = threadIdx.x;
   const int cnt = static_cast<int>(gm.d1 - gm.d0);
+  K x[VM], y[VM];
+  uint32_t xv[VM], yv[VM];
+#pragma unroll
+  for (int j = 0; j < VM; ++j) {
+    const int i = j * MBT + tid;
+    if (i < cnt) {
+      y[j] = gy[i];
+      if (HV) yv[j] = gyv[i];
+    }
+  }
+  if (wait) grid_dep_wait();
+  const uint64_t a_lo = splits[t];
+  const uint64_t a_hi = (gm.d1 == gm.la + gm.lb) ? gm.la : splits[t + 1];
   const int na = static_cast<int>(a_hi - a_lo);
   const uint64_t b_lo = gm.d0 - a_lo;
   // element i < na comes from A[a_lo + i], element i >= na from B[b_lo + i - na]
@@ -138,19 +172,12 @@ __device__ __forceinline__ void merge_level_tile_impl(K* keys, uint32_t* vals,
   uint32_t* gbv = HV ? vals + X + gm.pbase + gm.la + b_lo - na : nullptr;
   const int ps = tid + tid / PE;  // padded striped base
   const int pv = tid + tid / 32;
-  K x[VM], y[VM];
-  uint32_t xv[VM], yv[VM];
 #pragma unroll
   for (int j = 0; j < VM; ++j) {
     const int i = j * MBT + tid;
     if (i < cnt) {
-      K* src = (i < na ? ga : gb) + i;
-      x[j] = *src;
-      y[j] = gy[i];
-      if (HV) {
-        xv[j] = (i < na ? gav : gbv)[i];
-        yv[j] = gyv[i];
-      }
+      x[j] = (i < na ? ga : gb)[i];
+      if (HV) xv[j] = (i < na ? gav : gbv)[i];
     }
   }
   with_xf<K>(xf, [&](auto xc) {
@@ -173,29 +200,10 @@ __device__ __forceinline__ void merge_level_tile_impl(K* keys, uint32_t* vals,
 }
 
 template <class K, bool HV, bool CNT>
-__device__ __forceinline__ void merge_level_tile(K* keys, uint32_t* vals, uint64_t X, uint64_t Y,
-                                                 uint64_t m, uint64_t L, const uint64_t* splits,
-                                                 int xf, Desc* desc, uint64_t t) {
-  using C = MergeCfg<K, HV>;
-  constexpr int MT = C::MT;
-  const MGeom<MT> gm(m, L, t);
-  const uint64_t a_lo = splits[t];
-  const uint64_t a_hi = (gm.d1 == gm.la + gm.lb) ? gm.la : splits[t + 1];
-  K* gy = keys + Y + t * MT;
-  uint32_t* gyv = HV ? vals + Y + t * MT : nullptr;
-  __shared__ K sin[C::IN_K];
-  __shared__ K sout[C::IN_K];
-  __shared__ uint32_t svin[HV ? C::IN_V : 1];
-  __shared__ uint32_t svout[HV ? C::IN_V : 1];
-  merge_level_tile_impl<K, HV, CNT>(keys, vals, gm, a_lo, a_hi, gy, gyv, X, xf, desc, sin, sout,
-                                    svin, svout);
-}
-
-template <class K, bool HV, bool CNT>
 __global__ void __launch_bounds__(MBT, MergeCfg<K, HV>::MINB)
     k_merge_level3(K* keys, uint32_t* vals, uint64_t X, uint64_t Y, uint64_t m, uint64_t L,
                    const uint64_t* splits, int xf, Desc* desc) {
-  merge_level_tile<K, HV, CNT>(keys, vals, X, Y, m, L, splits, xf, desc, blockIdx.x);
+  merge_level_tile<K, HV, CNT>(keys, vals, X, Y, m, L, splits, xf, desc, blockIdx.x, true);
 }
 
 // One lane's merge-path search for diagonal d over A and B (global memory)
@@ -288,6 +296,7 @@ template <class K, bool HV, bool CNT>
 __global__ void __launch_bounds__(256) k_merge_split3(const K* keys, uint64_t X, uint64_t m,
                                                       uint64_t L, int xf, uint64_t* splits,
                                                       Desc* desc) {
+  grid_dep_trigger();  // the merge may start and load its buffer tiles
   uint64_t cmp = 0;
   split_group<K, HV, CNT>(keys, X, m, L, xf, splits,
                           (blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x) >> 5, cmp);

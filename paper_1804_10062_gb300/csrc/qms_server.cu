@@ -176,16 +176,16 @@ int run_group_typed(std::vector<Req*>& g, cudaStream_t st, int pivot) {
   }
   ok(cudaMemsetAsync(base, 0, hdr, st));
   ok(cudaMemcpyAsync(segs, hs.data(), hs.size() * sizeof(SegDesc), cudaMemcpyHostToDevice, st));
-  ok(smem_attr(reinterpret_cast<const void*>(k_batched_ptrs<K, false>), tile_smem_bytes<K, false>()));
+  ok(smem_attr(reinterpret_cast<const void*>(k_batched_ptrs<K, false>), cta_smem_bytes<K, false>()));
   int dev = 0, sms = 0, occ = 0;
   ok(cudaGetDevice(&dev));
   ok(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   ok(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batched_ptrs<K, false>, NT,
-                                                   tile_smem_bytes<K, false>()));
+                                                   cta_smem_bytes<K, false>()));
   const unsigned grid = static_cast<unsigned>(std::max<size_t>(
       1, std::min<size_t>(g.size(), static_cast<size_t>(sms) * std::max(occ, 1))));
   if (rc == QMS_OK) {
-    k_batched_ptrs<K, false><<<grid, NT, tile_smem_bytes<K, false>(), st>>>(
+    k_batched_ptrs<K, false><<<grid, NT, cta_smem_bytes<K, false>(), st>>>(
         segs, static_cast<uint32_t>(g.size()), ticket, pivot, desc);
     ok(cudaGetLastError());
   }

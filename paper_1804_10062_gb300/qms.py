@@ -100,6 +100,13 @@ def lib():
                 "qms_mergesort_half": ([vp, vp, sz, sz, i, vp], i),
                 "qms_sort_noalloc": ([vp, sz, i, ctypes.POINTER(qms_options), vp,
                                       ctypes.POINTER(qms_stats)], i),
+                "qms_batched_autotune": ([i, i, vp, ctypes.c_char_p, sz], i),
+                "qms_batched_get_plan": ([i, i, ctypes.POINTER(i), i, ctypes.POINTER(i)], i),
+                "qms_batched_set_plan": ([i, i, ctypes.POINTER(i), i], i),
+                "qms_batched_plan_read": ([ctypes.c_char_p, i, i, i, ctypes.POINTER(i), i], i),
+                "qms_batched_plan_write": ([ctypes.c_char_p, i, i, i, ctypes.POINTER(i),
+                                            ctypes.POINTER(ctypes.c_double), i], i),
+                "qms_batched_config_name": ([i], ctypes.c_char_p),
                 "qms_server_create": ([sz, i, i, i, ctypes.POINTER(vp)], i),
                 "qms_server_submit": ([vp, vp, vp, sz, i, i, u64p], i),
                 "qms_server_poll": ([vp, ctypes.c_uint64, ctypes.POINTER(i),
@@ -270,6 +277,59 @@ def qms_mergesort_half(keys, m: int, buf: int, vals=None, stream=None, dtype=Non
     rc = lib().qms_mergesort_half(ctypes.c_void_p(keys.data_ptr()), _check_vals(vals, keys.numel()),
                                   m, buf, code, _stream(stream))
     _raise(rc, "qms_mergesort_half")
+
+
+QMS_BATCH_BINS = 15
+BATCH_CONFIGS = ["group32x16", "group64x16", "group128x16", "group256x16", "group512x16",
+                 "group256x32", "group512x32", "block_qms"]
+BCFG = {name: i for i, name in enumerate(BATCH_CONFIGS)}
+
+
+def qms_batched_autotune(dtype: str = "u32", payload: bool = False, stream=None) -> str:
+    """Times every batched-form configuration per length bin on this GPU,
+    installs and stores the fastest plan; returns the timing report."""
+    buf = ctypes.create_string_buffer(1 << 16)
+    rc = lib().qms_batched_autotune(DTYPE_CODES[dtype], 1 if payload else 0, _stream(stream), buf,
+                                    len(buf))
+    _raise(rc, "qms_batched_autotune")
+    return buf.value.decode()
+
+
+def qms_batched_get_plan(dtype: str = "u32", payload: bool = False):
+    """(list of configuration names per length bin, tuned flag) on this device."""
+    cfg = (ctypes.c_int * QMS_BATCH_BINS)()
+    tuned = ctypes.c_int(0)
+    rc = lib().qms_batched_get_plan(DTYPE_CODES[dtype], 1 if payload else 0, cfg, QMS_BATCH_BINS,
+                                    ctypes.byref(tuned))
+    _raise(rc, "qms_batched_get_plan")
+    return [BATCH_CONFIGS[c] for c in cfg], bool(tuned.value)
+
+
+def qms_batched_set_plan(names, dtype: str = "u32", payload: bool = False):
+    cfg = (ctypes.c_int * QMS_BATCH_BINS)(*[BCFG[n] for n in names])
+    rc = lib().qms_batched_set_plan(DTYPE_CODES[dtype], 1 if payload else 0, cfg, QMS_BATCH_BINS)
+    _raise(rc, "qms_batched_set_plan")
+
+
+def qms_batched_plan_read(path: str, dtype: str = "u32", payload: bool = False, sm_count: int = 152):
+    """(names per bin, found) from a plan file; the default plan when not found."""
+    cfg = (ctypes.c_int * QMS_BATCH_BINS)()
+    rc = lib().qms_batched_plan_read(path.encode(), DTYPE_CODES[dtype], 1 if payload else 0, sm_count,
+                                     cfg, QMS_BATCH_BINS)
+    if rc not in (QMS_OK, QMS_EAGAIN):
+        _raise(rc, "qms_batched_plan_read")
+    return [BATCH_CONFIGS[c] for c in cfg], rc == QMS_OK
+
+
+def qms_batched_plan_write(path: str, names, dtype: str = "u32", payload: bool = False,
+                           sm_count: int = 152, ns_per_key=None):
+    cfg = (ctypes.c_int * QMS_BATCH_BINS)(*[BCFG[n] for n in names])
+    ns = None
+    if ns_per_key is not None:
+        ns = (ctypes.c_double * QMS_BATCH_BINS)(*ns_per_key)
+    rc = lib().qms_batched_plan_write(path.encode(), DTYPE_CODES[dtype], 1 if payload else 0,
+                                      sm_count, cfg, ns, QMS_BATCH_BINS)
+    _raise(rc, "qms_batched_plan_write")
 
 
 QMS_NOALLOC_MAX_N = 1 << 24

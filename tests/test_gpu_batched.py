@@ -146,3 +146,94 @@ def test_batched_full_size_sampled(q):
         oracle.sort(ref, variant="m3", mode="paper")
         got = d[a:b].cpu().numpy().view(np.uint32)
         assert got.tobytes() == ref.tobytes()
+
+
+CAPACITY = {"group32x16": 512, "group64x16": 1024, "group128x16": 2048, "group256x16": 4096,
+            "group512x16": 8192, "group256x32": 8192, "group512x32": 16384}
+
+
+def _forced_plan(q, cfg, dtype, payload):
+    """Every bin that cfg's tile holds takes cfg; the others the rounds."""
+    names = [cfg if CAPACITY[cfg] >= (1 << b) else "block_qms" for b in range(q.QMS_BATCH_BINS)]
+    q.qms_batched_set_plan(names, dtype=dtype, payload=payload)
+    return names
+
+
+@pytest.mark.parametrize("cfg", list(CAPACITY))
+def test_every_group_configuration_vs_oracle(q, cfg):
+    # Lengths across every bin up to the tile and a little beyond.
+    L = [0, 1, 2, 3, 5, 16, 17, 31, 32, 33, 100, 511, 512, 513, 1000, 1024, 1025, 2047, 2048,
+         2049, 4095, 4096, 4097, 8191, 8192, 8193, 12000, 16384, 16385, 20000]
+    L = np.array(L * 3, dtype=np.int64)
+    np.random.default_rng(2).shuffle(L)
+    off = gen.offsets_of(L)
+    cases = [("u32", None), ("f32", None)] if cfg.endswith("x32") else \
+        [("u32", None), ("f32", None), ("i64", None), ("u64", "pairs")]
+    try:
+        for dtype, extra in cases:
+            payload = extra == "pairs"
+            _forced_plan(q, cfg, dtype, payload)
+            n = int(off[-1])
+            k = gen.keys("mod16" if payload else ("normal" if dtype == "f32" else "uniform"), dtype, n, 5)
+            d = _dev(k)
+            doff = torch.from_numpy(off.view(np.int64)).cuda()
+            if payload:
+                v = gen.payload_index(n)
+                dv = _dev(v)
+                q.qms_sort_batched(d, doff, vals=dv, dtype=dtype)
+                vo = _host(dv, "u32")
+            else:
+                q.qms_sort_batched(d, doff, dtype=dtype)
+            out = _host(d, dtype)
+            for i in range(len(L)):
+                a, b = int(off[i]), int(off[i + 1])
+                ref = oracle.reference_sorted(k[a:b])
+                assert out[a:b].tobytes() == ref.tobytes(), (cfg, dtype, b - a)
+                if payload:
+                    assert np.array_equal(k[vo[a:b]], out[a:b]), (cfg, b - a)
+                    assert np.array_equal(np.sort(vo[a:b]), np.arange(a, b, dtype=np.uint32))
+    finally:
+        for dtype, payload in (("u32", False), ("f32", False), ("i64", False), ("u64", True)):
+            default = [min((c for c in CAPACITY if CAPACITY[c] >= (1 << b) and
+                            (not c.endswith("x32") or (dtype in ("u32", "f32") and not payload))),
+                           key=lambda c: CAPACITY[c], default="block_qms")
+                       for b in range(q.QMS_BATCH_BINS)]
+            q.qms_batched_set_plan(default, dtype=dtype, payload=payload)
+
+
+def test_group_configuration_comparison_count(q):
+    # The counting kernels of the group path report comparisons: at least
+    # lg(n!) per segment (every comparison sort needs that many).
+    L = np.array([300, 3000, 12000, 40] * 4, dtype=np.int64)
+    off = gen.offsets_of(L)
+    k = gen.keys("uniform", "u32", int(off[-1]), 8)
+    d = _dev(k)
+    st = q.qms_sort_batched(d, torch.from_numpy(off.view(np.int64)).cuda(), dtype="u32",
+                            count_cmps=True)
+    lg = sum(float(np.sum(np.log2(np.arange(2, m + 1)))) for m in L)
+    assert lg < st["comparisons"] < 3 * lg
+
+
+def test_autotuner_installs_and_stores_a_plan(q, tmp_path, monkeypatch):
+    monkeypatch.setenv("QMS_AUTOTUNE_DIR", str(tmp_path))
+    rep = q.qms_batched_autotune("u32")
+    assert "ns/key" in rep and "plan written" in rep
+    names, tuned = q.qms_batched_get_plan("u32")
+    assert tuned
+    for b, c in enumerate(names):
+        assert c == "block_qms" or CAPACITY[c] >= (1 << b)
+    files = list(tmp_path.glob("batched_k4_v0_sm*.json"))
+    assert len(files) == 1
+    sms = int(files[0].name.split("_sm")[1].split(".")[0])
+    got, found = q.qms_batched_plan_read(str(files[0]), "u32", sm_count=sms)
+    assert found and got[1:] == names[1:]
+    # the tuned plan sorts correctly
+    L = _lengths(4, 200)
+    off = gen.offsets_of(L)
+    k = gen.keys("uniform", "u32", int(off[-1]), 3)
+    d = _dev(k)
+    q.qms_sort_batched(d, torch.from_numpy(off.view(np.int64)).cuda(), dtype="u32")
+    out = _host(d, "u32")
+    for i in range(len(L)):
+        a, b = int(off[i]), int(off[i + 1])
+        assert out[a:b].tobytes() == np.sort(k[a:b]).tobytes()

@@ -37,13 +37,14 @@ def test_withheld_flag_times_out_and_next_sort_is_clean(q, host_driven):
     k = gen.keys("uniform", "u32", n, 71)
     d = _dev(k)
     with pytest.raises(q.QmsError) as ei:
-        q.qms_sort(d, side="larger", host_driven=host_driven, spin_limit=1, test_withhold=True)
+        q.qms_sort(d, side="larger", host_driven=host_driven, spin_limit=1, test_withhold=True,
+                   dtype="u32")
     assert ei.value.code == q.QMS_ETIMEOUT
     torch.cuda.synchronize()
     for side in ("larger", "fig3"):
         k2 = gen.keys("uniform", "u32", n, 72)
         d2 = _dev(k2)
-        q.qms_sort(d2, side=side, host_driven=host_driven)
+        q.qms_sort(d2, side=side, host_driven=host_driven, dtype="u32")
         out = d2.cpu().numpy().view(np.uint32)
         assert out.tobytes() == oracle.reference_sorted(k2).tobytes(), side
 
@@ -56,11 +57,11 @@ def test_spin_limit_alone_does_not_time_out(q):
     n = (1 << 20) + 3
     k = gen.keys("uniform", "u32", n, 73)
     d = _dev(k)
-    q.qms_sort(d, side="larger")
+    q.qms_sort(d, side="larger", dtype="u32")
     assert d.cpu().numpy().view(np.uint32).tobytes() == oracle.reference_sorted(k).tobytes()
     d = _dev(k)
     try:
-        q.qms_sort(d, side="larger", spin_limit=1)
+        q.qms_sort(d, side="larger", spin_limit=1, dtype="u32")
     except q.QmsError as e:
         assert e.code == q.QMS_ETIMEOUT
     else:
