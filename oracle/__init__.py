@@ -93,6 +93,15 @@ def lib():
                                              ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                              ctypes.c_void_p, ctypes.c_size_t, szp, u64p]
             L.qms_ref_rounds_u32.restype = ctypes.c_int
+            L.qms_ref_qmqs_u32.argtypes = [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int,
+                                           ctypes.c_int, ctypes.c_size_t, u64p]
+            L.qms_ref_qmqs_u32.restype = ctypes.c_int
+            L.qms_ref_dp_qmqs.argtypes = [ctypes.c_size_t, ctypes.c_size_t, ctypes.c_void_p,
+                                          ctypes.c_void_p]
+            L.qms_ref_dp_qmqs.restype = ctypes.c_int
+            L.qms_ref_out_x_u32.argtypes = [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_size_t,
+                                            ctypes.c_size_t, ctypes.c_int, ctypes.c_size_t, u64p]
+            L.qms_ref_out_x_u32.restype = ctypes.c_int
             _lib = L
     return _lib
 
@@ -189,6 +198,40 @@ def select_u32(a: np.ndarray, i: int, adaptive: bool = False, trace_cap: int = 4
         raise RuntimeError("qms_ref_select_u32 failed")
     k = min(ln.value, trace_cap)
     return pos.value, c.value, tr[: 2 * k].reshape(k, 2)
+
+
+def qmqs_u32(keys: np.ndarray, x_thresh: int, variant: str = "m3", mode: str = "analysis") -> int:
+    """QuickMergeXsort (Sec. 3): Mergesort stops below ``x_thresh`` elements
+    and X = CleverQuicksort sorts the block.  Sorts in place; returns the
+    comparisons."""
+    assert keys.dtype == np.uint32 and keys.flags.c_contiguous
+    c = ctypes.c_uint64(0)
+    rc = lib().qms_ref_qmqs_u32(keys.ctypes.data, len(keys), VARIANTS[variant], MODES[mode],
+                                x_thresh, ctypes.byref(c))
+    if rc != 0:
+        raise RuntimeError("qms_ref_qmqs_u32 failed")
+    return c.value
+
+
+def out_x_u32(a: np.ndarray, b: int, e: int, temp: int, x_thresh: int, mode: str = "analysis") -> int:
+    """Fig. 3 ``out`` with X = CleverQuicksort for msort calls below x_thresh."""
+    assert a.dtype == np.uint32 and a.flags.c_contiguous
+    c = ctypes.c_uint64(0)
+    rc = lib().qms_ref_out_x_u32(a.ctypes.data, b, e, temp, MODES[mode], x_thresh, ctypes.byref(c))
+    if rc != 0:
+        raise RuntimeError("qms_ref_out_x_u32 failed")
+    return c.value
+
+
+def dp_qmqs(nmax: int, x_thresh: int):
+    """Exact-average tables (T, Q) of QuickMergeXsort with X = CleverQuicksort
+    below x_thresh (T) and of CleverQuicksort alone (Q), n = 0..nmax."""
+    T = np.zeros(nmax + 1, dtype=np.float64)
+    Q = np.zeros(nmax + 1, dtype=np.float64)
+    rc = lib().qms_ref_dp_qmqs(nmax, x_thresh, T.ctypes.data, Q.ctypes.data)
+    if rc != 0:
+        raise RuntimeError("qms_ref_dp_qmqs failed")
+    return T, Q
 
 
 ROUND_FIELDS = ("b", "e", "lt", "gt", "mom", "cmp_pivot", "cmp_part", "left")

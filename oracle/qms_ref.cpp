@@ -25,6 +25,11 @@
 //   * An element-move counter [Sec. 5, the moves experiment]: the sort run on
 //     a key type whose construction and assignment from another element
 //     count one move each, so a swap counts three.
+//   * QuickMergeXsort [Sec. 3, Thm. 3]: an option x_thresh > 0 stops the
+//     Mergesort recursion (msort) below x_thresh elements and sorts such a
+//     block with X = CleverQuicksort (median-of-3 quicksort: the same sort3,
+//     Lomuto partition and recursion on both sides), then moves it into its
+//     target; the paper's QMQS takes x_thresh near sqrt(n).
 //   * The MoM details of Sec. 4 as an option ("faithful" MoM): adaptive
 //     selection inside the median-of-medians routine, and a partition of
 //     only the 2n/3 elements that are not medians of triples (the medians
@@ -154,8 +159,9 @@ thread_local uint64_t Counted<K>::moves = 0;
 template <class E, class Less>
 class QuickMergesort {
  public:
-  QuickMergesort(E* a, Less less, int variant, int mode, int side, int mom = 0)
-      : a_(a), less_(less), variant_(variant), mode_(mode), side_(side), mom_(mom) {}
+  QuickMergesort(E* a, Less less, int variant, int mode, int side, int mom = 0, size_t x_thresh = 0)
+      : a_(a), less_(less), variant_(variant), mode_(mode), side_(side), mom_(mom),
+        x_thresh_(x_thresh) {}
 
   uint64_t comparisons() const { return cmps_; }
   uint64_t rounds() const { return rounds_; }
@@ -262,6 +268,12 @@ class QuickMergesort {
   // end up in a[b, e).  r = n - floor(n/2) is used for the odd case.
   void msort(size_t b, size_t e, size_t t) {
     const size_t n = e - b;
+    if (x_thresh_ > 0 && n < x_thresh_) {
+      // QuickMergeXsort: X sorts the block, which then moves to its target.
+      clever_quicksort(b, e);
+      for (size_t i = 0; i < n; ++i) std::swap(a_[b + i], a_[t + i]);
+      return;
+    }
     const size_t leaf = (mode_ == PAPER) ? 10 : 2;
     if (n < leaf) {
       if (mode_ == PAPER) insertion_sort(b, e);
@@ -272,6 +284,30 @@ class QuickMergesort {
     msort(b + q, e, t + q);
     msort(b, b + q, b + r);
     merge(b + r, b + n, t, t + n);
+  }
+
+  // X = CleverQuicksort [Sec. 3]: median-of-3 quicksort.  A range of two
+  // gets one compare-and-swap; from three on, sort3 on the first, middle and
+  // last element, the median parked at b + 1, the other n - 3 elements
+  // compared once each (Lomuto), and both sides sorted the same way.  The
+  // smaller side recurses, the larger one loops (O(log n) stack).
+  void clever_quicksort(size_t b, size_t e) {
+    while (e - b >= 3) {
+      const size_t n = e - b, m = b + n / 2;
+      sort3(b, m, e - 1);
+      std::swap(a_[m], a_[b + 1]);
+      size_t i = lomuto(b + 1, b + 2, e - 1);
+      std::swap(a_[b + 1], a_[i - 1]);
+      const size_t k = i - 1;  // the pivot's final index
+      if (k - b < e - (k + 1)) {
+        clever_quicksort(b, k);
+        b = k + 1;
+      } else {
+        clever_quicksort(k + 1, e);
+        e = k;
+      }
+    }
+    if (e - b == 2 && lt(a_[b + 1], a_[b])) std::swap(a_[b], a_[b + 1]);
   }
 
   void insertion_sort(size_t b, size_t e) {
@@ -357,7 +393,7 @@ class QuickMergesort {
     const size_t step = n / k;
     for (size_t i = 0; i < k; ++i) std::swap(a_[b + i], a_[b + i * step]);
     // Sort the sample with this same algorithm (counted).
-    QuickMergesort inner(a_, less_, variant_, mode_, side_, mom_);
+    QuickMergesort inner(a_, less_, variant_, mode_, side_, mom_, x_thresh_);
     inner.sort(b, b + k);
     cmps_ += inner.comparisons();
     const size_t pm = b + k / 2;
@@ -505,6 +541,7 @@ class QuickMergesort {
   E* a_;
   Less less_;
   int variant_, mode_, side_, mom_;
+  size_t x_thresh_;
   uint64_t cmps_ = 0;
   uint64_t rounds_ = 0;
   uint64_t part_cmps_ = 0;  // comparisons of the last MoM round's partition
@@ -705,6 +742,75 @@ int qms_ref_rounds_u32(uint32_t* keys, size_t n, int variant, int mode, int side
     const RoundRec& r = log[j];
     const uint64_t w[8] = {r.b, r.e, r.lt, r.gt, r.mom, r.cmp_pivot, r.cmp_part, r.left};
     std::memcpy(rec + 8 * j, w, sizeof(w));
+  }
+  return 0;
+}
+
+// Fig. 3 "out" with the QuickMergeXsort stopper: Mergesort of a[b, e) with
+// the buffer at a[temp, ...), X = CleverQuicksort for msort calls below
+// x_thresh elements.
+int qms_ref_out_x_u32(uint32_t* a, size_t b, size_t e, size_t temp, int mode, size_t x_thresh,
+                      uint64_t* cmps) {
+  if (a == nullptr || e < b) return -1;
+  const size_t r = (e - b) - (e - b) / 2;
+  if (temp < e && temp + r > b) return -1;
+  using Less = ByKey<uint32_t, LessU32>;
+  QuickMergesort<uint32_t, Less> s(a, Less{}, M3, mode, 0, 0, x_thresh);
+  s.out(b, e, temp);
+  if (cmps) *cmps = s.comparisons();
+  return 0;
+}
+
+// QuickMergeXsort on uint32 keys [Sec. 3]: the sort with x_thresh (X =
+// CleverQuicksort below x_thresh elements inside Mergesort).
+int qms_ref_qmqs_u32(uint32_t* keys, size_t n, int variant, int mode, size_t x_thresh,
+                     uint64_t* cmps) {
+  if ((keys == nullptr && n > 0) || variant < 0 || variant > 3 || mode < 0 || mode > 1) return -1;
+  using Less = ByKey<uint32_t, LessU32>;
+  QuickMergesort<uint32_t, Less> s(keys, Less{}, variant, mode, 0, 0, x_thresh);
+  if (n > 1) s.sort(0, n);
+  if (cmps) *cmps = s.comparisons();
+  return 0;
+}
+
+// Exact average comparisons of the analysis-mode median-of-3 QuickMergeXsort
+// with X = CleverQuicksort below x_thresh, on random permutations, by the
+// same argument as qms_ref_dp: partitioning keeps both sides random, so
+//   Q(n) = 8/3 + (n - 3) + sum_k Pr[k] (Q(k-1) + Q(n-k)),  Q(2) = 1,
+//   X-msort(n) = Q(n) for n < x_thresh, else the two halves plus E,
+//   out(n) = X-msort(floor(n/2)) + X-msort(ceil(n/2)) + E,
+// and T(n) as in qms_ref_dp with out in place of Mergesort.
+int qms_ref_dp_qmqs(size_t nmax, size_t x_thresh, double* T, double* Q) {
+  if (T == nullptr || Q == nullptr) return -1;
+  std::vector<double> MX(nmax + 1, 0.0), MO(nmax + 1, 0.0);
+  auto pk = [](size_t n, size_t k) {
+    const double nd = static_cast<double>(n);
+    return static_cast<double>(k - 1) * static_cast<double>(n - k) / (nd * (nd - 1.0) * (nd - 2.0) / 6.0);
+  };
+  for (size_t n = 0; n <= nmax; ++n) {
+    if (n <= 1) { Q[n] = 0.0; continue; }
+    if (n == 2) { Q[n] = 1.0; continue; }
+    double s = 0.0;
+    for (size_t k = 1; k <= n; ++k) s += pk(n, k) * (Q[k - 1] + Q[n - k]);
+    Q[n] = 8.0 / 3.0 + static_cast<double>(n - 3) + s;
+  }
+  auto E = [](double a, double b) { return a + b - a / (b + 1.0) - b / (a + 1.0); };
+  for (size_t n = 0; n <= nmax; ++n) {
+    if (n <= 1) { MX[n] = 0.0; MO[n] = 0.0; continue; }
+    const size_t q = n / 2, r = n - q;
+    const double e = E(static_cast<double>(q), static_cast<double>(r));
+    MX[n] = (x_thresh > 0 && n < x_thresh) ? Q[n] : MX[q] + MX[r] + e;
+    MO[n] = MX[q] + MX[r] + e;
+  }
+  for (size_t n = 0; n <= nmax; ++n) {
+    if (n <= 1) { T[n] = 0.0; continue; }
+    if (n == 2) { T[n] = 1.0; continue; }
+    double s = 0.0;
+    for (size_t k = 1; k <= n; ++k) {
+      const double rest = (k - 1 < n / 2) ? (MO[k - 1] + T[n - k]) : (MO[n - k] + T[k - 1]);
+      s += pk(n, k) * rest;
+    }
+    T[n] = 8.0 / 3.0 + static_cast<double>(n - 3) + s;
   }
   return 0;
 }
