@@ -46,11 +46,45 @@ def parse():
     ap.add_argument("--no-configs", action="store_true",
                     help="skip the per-configuration records (C1-C3 workloads)")
     ap.add_argument("--batched-segments", type=int, default=65536)
-    ap.add_argument("--served-requests", type=int, default=2000)
+    ap.add_argument("--served-requests", type=int, default=20000)
     ap.add_argument("--served-lg-max", type=float, default=26.0)
-    ap.add_argument("--served-load", type=float, default=0.8,
-                    help="offered load as a fraction of the plain FIFO throughput")
+    ap.add_argument("--served-loads", default="0.5,0.8,0.95",
+                    help="offered loads as fractions of the plain FIFO throughput")
     return ap.parse_args()
+
+
+class Ranks:
+    """World size, rank and the process group of a torchrun launch (world
+    size 1: no group)."""
+
+    def __init__(self, ws, rank, dist):
+        self.ws, self.rank, self.dist = ws, rank, dist
+
+    def max(self, torch, x):
+        if self.dist is None:
+            return x
+        t = torch.tensor([float(x)], dtype=torch.float64, device="cuda")
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def gather(self, obj):
+        if self.dist is None:
+            return [obj]
+        out = [None] * self.ws
+        self.dist.all_gather_object(out, obj)
+        return out
+
+    def barrier(self):
+        if self.dist is not None:
+            self.dist.barrier()
+
+    def share(self, lengths):
+        """This rank's units (indices) under LPT over n log n costs."""
+        import numpy as np
+        if self.ws == 1:
+            return np.arange(len(lengths))
+        from paper_1804_10062_gb300.shard import lpt_assign
+        return lpt_assign(lengths, self.ws)[self.rank]
 
 
 def dist_init(args):
@@ -249,16 +283,25 @@ def oracle_all_cores(np, keys, off, every=8):
 # batched and served forms
 
 
-def bench_batched(args, q, torch, np):
+def bench_batched(args, q, torch, np, ranks):
     """65,536 segments, lengths log-uniform in [16, 65536], uint32 and
-    float32 U(0,1) keys: one batched call vs one plain call per segment."""
+    float32 U(0,1) keys: one batched call vs one plain call per segment.
+    With several ranks each sorts its LPT share of the segments (no
+    collective on the data path); the time is the maximum over ranks and
+    the throughput counts every rank's keys."""
     import qms_inputs as gen
-    nseg = args.batched_segments
-    L = gen.batch_lengths(nseg, 1, 16, 65536)
+    nseg_all = args.batched_segments
+    L_all = gen.batch_lengths(nseg_all, 1, 16, 65536)
+    off_all = gen.offsets_of(L_all)
+    n_all = int(off_all[-1])
+    mine = ranks.share(L_all)
+    L = L_all[mine]
+    nseg = len(L)
     off = gen.offsets_of(L)
     n = int(off[-1])
     doff = torch.from_numpy(off.view(np.int64)).cuda()
-    out = {"segments": nseg, "keys": n, "lengths": "floor(exp(U(ln 16, ln 65536)))"}
+    out = {"segments": nseg_all, "keys": n_all, "lengths": "floor(exp(U(ln 16, ln 65536)))",
+           "sharding": "LPT over %d ranks (n log n costs)" % ranks.ws if ranks.ws > 1 else "single GPU"}
     peak, _ = measured_peak_hbm()
     # Autotune the per-bin kernel configurations on this GPU (4-byte keys
     # without payloads: uint32 and float32 share the plan), untimed.
@@ -270,7 +313,10 @@ def bench_batched(args, q, torch, np):
                                 for b, c in enumerate(plan)},
                        "report": report.strip().splitlines()}
     for dt in ("u32", "f32"):
-        k = gen.keys("uniform", dt, n, 1)
+        k_all = gen.keys("uniform", dt, n_all, 1)
+        k = k_all if ranks.ws == 1 else np.concatenate(
+            [k_all[int(off_all[i]):int(off_all[i + 1])] for i in mine])
+        del k_all
         src = torch.from_numpy(k.view(np.int32)).cuda()
         cpu_all = oracle_all_cores(np, k, off) if (dt == "u32" and not args.no_cpu_baseline) else None
         del k
@@ -281,12 +327,13 @@ def bench_batched(args, q, torch, np):
         for _ in range(3):
             work.copy_(src)
             torch.cuda.synchronize()
+            ranks.barrier()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
             q.qms_sort_batched(work, doff, dtype=dt, profile=prof)
             e1.record()
             torch.cuda.synchronize()
-            times.append(e0.elapsed_time(e1))
+            times.append(ranks.max(torch, e0.elapsed_time(e1)))
         ms = min(times)
         pb = prof.as_dict()["batch"]
         kern_ms = pb["ms"] / max(1, pb["launches"])
@@ -305,11 +352,11 @@ def bench_batched(args, q, torch, np):
         e1.record()
         torch.cuda.synchronize()
         plain_gk = ks / (e0.elapsed_time(e1) / 1e3) / 1e9
-        v = n / (ms / 1e3) / 1e9
+        v = n_all / (ms / 1e3) / 1e9
         out[dt] = {"value": v, "unit": "GKeys/s", "ms": ms,
                    "plain_per_array": {"value": plain_gk, "unit": "GKeys/s",
                                        "sample": "%d seeded segments, one qms_sort each" % len(idx)},
-                   "speedup_vs_plain": v / plain_gk,
+                   "speedup_vs_plain": (n / (ms / 1e3) / 1e9) / plain_gk,  # one GPU's share
                    "cpu_baseline": cpu_all,
                    "roofline": {"bound": "hbm", "kernel": "k_batched",
                                 "achieved": alg / (kern_ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
@@ -322,51 +369,73 @@ def bench_batched(args, q, torch, np):
     return out
 
 
-def bench_served(args, q, torch, np):
-    """Poisson stream of requests, sizes floor(2^U(10, lg_max)), dtype mix
-    50/30/20 uint32/uint64/float32 uniform, 16 GB HBM budget; inputs are
-    device-resident slices, results go to a device output ring."""
+def bench_served(args, q, torch, np, ranks):
+    """Served form: a Poisson stream of requests (20,000 by default), sizes
+    floor(2^U(10, 26)), dtype mix 50/30/20 uint32/uint64/float32 uniform,
+    admitted against a 16 GB HBM budget.  Inputs live in pinned host memory
+    and results go back to host memory, so every admitted request holds a
+    device slot charged to the budget.  The FIFO baseline sorts the same
+    request list one request at a time through the plain API (upload, sort,
+    download).  Offered loads are fractions of that FIFO throughput; the
+    saturation run submits every request at once.  With several ranks each
+    serves its LPT share of the requests; throughputs count every rank's
+    keys over the longest rank's time and latencies pool all ranks."""
     import qms_inputs as gen
     nreq = args.served_requests
     lg_max = args.served_lg_max
+    loads = [float(x) for x in args.served_loads.split(",") if x]
     maxn = 1 << int(math.ceil(lg_max))
+    esz = {"u32": 4, "u64": 8, "f32": 4}
+    tdt = {"u32": torch.int32, "u64": torch.int64, "f32": torch.int32}
     pristine = {}
     for dt in ("u32", "u64", "f32"):
         k = gen.keys("uniform", dt, maxn, 77)
-        pristine[dt] = torch.from_numpy(k.view(np.int32 if k.itemsize == 4 else np.int64)).cuda()
+        t = torch.empty(maxn, dtype=tdt[dt], pin_memory=True)
+        t.copy_(torch.from_numpy(k.view(np.int32 if k.itemsize == 4 else np.int64)))
+        pristine[dt] = t
         del k
-    reqs0 = gen.request_stream(nreq, 5, 10.0, lg_max, rate_per_s=1.0)
-    esz = {"u32": 4, "u64": 8, "f32": 4}
-    ring_bytes = 24 << 30
-    ring = torch.empty(ring_bytes, dtype=torch.uint8, device="cuda")
-    torch.cuda.synchronize()
+    reqs_all = gen.request_stream(nreq, 5, 10.0, lg_max, rate_per_s=1.0)
+    all_keys = sum(r[1] for r in reqs_all)
+    mine = ranks.share([r[1] for r in reqs_all])
+    reqs0 = [reqs_all[i] for i in mine]
+    total_keys = sum(r[1] for r in reqs0)
+    mean_n = total_keys / len(reqs0)
+    budget = 16 * 10**9
+    # host output ring: every request in flight holds at most the budget
+    ring_bytes = (budget + maxn * 8 + (1 << 30)) // 256 * 256
+    ring = torch.empty(ring_bytes, dtype=torch.uint8, pin_memory=True)
 
     def fifo_plain():
-        # one request at a time through the plain API (saturated), as the
-        # baseline of the served form
-        work = {dt: torch.empty_like(pristine[dt]) for dt in pristine}
-        t0 = time.perf_counter()
-        keys = 0
-        for _, n, dt in reqs0[: max(1, nreq // 4)]:
-            w = work[dt][:n]
-            w.copy_(pristine[dt][:n])
-            q.qms_sort(w, dtype=dt)
-            keys += n
+        dev = {dt: torch.empty(maxn, dtype=tdt[dt], device="cuda") for dt in pristine}
+        st = torch.cuda.current_stream()
         torch.cuda.synchronize()
-        return keys / (time.perf_counter() - t0) / 1e9
+        t0 = time.perf_counter()
+        head = 0
+        for _, n, dt in reqs0:
+            nb = n * esz[dt]
+            if head + nb > ring_bytes:
+                head = 0
+            d = dev[dt][:n]
+            d.copy_(pristine[dt][:n], non_blocking=True)
+            q.qms_sort(d, dtype=dt)  # returns once the sort has finished
+            ring[head: head + nb].view(tdt[dt]).copy_(d, non_blocking=True)
+            head += (nb + 255) // 256 * 256
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        del dev
+        torch.cuda.empty_cache()
+        return total_keys / el / 1e9, el  # this rank's requests
 
     def run(rate_gkeys):
-        mean_n = sum(r[1] for r in reqs0) / len(reqs0)
+        ranks.barrier()
         lam = None if rate_gkeys is None else rate_gkeys * 1e9 / mean_n
-        srv = q.QmsServer(16 * 10**9, max_slots=1024, workers=4, max_batch=4096)
-        out = []
-        live = []  # (ticket, ring_off, nbytes)
+        srv = q.QmsServer(budget, max_slots=1024, workers=4, max_batch=4096)
+        tickets, live, infos = [], [], {}
         head = 0
-        t_start = time.perf_counter()
-        arr = 0.0
         rng = np.random.default_rng(9)
-        infos = {}
-        for i, (_, n, dt) in enumerate(reqs0):
+        arr = 0.0
+        t_start = time.perf_counter()
+        for _, n, dt in reqs0:
             if lam is not None:
                 arr += -math.log1p(-rng.random()) / lam
                 while time.perf_counter() - t_start < arr:
@@ -375,40 +444,46 @@ def bench_served(args, q, torch, np):
             nb_al = (nb + 255) // 256 * 256
             if head + nb_al > ring_bytes:
                 head = 0
-            # wait for outstanding requests overlapping [head, head + nb)
+            # wait for outstanding requests whose outputs overlap [head, head + nb)
             while live and any(o < head + nb_al and head < o + b for _, o, b in live):
                 t, o, b = live.pop(0)
                 infos[t] = srv.qms_server_wait(t, 600000.0)
             src = pristine[dt][:n]
-            dst = ring[head: head + nb]
-            t = srv.qms_server_submit(src.data_ptr(), dst.data_ptr(), n, dt)
+            t = srv.qms_server_submit(src.data_ptr(), ring.data_ptr() + head, n, dt)
             live.append((t, head, nb_al))
-            out.append(t)
+            tickets.append(t)
             head += nb_al
         for t, o, b in live:
             infos[t] = srv.qms_server_wait(t, 600000.0)
-        el = time.perf_counter() - t_start
+        el = ranks.max(torch, time.perf_counter() - t_start)
         st = srv.qms_server_get_stats()
         srv.qms_server_destroy()
-        lat = sorted(infos[t]["latency_ms"] for t in out)
-        keys = sum(r[1] for r in reqs0)
-        return {"sustained": keys / el / 1e9, "unit": "GKeys/s", "p50_ms": lat[len(lat) // 2],
-                "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+        lat = sorted(x for part in ranks.gather([infos[t]["latency_ms"] for t in tickets]) for x in part)
+        bad = sum(ranks.gather(sum(1 for t in tickets if infos[t]["status"] != 0)))
+        return {"sustained": all_keys / el / 1e9, "unit": "GKeys/s",
+                "offered_GKeys_s": None if rate_gkeys is None else rate_gkeys * ranks.ws,
+                "p50_ms": lat[len(lat) // 2], "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
                 "mean_batch": st["batched_requests"] / max(1, st["batches"]),
-                "peak_in_flight": st["peak_in_flight"],
-                "peak_used_GB": st["peak_used_bytes"] / 1e9, "wall_s": el}
+                "peak_in_flight": st["peak_in_flight"], "peak_used_GB": st["peak_used_bytes"] / 1e9,
+                "wall_s": el, "failed_requests": bad}
 
-    fifo = fifo_plain()
+    ranks.barrier()
+    fifo_local, fifo_s = fifo_plain()
+    fifo_s = ranks.max(torch, fifo_s)
+    fifo = all_keys / fifo_s / 1e9
+    out = {"requests": nreq, "keys": all_keys, "sizes": "floor(2^U(10, %g))" % lg_max,
+           "dtype_mix": "50/30/20 u32/u64/f32 uniform", "budget_GB": budget / 1e9,
+           "inputs": "pinned host memory; results written back to pinned host memory",
+           "fifo_plain": {"value": fifo, "unit": "GKeys/s", "wall_s": fifo_s,
+                          "sample": "the same %d requests one at a time: upload, qms_sort, "
+                                    "download" % nreq}}
     sat = run(None)
-    load = run(args.served_load * fifo)
-    # spot check: one request alone equals its slice sorted
-    return {"requests": nreq, "sizes": "floor(2^U(10, %g))" % lg_max,
-            "dtype_mix": "50/30/20 u32/u64/f32 uniform", "budget_GB": 16,
-            "fifo_plain": {"value": fifo, "unit": "GKeys/s",
-                           "sample": "first %d requests back to back, one qms_sort each" %
-                                     max(1, nreq // 4)},
-            "saturation": sat, "offered_%.2f" % args.served_load: load,
-            "speedup_vs_fifo_plain": sat["sustained"] / fifo}
+    out["saturation"] = sat
+    for rho in loads:
+        out["offered_%.2f" % rho] = run(rho * fifo_local)  # per rank: rho x its own FIFO rate
+    out["speedup_vs_fifo_plain"] = sat["sustained"] / fifo
+    # one request alone equals its slice sorted (spot check of the served path)
+    return out
 
 
 def _to_dev(torch, np, k):
@@ -461,7 +536,7 @@ def plain_record(q, torch, np, k, dtype, pivot, dist, pairs=False, reps=3, count
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record()
-        sort(wait=False)
+        sort()
         e1.record()
         torch.cuda.synchronize()
         ts.append(e0.elapsed_time(e1))
@@ -619,8 +694,10 @@ def run_qms(args):
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for i in range(args.steps):
-        # device-driven sort: the whole round loop is one CUDA graph launch
-        q.qms_sort(bufs[i], pivot=args.pivot, dtype=args.dtype, wait=False)
+        # the plain API: each call returns once its sort has finished (arrays
+        # this large run their rounds from the host; smaller ones as one
+        # device-driven CUDA graph)
+        q.qms_sort(bufs[i], pivot=args.pivot, dtype=args.dtype)
     e1.record(stream)
     torch.cuda.synchronize()
     barrier()
@@ -702,15 +779,22 @@ def run_qms(args):
             up = [torch.cuda.Event() for _ in range(steps)]
             srt = [torch.cuda.Event() for _ in range(steps)]
             down = [torch.cuda.Event() for _ in range(steps)]
-            for i in range(steps):
-                d = dbuf[i % 2]
+
+            def upload(i):
                 with torch.cuda.stream(s_up):
                     if i >= 2:
                         s_up.wait_event(down[i - 2])  # this buffer's previous result is out
-                    d.copy_(hbuf, non_blocking=True)
+                    dbuf[i % 2].copy_(hbuf, non_blocking=True)
                     up[i].record(s_up)
+
+            upload(0)
+            for i in range(steps):
+                d = dbuf[i % 2]
+                if i + 1 < steps:
+                    upload(i + 1)  # enqueued before the sort, so it overlaps it
                 s_sort.wait_event(up[i])
-                q.qms_sort(d, pivot=args.pivot, dtype=args.dtype, stream=s_sort, wait=False)
+                # the plain API; it returns once the sort has finished
+                q.qms_sort(d, pivot=args.pivot, dtype=args.dtype, stream=s_sort)
                 srt[i].record(s_sort)
                 with torch.cuda.stream(s_down):
                     s_down.wait_event(srt[i])
@@ -760,8 +844,9 @@ def run_qms(args):
     if not args.no_forms:
         bufs, work = [], None
         torch.cuda.empty_cache()
-        forms = {"batched": bench_batched(args, q, torch, np),
-                 "served": bench_served(args, q, torch, np)}
+        ranks = Ranks(ws, rank, dist)
+        forms = {"batched": bench_batched(args, q, torch, np, ranks),
+                 "served": bench_served(args, q, torch, np, ranks)}
 
     if rank == 0:
         line = {"metric": METRIC,

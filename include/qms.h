@@ -129,12 +129,15 @@ const char* qms_error_string(int code);
 /* Sorts d_keys[0, n) in place, ascending (the QuickMergesort driver loop of
  * Fig. 3: partition, Mergesort the side left of the midpoint test, continue
  * on the other side; a last range of at most one Mergesort leaf -- 16384
- * keys, 8192 with payloads -- is finished by the base case).  By default
- * the whole round loop runs on the device as one CUDA graph with
- * conditional nodes (instances are cached per key type, pivot rule and
- * device; the first call of a kind builds one) and the call returns
- * after the sort finished; with QMS_FLAG_ASYNC and stats == NULL it returns
- * once the sort is enqueued on `stream`.  Errors: QMS_EINVAL (d_keys NULL
+ * keys, 8192 with payloads -- is finished by the base case).  The round
+ * loop runs on the device as one CUDA graph with conditional nodes
+ * (instances are cached per key type, pivot rule and device; the first call
+ * of a kind builds one), and the call returns after the sort finished; with
+ * QMS_FLAG_ASYNC and stats == NULL it returns once the sort is enqueued on
+ * `stream`.  A call that waits for arrays of 2^26 keys or more runs the
+ * rounds from the host instead (as QMS_FLAG_HOST_DRIVEN), which is faster
+ * there: one small read-back per round costs less than the graph's
+ * conditional nodes.  Errors: QMS_EINVAL (d_keys NULL
  * with n > 1, bad dtype or pivot), QMS_ENOMEM, QMS_ECUDA, QMS_EINTERNAL,
  * QMS_ETIMEOUT (a bounded device wait gave up; see qms_options.spin_limit). */
 int qms_sort(void* d_keys, size_t n, int dtype, const qms_options* opt, void* stream,
@@ -218,12 +221,17 @@ const char* qms_batched_config_name(int cfg);
  * admitted in arrival order against a device-memory budget -- the bytes the
  * server itself holds for a request: a device slot for its keys, unless the
  * keys are a device array sorted in place (in == out), plus the sort's
- * workspace (about n/27 bytes) -- and a maximum number of admitted requests.
- * Worker threads, each with its own stream, run admitted work concurrently:
- * a request longer than 64 * 8192 keys runs alone through the grid-wide
- * rounds; shorter ones waiting at the head of the queue are sorted together
- * in one persistent launch (one block each, longest first).  Requests never
- * share memory, so each result equals that request's sort alone. */
+ * workspace (charged as n/16 bytes + 64 KB) -- and a maximum number of
+ * admitted requests.  A staging thread admits the next request as soon as
+ * it fits, allocates its slot and starts the upload of its keys, so admitted
+ * requests hold their share of the budget while they wait and uploads
+ * overlap earlier sorts.  Worker threads, each with its own stream, take
+ * admitted requests in order: a request longer than 64 * 8192 keys runs
+ * alone through the grid-wide rounds; shorter ones waiting at the head are
+ * sorted together in one persistent launch (one block each, longest first).
+ * Results are copied out and the slot freed before a request completes.
+ * Requests never share memory, so each result equals that request's sort
+ * alone. */
 typedef struct qms_server qms_server;
 
 typedef struct {
@@ -266,9 +274,10 @@ int qms_server_wait(qms_server* srv, uint64_t ticket, double timeout_ms, qms_req
 
 int qms_server_get_stats(qms_server* srv, qms_server_stats* out);
 
-/* Host-side control for failure handling and tests: while paused, workers
- * take no new request (work already on the GPU finishes); waits on queued
- * requests then run into their timeouts.  paused = 0 resumes. */
+/* Host-side control for failure handling and tests: while paused, nothing
+ * new is admitted and workers take no new request (work already on the GPU
+ * finishes); waits on queued requests then run into their timeouts.
+ * paused = 0 resumes. */
 int qms_server_pause(qms_server* srv, int paused);
 
 /* Finishes every queued request, stops the workers and frees the server. */

@@ -190,6 +190,43 @@ class Profiler {
   std::vector<Rec> recs_;
 };
 
+// Stores a partition pass's result (left count, misplaced pairs, tie and
+// error bits) into mapped host memory for the host-driven driver.
+__global__ void k_report(const Desc* d, unsigned long long* out) {
+  if (threadIdx.x != 0) return;
+  out[0] = d->L;
+  out[1] = d->mis;
+  out[2] = static_cast<unsigned long long>(d->tie) | (static_cast<unsigned long long>(d->err) << 32);
+  __threadfence_system();
+}
+
+// Mapped pinned host words for k_report, one block per host thread and
+// device (host-driven sorts are synchronous, so a thread runs one at a time);
+// allocated on first use and kept.  Null if the allocation fails.
+unsigned long long* report_words() {
+  struct Slots {
+    std::map<int, unsigned long long*> by_dev;
+    ~Slots() {
+      for (auto& kv : by_dev) cudaFreeHost(kv.second);
+    }
+  };
+  thread_local Slots slots;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return nullptr;
+  }
+  auto it = slots.by_dev.find(dev);
+  if (it != slots.by_dev.end()) return it->second;
+  void* p = nullptr;
+  if (cudaHostAlloc(&p, 64, cudaHostAllocMapped) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return nullptr;
+  }
+  slots.by_dev[dev] = static_cast<unsigned long long*>(p);
+  return static_cast<unsigned long long*>(p);
+}
+
 template <class K, bool HV, bool CNT>
 class Sorter {
  public:
@@ -205,6 +242,9 @@ class Sorter {
   bool fig3_side = true;         // Fig. 3's side rule; false: the larger side when it fits
   unsigned spin_limit = kOvlSpinLimit;  // polls of one flag in a bounded device wait
   int withhold = 0;                     // test hook (QMS_FLAG_TEST_WITHHOLD)
+  // Mapped pinned host words the round results are stored to (null: the
+  // results are copied back with cudaMemcpyAsync instead).
+  unsigned long long* report_ = nullptr;
 
   // ---- steps ------------------------------------------------------------
 
@@ -369,9 +409,22 @@ class Sorter {
       unsigned long long L, mis;
       unsigned tie, err;
     } h;
-    ck(cudaMemcpyAsync(&h.L, &ws_.desc->L, 2 * sizeof(h.L), cudaMemcpyDeviceToHost, st_));
-    ck(cudaMemcpyAsync(&h.tie, &ws_.desc->tie, 2 * sizeof(unsigned), cudaMemcpyDeviceToHost, st_));
-    ck(cudaStreamSynchronize(st_));
+    if (report_) {
+      // A kernel stores the round's result into mapped host memory: no copy
+      // engine is involved, so the read-back does not queue behind large
+      // copies that other streams may have in flight.
+      k_report<<<1, 32, 0, st_>>>(ws_.desc, report_);
+      ck(cudaStreamSynchronize(st_));
+      const volatile unsigned long long* r = report_;
+      h.L = r[0];
+      h.mis = r[1];
+      h.tie = static_cast<unsigned>(r[2]);
+      h.err = static_cast<unsigned>(r[2] >> 32);
+    } else {
+      ck(cudaMemcpyAsync(&h.L, &ws_.desc->L, 2 * sizeof(h.L), cudaMemcpyDeviceToHost, st_));
+      ck(cudaMemcpyAsync(&h.tie, &ws_.desc->tie, 2 * sizeof(unsigned), cudaMemcpyDeviceToHost, st_));
+      ck(cudaStreamSynchronize(st_));
+    }
     ck(cudaGetLastError());
     if (h.err) throw Err{err_code(h.err)};
     if (tie) *tie = h.tie;
@@ -898,6 +951,7 @@ int run_typed(const Args& a, qms_stats* stats, Fn&& fn) {
   ws.alloc(a.n, a.st);
   Profiler prof(a.prof);
   Sorter<K, HV, CNT> s(static_cast<K*>(a.keys), a.vals, xform_of(a.dtype), a.st, ws, prof);
+  s.report_ = report_words();
   fn(s);
   unsigned long long cmp = 0;
   unsigned err = 0;
@@ -938,6 +992,9 @@ int dispatch(const Args& a, qms_stats* stats, Fn&& fn) {
 }
 
 bool valid_dtype(int d) { return d >= QMS_U32 && d <= QMS_F32; }
+
+// Arrays from this size on are sorted host-driven by calls that wait.
+constexpr uint64_t kHostDrivenMinN = 1ull << 26;
 
 // Polls of one flag before a bounded device wait gives up.
 unsigned spin_limit_of(const qms_options* opt) {
@@ -1226,6 +1283,7 @@ int run_batched(void* keys, uint32_t* vals, const uint64_t* d_off, size_t nseg, 
       ck(cudaMemsetAsync(ws.desc, 0, sizeof(Desc), st));
       Sorter<K, HV, CNT> srt(static_cast<K*>(keys) + off[i], HV ? vals + off[i] : nullptr, xf, st, ws,
                              prof);
+      srt.report_ = report_words();
       srt.sort(off[i + 1] - off[i], pivot);
       rounds += srt.rounds;
       mom_rounds += srt.mom_rounds;
@@ -1513,7 +1571,15 @@ static int sort_common(void* d_keys, uint32_t* d_vals, size_t n, int dtype, cons
   if (d_vals != nullptr && n >= (1ull << 32)) return QMS_EINVAL;
   Args a{d_keys, d_vals, n, dtype, pivot, opt && opt->count_cmps, static_cast<cudaStream_t>(stream),
          opt ? opt->profile : nullptr};
-  const bool host_driven = (opt && (opt->profile || (opt->flags & QMS_FLAG_HOST_DRIVEN)));
+  // A call that waits for its result runs the rounds from the host once the
+  // array is large: one small read-back per round then costs less than the
+  // graph's conditional nodes (2^28 keys: 17.7 ms against 18.8; at 2^24 the
+  // graph is ahead, 3.17 against 3.28 ms).  Asynchronous calls always take
+  // the graph, which needs no host thread.
+  const bool wait = !(opt && (opt->flags & QMS_FLAG_ASYNC)) || stats != nullptr;
+  const bool big_sync = wait && n >= kHostDrivenMinN && std::getenv("QMS_GRAPH_ALWAYS") == nullptr;
+  const bool host_driven =
+      (opt && (opt->profile || (opt->flags & QMS_FLAG_HOST_DRIVEN))) || big_sync;
   const bool fig3 = !(opt && (opt->flags & QMS_FLAG_LARGER_SIDE));
   const unsigned spin = spin_limit_of(opt);
   const int withhold = (opt && (opt->flags & QMS_FLAG_TEST_WITHHOLD)) ? 1 : 0;

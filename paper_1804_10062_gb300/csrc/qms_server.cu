@@ -62,6 +62,8 @@ struct Req {
   int pivot = 0;
   bool in_place = false;  // in == out is a device array: sorted where it is
   size_t bytes = 0;       // budget charge
+  void* slot = nullptr;   // device copy of the keys (not in place)
+  cudaEvent_t ready = nullptr;  // recorded once the keys are in the slot
   int rc = QMS_OK;
   bool done = false;
   int batch = 0;
@@ -77,8 +79,9 @@ struct qms_server {
   int max_batch = 0;
   int device = 0;
   std::mutex mu;
-  std::condition_variable cv_work, cv_done;
-  std::deque<qms::Req*> pending;
+  std::condition_variable cv_work, cv_ready, cv_done;
+  std::deque<qms::Req*> pending;  // submitted, not admitted yet
+  std::deque<qms::Req*> ready;    // admitted: slot held, keys staged or on their way
   std::unordered_map<uint64_t, qms::Req*> reqs;
   uint64_t next_id = 1;
   size_t used = 0, peak_used = 0;
@@ -86,6 +89,8 @@ struct qms_server {
   uint64_t completed = 0, keys_done = 0, batches = 0, batched_reqs = 0;
   bool stop = false;
   bool paused = false;
+  bool staging_done = false;
+  std::thread stager;
   std::vector<std::thread> workers;
 };
 
@@ -113,44 +118,19 @@ void admit(qms_server* S, Req* r) {
   r->t_admit = Clock::now();
 }
 
-// Sorts one long request alone through the grid-wide driver.
+// Sorts one long request alone through the grid-wide driver, in its slot.
 int run_long(Req* r, cudaStream_t st) {
-  const size_t kb = r->n * key_bytes(r->dtype);
-  void* slot = nullptr;
-  if (!r->in_place) {
-    if (cudaMallocAsync(&slot, kb, st) != cudaSuccess) {
-      (void)cudaGetLastError();
-      return QMS_ENOMEM;
-    }
-    if (cudaMemcpyAsync(slot, r->in, kb, cudaMemcpyDefault, st) != cudaSuccess) {
-      cudaFreeAsync(slot, st);
-      return QMS_ECUDA;
-    }
-  }
   qms_options opt{};
   opt.pivot = r->pivot;
-  int rc = qms_sort(r->in_place ? r->out : slot, r->n, r->dtype, &opt, st, nullptr);
-  if (!r->in_place) {
-    if (rc == QMS_OK && cudaMemcpyAsync(r->out, slot, kb, cudaMemcpyDefault, st) != cudaSuccess)
-      rc = QMS_ECUDA;
-    cudaFreeAsync(slot, st);
-  }
-  if (cudaStreamSynchronize(st) != cudaSuccess && rc == QMS_OK) rc = QMS_ECUDA;
-  return rc;
+  return qms_sort(r->in_place ? r->out : r->slot, r->n, r->dtype, &opt, st, nullptr);
 }
 
 template <class K>
 int run_group_typed(std::vector<Req*>& g, cudaStream_t st, int pivot) {
-  // One allocation: Desc + ticket, segment descriptors, then the slots.
+  // One allocation: Desc + ticket, then the segment descriptors; the keys
+  // are in the requests' slots (or in place).
   const size_t hdr = r256(sizeof(Desc)) + 256;
-  const size_t segb = r256(g.size() * sizeof(SegDesc));
-  size_t total = hdr + segb;
-  std::vector<size_t> slot_off(g.size(), 0);
-  for (size_t i = 0; i < g.size(); ++i) {
-    if (g[i]->in_place) continue;
-    slot_off[i] = total;
-    total += r256(g[i]->n * sizeof(K));
-  }
+  const size_t total = hdr + r256(g.size() * sizeof(SegDesc));
   unsigned char* base = nullptr;
   if (cudaMallocAsync(reinterpret_cast<void**>(&base), total, st) != cudaSuccess) {
     (void)cudaGetLastError();
@@ -170,9 +150,7 @@ int run_group_typed(std::vector<Req*>& g, cudaStream_t st, int pivot) {
   std::vector<SegDesc> hs(g.size());
   for (size_t j = 0; j < ord.size(); ++j) {
     Req* r = g[ord[j]];
-    void* p = r->in_place ? r->out : static_cast<void*>(base + slot_off[ord[j]]);
-    if (!r->in_place) ok(cudaMemcpyAsync(p, r->in, r->n * sizeof(K), cudaMemcpyDefault, st));
-    hs[j] = SegDesc{p, r->n, xform(r->dtype), 0};
+    hs[j] = SegDesc{r->in_place ? r->out : r->slot, r->n, xform(r->dtype), 0};
   }
   ok(cudaMemsetAsync(base, 0, hdr, st));
   ok(cudaMemcpyAsync(segs, hs.data(), hs.size() * sizeof(SegDesc), cudaMemcpyHostToDevice, st));
@@ -189,11 +167,6 @@ int run_group_typed(std::vector<Req*>& g, cudaStream_t st, int pivot) {
         segs, static_cast<uint32_t>(g.size()), ticket, pivot, desc);
     ok(cudaGetLastError());
   }
-  for (size_t j = 0; j < ord.size(); ++j) {
-    Req* r = g[ord[j]];
-    if (!r->in_place && rc == QMS_OK)
-      ok(cudaMemcpyAsync(r->out, hs[j].keys, r->n * sizeof(K), cudaMemcpyDefault, st));
-  }
   unsigned err = 0;
   ok(cudaMemcpyAsync(&err, &desc->err, sizeof(err), cudaMemcpyDeviceToHost, st));
   cudaFreeAsync(base, st);
@@ -202,6 +175,69 @@ int run_group_typed(std::vector<Req*>& g, cudaStream_t st, int pivot) {
   return rc;
 }
 
+// Admission and staging, in arrival order: a request is admitted once its
+// bytes fit the budget (and a slot count is free); its device slot is
+// allocated and its keys start their upload at once, so admitted requests
+// hold their share of the budget while they wait for a worker, and uploads
+// overlap the sorts of earlier requests.
+void stager_loop(qms_server* S) {
+  cudaSetDevice(S->device);
+  cudaStream_t st = nullptr;
+  if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+    (void)cudaGetLastError();
+    st = nullptr;
+  }
+  while (true) {
+    Req* r = nullptr;
+    {
+      std::unique_lock<std::mutex> lk(S->mu);
+      S->cv_work.wait(lk, [&] {
+        return (S->stop && S->pending.empty()) ||
+               (!S->paused && !S->pending.empty() && fits(S, S->pending.front()));
+      });
+      if (S->pending.empty()) break;  // stopping and drained
+      r = S->pending.front();
+      S->pending.pop_front();
+      admit(S, r);
+    }
+    int rc = QMS_OK;
+    if (!r->in_place) {
+      const size_t kb = r->n * key_bytes(r->dtype);
+      if (cudaMallocAsync(&r->slot, kb, st) != cudaSuccess) {
+        (void)cudaGetLastError();
+        r->slot = nullptr;
+        rc = QMS_ENOMEM;
+      } else if (cudaMemcpyAsync(r->slot, r->in, kb, cudaMemcpyDefault, st) != cudaSuccess) {
+        (void)cudaGetLastError();
+        rc = QMS_ECUDA;
+      }
+    }
+    if (rc == QMS_OK && (cudaEventCreateWithFlags(&r->ready, cudaEventDisableTiming) != cudaSuccess ||
+                         cudaEventRecord(r->ready, st) != cudaSuccess)) {
+      (void)cudaGetLastError();
+      rc = QMS_ECUDA;
+    }
+    r->rc = rc;
+    {
+      std::lock_guard<std::mutex> lk(S->mu);
+      S->ready.push_back(r);
+    }
+    S->cv_ready.notify_one();
+  }
+  if (st) {
+    cudaStreamSynchronize(st);
+    cudaStreamDestroy(st);
+  }
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->staging_done = true;
+  }
+  S->cv_ready.notify_all();
+}
+
+// Workers take admitted requests in order: a request longer than
+// kShortMax keys runs alone through the grid-wide rounds; shorter ones
+// waiting at the head are sorted together in one launch (one block each).
 void worker_loop(qms_server* S) {
   cudaSetDevice(S->device);
   cudaStream_t st = nullptr;
@@ -213,34 +249,50 @@ void worker_loop(qms_server* S) {
     std::vector<Req*> g;
     {
       std::unique_lock<std::mutex> lk(S->mu);
-      S->cv_work.wait(lk, [&] {
-        return (S->stop && S->pending.empty()) ||
-               (!S->paused && !S->pending.empty() && fits(S, S->pending.front()));
+      S->cv_ready.wait(lk, [&] {
+        return (!S->paused && !S->ready.empty()) || (S->staging_done && S->ready.empty());
       });
-      if (S->pending.empty()) break;  // stopping and drained
-      Req* h = S->pending.front();
-      S->pending.pop_front();
-      admit(S, h);
+      if (S->ready.empty()) break;  // staging finished and everything sorted
+      Req* h = S->ready.front();
+      S->ready.pop_front();
       g.push_back(h);
-      if (h->n <= kShortMax) {
-        // Continuous batching: every admissible short request of the same
-        // key width waiting behind the head joins this launch.
-        while (!S->pending.empty() && static_cast<int>(g.size()) < S->max_batch) {
-          Req* r = S->pending.front();
-          if (r->n > kShortMax || key_bytes(r->dtype) != key_bytes(h->dtype) || !fits(S, r)) break;
-          S->pending.pop_front();
-          admit(S, r);
+      if (h->n <= kShortMax && h->rc == QMS_OK) {
+        // Continuous batching: every admitted short request of the same key
+        // width waiting behind the head joins this launch.
+        while (!S->ready.empty() && static_cast<int>(g.size()) < S->max_batch) {
+          Req* r = S->ready.front();
+          if (r->n > kShortMax || key_bytes(r->dtype) != key_bytes(h->dtype) || r->rc != QMS_OK) break;
+          S->ready.pop_front();
           g.push_back(r);
         }
       }
-      if (!S->pending.empty()) S->cv_work.notify_one();
+      if (!S->ready.empty()) S->cv_ready.notify_one();
     }
-    int rc;
-    if (g.size() == 1 && g[0]->n > kShortMax) {
-      rc = run_long(g[0], st);
-    } else {
-      rc = key_bytes(g[0]->dtype) == 8 ? run_group_typed<uint64_t>(g, st, g[0]->pivot)
-                                       : run_group_typed<uint32_t>(g, st, g[0]->pivot);
+    for (Req* r : g)
+      if (r->ready) cudaStreamWaitEvent(st, r->ready, 0);  // its keys are in the slot
+    int rc = g[0]->rc;
+    if (rc == QMS_OK) {
+      if (g.size() == 1 && g[0]->n > kShortMax) {
+        rc = run_long(g[0], st);
+      } else {
+        rc = key_bytes(g[0]->dtype) == 8 ? run_group_typed<uint64_t>(g, st, g[0]->pivot)
+                                         : run_group_typed<uint32_t>(g, st, g[0]->pivot);
+      }
+    }
+    for (Req* r : g) {
+      if (r->in_place || r->slot == nullptr) continue;
+      if (rc == QMS_OK &&
+          cudaMemcpyAsync(r->out, r->slot, r->n * key_bytes(r->dtype), cudaMemcpyDefault, st) != cudaSuccess) {
+        (void)cudaGetLastError();
+        rc = QMS_ECUDA;
+      }
+      cudaFreeAsync(r->slot, st);
+      r->slot = nullptr;
+    }
+    if (cudaStreamSynchronize(st) != cudaSuccess && rc == QMS_OK) rc = QMS_ECUDA;
+    for (Req* r : g) {
+      if (r->ready) cudaEventDestroy(r->ready);
+      r->ready = nullptr;
     }
     {
       std::lock_guard<std::mutex> lk(S->mu);
@@ -299,6 +351,7 @@ int qms_server_create(size_t hbm_budget_bytes, int max_slots, int workers, int m
     delete S;
     return QMS_ECUDA;
   }
+  S->stager = std::thread(stager_loop, S);
   for (int i = 0; i < workers; ++i) S->workers.emplace_back(worker_loop, S);
   *out = S;
   return QMS_OK;
@@ -319,7 +372,7 @@ int qms_server_submit(qms_server* S, const void* in, void* out, size_t n, int dt
   r->pivot = pivot;
   r->in_place = (in == out) && n > 0 && is_device_ptr(out);
   const size_t data = r->in_place ? 0 : r256(n * key_bytes(dtype));
-  r->bytes = data + 3 * (n / TILE + 3) * 8 + 4096;
+  r->bytes = data + n / 16 + 65536;  // slot plus the sort's workspace (about n/27 bytes)
   if (r->bytes > S->budget) {
     delete r;
     return QMS_EBUDGET;
@@ -406,6 +459,7 @@ int qms_server_pause(qms_server* S, int paused) {
     S->paused = paused != 0;
   }
   S->cv_work.notify_all();
+  S->cv_ready.notify_all();
   return QMS_OK;
 }
 
@@ -417,6 +471,8 @@ int qms_server_destroy(qms_server* S) {
     S->paused = false;
   }
   S->cv_work.notify_all();
+  S->cv_ready.notify_all();
+  S->stager.join();
   for (auto& t : S->workers) t.join();
   for (auto& kv : S->reqs) delete kv.second;
   delete S;

@@ -75,10 +75,22 @@ def test_full_size_2_28(q, dtype, dist, pivot, seed):
     n = 1 << 28
     k = gen.keys(dist, dtype, n, seed)
     d = _dev(k)
-    q.qms_sort(d, pivot=pivot, dtype=dtype)
+    q.qms_sort(d, pivot=pivot, dtype=dtype)  # a waiting call: host-driven rounds at this size
     out = _host(d, dtype)
     del d
     _check_keys(k, out, dtype, seed=seed)
+
+
+def test_full_size_2_28_device_driven(q):
+    # The same workload as the benchmark through the device-driven graph (an
+    # asynchronous call, which always takes the graph).
+    n = 1 << 28
+    k = gen.keys("uniform", "u32", n, 2)
+    d = _dev(k)
+    q.qms_sort(d, pivot="m3", dtype="u32", wait=False)
+    out = _host(d, "u32")
+    del d
+    _check_keys(k, out, "u32", seed=2)
 
 
 @pytest.mark.parametrize("dist", ["uniform", "mod16", "killer"])
