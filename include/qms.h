@@ -52,7 +52,7 @@ extern "C" {
 /* Pivot rules (qms_options.pivot).
  *   M3     : median of positions b, b + floor(n/2), e - 1 (Sec. 2, Thm. 1).
  *   SQRTN  : median of an evenly spaced sample of the largest odd k <=
- *            ceil(sqrt n) elements, k capped at 8191 (Sec. 2, Thm. 2).
+ *            ceil(sqrt n) elements, k capped at 16383 (Sec. 2, Thm. 2).
  *   MOM    : exact median of the floor(n/3) medians of consecutive triples
  *            (MoMQuickMergesort, Sec. 4; the selection is a radix select).
  *   HYBRID : M3, but a pivot whose rank lies outside [n/16, n - 1 - n/16]

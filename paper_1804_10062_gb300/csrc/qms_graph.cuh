@@ -154,26 +154,26 @@ __global__ void k_g_begin(DState* S, cudaGraphConditionalHandle h_round) {
 
 // Median-of-sqrt(n) sample pivot (one block).
 template <class K, bool HV, bool CNT>
-__global__ void __launch_bounds__(NT) k_g_pivot_sample(DState* S) {
+__global__ void __launch_bounds__(SAMPLE_T) k_g_pivot_sample(DState* S) {
   count_launch(S);
   DState& s = *S;
   if (!s.active || s.rule != RULE_SQRTN) return;
   extern __shared__ __align__(16) unsigned char smem[];
-  const auto sm = TileSmem<K, true>::carve(smem);
+  const auto sm = TileSmem<K, true, SAMPLE_T, V>::carve(smem);
   uint64_t cmp = 0;
   const uint64_t b = s.b, e = s.e, n = e - b;
   uint64_t c = 1;
   while (c * c < n) ++c;
   uint64_t kk = (c & 1) ? c : c - 1;
-  if (kk > static_cast<uint64_t>(TILE - 1)) kk = TILE - 1;
+  if (kk > static_cast<uint64_t>(SAMPLE_MAX)) kk = SAMPLE_MAX;
   const int ks = static_cast<int>(kk);
   const uint64_t step = n / kk;
   K* keys = static_cast<K*>(s.keys);
-  for (int i = threadIdx.x; i < TILE; i += NT) {
+  for (int i = threadIdx.x; i < SAMPLE_T * V; i += SAMPLE_T) {
     sm.k[sk_i<K>(i)] = (i < ks) ? enc_key(keys[b + static_cast<uint64_t>(i) * step], s.xf) : key_max<K>();
     sm.v[sv_i(i)] = static_cast<uint32_t>(i);
   }
-  block_sort_tile<K, true, CNT>(sm, cmp);
+  block_sort_tile<K, true, CNT, SAMPLE_T, V>(sm, cmp);
   if (CNT) flush_count(cmp, &s.desc->cmp);
   if (threadIdx.x == 0) {
     const int h = ks / 2;

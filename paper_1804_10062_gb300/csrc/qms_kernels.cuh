@@ -115,20 +115,26 @@ __global__ void k_pivot_m3(K* keys, uint32_t* vals, uint64_t b, uint64_t e, int 
   if (CNT) desc->cmp += c + 2;
 }
 
-// Median of a sample of ks (odd, <= TILE - 1) elements at b + i*step
+// The median-of-sqrt(n) sample is sorted by one block of SAMPLE_T threads
+// with V keys each, so it may hold SAMPLE_MAX = SAMPLE_T * V - 1 keys: about
+// sqrt(n) up to n = 2^28.
+constexpr int SAMPLE_T = 2 * NT;
+constexpr int SAMPLE_MAX = SAMPLE_T * V - 1;
+
+// Median of a sample of ks (odd, <= SAMPLE_MAX) elements at b + i*step
 // (median-of-sqrt(n), Sec. 2 / Thm. 2).  One block sorts the sample with the
 // base-case sort, carrying the sample index as payload.
 template <class K, bool HV, bool CNT>
-__global__ void __launch_bounds__(NT) k_pivot_sample(K* keys, uint32_t* vals, uint64_t b, uint64_t e,
-                                                     int ks, uint64_t step, int xf, Desc* desc) {
+__global__ void __launch_bounds__(SAMPLE_T) k_pivot_sample(K* keys, uint32_t* vals, uint64_t b, uint64_t e,
+                                                           int ks, uint64_t step, int xf, Desc* desc) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const auto s = TileSmem<K, true>::carve(smem);
+  const auto s = TileSmem<K, true, SAMPLE_T, V>::carve(smem);
   uint64_t cmp = 0;
-  for (int i = threadIdx.x; i < TILE; i += NT) {
+  for (int i = threadIdx.x; i < SAMPLE_T * V; i += SAMPLE_T) {
     s.k[sk_i<K>(i)] = (i < ks) ? enc_key(keys[b + static_cast<uint64_t>(i) * step], xf) : key_max<K>();
     s.v[sv_i(i)] = static_cast<uint32_t>(i);
   }
-  block_sort_tile<K, true, CNT>(s, cmp);
+  block_sort_tile<K, true, CNT, SAMPLE_T, V>(s, cmp);
   if (CNT) flush_count(cmp, &desc->cmp);
   if (threadIdx.x == 0) {
     const int h = ks / 2;

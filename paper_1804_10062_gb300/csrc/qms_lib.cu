@@ -234,7 +234,7 @@ class Sorter {
       : keys_(keys), vals_(vals), xf_(xf), st_(st), ws_(ws), prof_(prof) {
     allow_smem(k_leaf_sort<K, HV, CNT>,
                tile_smem_bytes<K, HV, LeafCfg<K, HV>::LT, LeafCfg<K, HV>::VL>());
-    allow_smem(k_pivot_sample<K, HV, CNT>, tile_smem_bytes<K, true>());
+    allow_smem(k_pivot_sample<K, HV, CNT>, tile_smem_bytes<K, true, SAMPLE_T, V>());
   }
 
   uint64_t rounds = 0, mom_rounds = 0, launches = 0;
@@ -331,10 +331,10 @@ class Sorter {
       uint64_t c = 1;
       while (c * c < n) ++c;  // ceil(sqrt(n)); n < 2^40 here
       uint64_t k = (c & 1) ? c : c - 1;
-      if (k > static_cast<uint64_t>(TILE - 1)) k = TILE - 1;
+      if (k > static_cast<uint64_t>(SAMPLE_MAX)) k = SAMPLE_MAX;
       if (k < 1) k = 1;
       const uint64_t step = n / k;
-      k_pivot_sample<K, HV, CNT><<<1, NT, tile_smem_bytes<K, true>(), st_>>>(
+      k_pivot_sample<K, HV, CNT><<<1, SAMPLE_T, tile_smem_bytes<K, true, SAMPLE_T, V>(), st_>>>(
           keys_, vals_, b, e, static_cast<int>(k), step, xf_, ws_.desc);
       launched();
     } else if (rule == QMS_PIVOT_MOM) {
@@ -624,7 +624,7 @@ class GraphRunner {
     ck(cudaGetDevice(&dev));
     ck(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     using LC = LeafCfg<K, HV>;
-    const size_t tsm = tile_smem_bytes<K, HV>(), tsm_s = tile_smem_bytes<K, true>();
+    const size_t tsm = tile_smem_bytes<K, HV>(), tsm_s = tile_smem_bytes<K, true, SAMPLE_T, V>();
     const size_t tsm_l = tile_smem_bytes<K, HV, LC::LT, LC::VL>();
     allow_smem(k_g_leaf<K, HV, CNT>, tsm_l);
     allow_smem(k_g_final<K, HV, CNT>, tsm_l);
@@ -688,7 +688,7 @@ class GraphRunner {
     cudaGraphNode_t n = add_kernel(body, nullptr, reinterpret_cast<const void*>(k_g_begin<K, HV, CNT>),
                                    1, 32, 0, a_round);
     if (pivot == QMS_PIVOT_SQRTN) {
-      n = add_kernel(body, n, reinterpret_cast<const void*>(k_g_pivot_sample<K, HV, CNT>), 1, NT,
+      n = add_kernel(body, n, reinterpret_cast<const void*>(k_g_pivot_sample<K, HV, CNT>), 1, SAMPLE_T,
                      tsm_s, a_s);
     }
     if (pivot == QMS_PIVOT_MOM || pivot == QMS_PIVOT_HYBRID) {

@@ -78,6 +78,7 @@ struct qms_server {
   int max_slots = 0;
   int max_batch = 0;
   int device = 0;
+  cudaMemPool_t pool = nullptr;  // the slots' memory pool (keeps up to the budget)
   std::mutex mu;
   std::condition_variable cv_work, cv_ready, cv_done;
   std::deque<qms::Req*> pending;  // submitted, not admitted yet
@@ -203,7 +204,8 @@ void stager_loop(qms_server* S) {
     int rc = QMS_OK;
     if (!r->in_place) {
       const size_t kb = r->n * key_bytes(r->dtype);
-      if (cudaMallocAsync(&r->slot, kb, st) != cudaSuccess) {
+      if ((S->pool ? cudaMallocFromPoolAsync(&r->slot, kb, S->pool, st)
+                   : cudaMallocAsync(&r->slot, kb, st)) != cudaSuccess) {
         (void)cudaGetLastError();
         r->slot = nullptr;
         rc = QMS_ENOMEM;
@@ -351,6 +353,23 @@ int qms_server_create(size_t hbm_budget_bytes, int max_slots, int workers, int m
     delete S;
     return QMS_ECUDA;
   }
+  // The slots come from a pool of the server's own that keeps up to the
+  // budget mapped: slots freed by the workers are reused by the stager
+  // without mapping device memory again.  (Without a pool: the device's
+  // default one.)
+  {
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = S->device;
+    if (cudaMemPoolCreate(&S->pool, &props) == cudaSuccess) {
+      uint64_t keep = hbm_budget_bytes;
+      cudaMemPoolSetAttribute(S->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    } else {
+      (void)cudaGetLastError();
+      S->pool = nullptr;
+    }
+  }
   S->stager = std::thread(stager_loop, S);
   for (int i = 0; i < workers; ++i) S->workers.emplace_back(worker_loop, S);
   *out = S;
@@ -475,6 +494,10 @@ int qms_server_destroy(qms_server* S) {
   S->stager.join();
   for (auto& t : S->workers) t.join();
   for (auto& kv : S->reqs) delete kv.second;
+  if (S->pool) {
+    cudaDeviceSynchronize();  // every slot has been freed on its worker's stream
+    cudaMemPoolDestroy(S->pool);
+  }
   delete S;
   return QMS_OK;
 }

@@ -11,8 +11,9 @@ checked through properties that hold at any size, each against the input:
 * for key-value pairs: the payloads (original indices) form a permutation
   and every output key equals the input key at its payload.
 
-The plain sort runs through the same entry point and launch configuration
-that bench.py times (the device-driven graph)."""
+The plain sort runs through the same entry point that bench.py times (a
+waiting qms_sort call, host-driven rounds at these sizes); one case runs the
+device-driven graph at full size as well."""
 import numpy as np
 import pytest
 
@@ -70,6 +71,7 @@ def _check_keys(inp, out, dtype, samples=24, seed=0):
     ("u32", "uniform", "m3", 2),      # the benchmark workload itself
     ("i64", "uniform", "hybrid", 3),
     ("f32", "normal", "sqrtn", 4),
+    ("u32", "uniform", "mom", 5),     # the worst-case-guaranteed variant (Sec. 4)
 ])
 def test_full_size_2_28(q, dtype, dist, pivot, seed):
     n = 1 << 28
@@ -93,7 +95,7 @@ def test_full_size_2_28_device_driven(q):
     _check_keys(k, out, "u32", seed=2)
 
 
-@pytest.mark.parametrize("dist", ["uniform", "mod16", "killer"])
+@pytest.mark.parametrize("dist", ["uniform", "mod16", "sorted", "reverse", "organ", "killer"])
 def test_full_size_pairs_2_27(q, dist):
     # 2^27 uint64 keys with uint32 payload = original index, hybrid pivot.
     n = 1 << 27
