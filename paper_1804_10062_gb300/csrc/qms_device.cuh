@@ -27,6 +27,21 @@ constexpr int NWARP = NT / 32;
 enum : int { XF_NONE = 0, XF_F32 = 1, XF_I64 = 2 };
 
 // ---------------------------------------------------------------------------
+// Programmatic dependent launch.  A kernel launched with a programmatic
+// dependency on the one before it in its stream (or graph) may start while
+// that one still runs.  grid_dep_wait() returns once the earlier grid has
+// finished and its writes are visible (at once when there is no such
+// dependency); grid_dep_trigger() lets the next kernel start once every
+// block of this one has called it.  Kernels call wait before trigger, so a
+// kernel that starts early never overlaps the one two steps back.
+__device__ __forceinline__ void grid_dep_wait() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+__device__ __forceinline__ void grid_dep_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// ---------------------------------------------------------------------------
 // Order keys
 
 __device__ __forceinline__ uint32_t enc_key(uint32_t b, int xf) {

@@ -566,6 +566,7 @@ __global__ void __launch_bounds__(LeafCfg<K, HV>::LT, LeafCfg<K, HV>::MINB) k_g_
 
 template <class K, bool HV, bool CNT>
 __global__ void __launch_bounds__(256) k_g_split(DState* S) {
+  grid_dep_wait();
   grid_dep_trigger();  // the merge node may start and load its buffer tiles
   count_launch(S);
   const DState& s = *S;

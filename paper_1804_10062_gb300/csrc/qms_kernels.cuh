@@ -67,6 +67,8 @@ template <class K, bool HV, bool CNT>
 __global__ void __launch_bounds__(LeafCfg<K, HV>::LT, LeafCfg<K, HV>::MINB) k_leaf_sort(K* keys, uint32_t* vals, uint64_t P,
                                                                   uint64_t m, uint64_t Bb, int to_buf,
                                                                   int xf, Desc* desc) {
+  grid_dep_wait();
+  grid_dep_trigger();
   constexpr int LT = LeafCfg<K, HV>::LT, TL = LeafCfg<K, HV>::TILE_L, VL = LeafCfg<K, HV>::VL;
   extern __shared__ __align__(16) unsigned char smem[];
   const auto s = TileSmem<K, HV, LT, VL>::carve(smem);
@@ -92,6 +94,8 @@ __global__ void __launch_bounds__(LeafCfg<K, HV>::LT, LeafCfg<K, HV>::MINB) k_le
 // Median-of-3 at b, b + floor(n/2), e - 1 (proof of Thm. 1).
 template <class K, bool HV, bool CNT>
 __global__ void k_pivot_m3(K* keys, uint32_t* vals, uint64_t b, uint64_t e, int xf, Desc* desc) {
+  grid_dep_wait();
+  grid_dep_trigger();
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   const uint64_t n = e - b;
   uint64_t p0 = b, p1 = b + n / 2, p2 = e - 1;
@@ -112,6 +116,7 @@ __global__ void k_pivot_m3(K* keys, uint32_t* vals, uint64_t b, uint64_t e, int 
   }
   desc->pivot = static_cast<unsigned long long>(u1);
   desc->tie = tie ? 1u : 0u;
+  desc->L = 0;  // the round's partition counts from zero
   if (CNT) desc->cmp += c + 2;
 }
 
@@ -127,6 +132,8 @@ constexpr int SAMPLE_MAX = SAMPLE_T * V - 1;
 template <class K, bool HV, bool CNT>
 __global__ void __launch_bounds__(SAMPLE_T) k_pivot_sample(K* keys, uint32_t* vals, uint64_t b, uint64_t e,
                                                            int ks, uint64_t step, int xf, Desc* desc) {
+  grid_dep_wait();
+  grid_dep_trigger();
   extern __shared__ __align__(16) unsigned char smem[];
   const auto s = TileSmem<K, true, SAMPLE_T, V>::carve(smem);
   uint64_t cmp = 0;
@@ -148,6 +155,7 @@ __global__ void __launch_bounds__(SAMPLE_T) k_pivot_sample(K* keys, uint32_t* va
     }
     desc->pivot = static_cast<unsigned long long>(med);
     desc->tie = tie ? 1u : 0u;
+    desc->L = 0;
     if (CNT) desc->cmp += 2;
   }
 }
@@ -237,6 +245,7 @@ __global__ void k_mom_place(K* keys, uint32_t* vals, uint64_t b, uint64_t e, uin
   }
   desc->pivot = desc->sel_prefix;
   desc->tie = desc->sel_eq > 1 ? 1u : 0u;
+  desc->L = 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -248,6 +257,8 @@ __global__ void k_mom_place(K* keys, uint32_t* vals, uint64_t b, uint64_t e, uin
 template <class K, bool HV, bool CNT>
 __global__ void __launch_bounds__(PNT) k_part_local(K* keys, uint32_t* vals, uint64_t lo, uint64_t hi,
                                                     int le, int xf, Desc* desc, uint32_t* counts) {
+  grid_dep_wait();
+  grid_dep_trigger();
   __shared__ K sk[pk_len<K>()];
   __shared__ uint32_t sv[HV ? pv_len() : 1];
   __shared__ uint32_t scr[PNWARP + 1];
@@ -399,6 +410,8 @@ __device__ __forceinline__ void scan_prefix_body(uint64_t lo, uint64_t hi, const
 
 static __global__ void __launch_bounds__(NT) k_part_chunks(uint64_t lo, uint64_t hi,
                                                            const uint32_t* counts, Desc* desc) {
+  grid_dep_wait();
+  grid_dep_trigger();
   scan_chunks_body(lo, hi, counts, desc);
 }
 
@@ -406,6 +419,8 @@ static __global__ void __launch_bounds__(NT) k_part_prefix(uint64_t lo, uint64_t
                                                            const uint32_t* counts, uint64_t* pml,
                                                            uint64_t* pmr, uint32_t* wtl,
                                                            uint32_t* wtr, Desc* desc) {
+  grid_dep_wait();
+  grid_dep_trigger();
   scan_prefix_body(lo, hi, counts, pml, pmr, wtl, wtr, desc);
 }
 
@@ -419,6 +434,8 @@ __global__ void __launch_bounds__(EXB, (sizeof(K) == 4 && !HV) ? 5 : 1) k_part_e
                                                        const uint32_t* counts, const uint64_t* pml,
                                                        const uint64_t* pmr, const uint32_t* wtl,
                                                        const uint32_t* wtr, const Desc* desc) {
+  grid_dep_wait();
+  grid_dep_trigger();
   const uint64_t mis = desc->mis;
   const uint64_t s = lo + desc->L;
   const uint64_t w0 = (blockIdx.x * static_cast<uint64_t>(EXB) + threadIdx.x) >> 5;
@@ -431,6 +448,8 @@ __global__ void __launch_bounds__(EXB, (sizeof(K) == 4 && !HV) ? 5 : 1) k_part_e
 // lo + L.
 template <class K, bool HV>
 __global__ void k_place_pivot(K* keys, uint32_t* vals, uint64_t lo, uint64_t parked, Desc* desc) {
+  grid_dep_wait();
+  grid_dep_trigger();
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   const uint64_t k = lo + desc->L;
   if (k != parked) {

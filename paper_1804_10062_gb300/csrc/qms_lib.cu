@@ -192,11 +192,14 @@ class Profiler {
 
 // Stores a partition pass's result (left count, misplaced pairs, tie and
 // error bits) into mapped host memory for the host-driven driver.
-__global__ void k_report(const Desc* d, unsigned long long* out) {
+__global__ void k_report(Desc* d, unsigned long long* out) {
+  grid_dep_wait();
+  grid_dep_trigger();
   if (threadIdx.x != 0) return;
   out[0] = d->L;
   out[1] = d->mis;
   out[2] = static_cast<unsigned long long>(d->tie) | (static_cast<unsigned long long>(d->err) << 32);
+  d->L = 0;  // a further pass of the round counts from zero
   __threadfence_system();
 }
 
@@ -255,8 +258,8 @@ class Sorter {
     using LC = LeafCfg<K, HV>;
     const uint64_t nt = (m + LC::TILE_L - 1) / LC::TILE_L;
     prof_.begin(st_);
-    k_leaf_sort<K, HV, CNT><<<grid_of(nt), LC::LT, tile_smem_bytes<K, HV, LC::LT, LC::VL>(), st_>>>(
-        keys_, vals_, P, m, Bb, to_buf ? 1 : 0, xf_, ws_.desc);
+    launch(k_leaf_sort<K, HV, CNT>, grid_of(nt), LC::LT, tile_smem_bytes<K, HV, LC::LT, LC::VL>(), keys_,
+           vals_, P, m, Bb, to_buf ? 1 : 0, xf_, ws_.desc);
     prof_.end(st_, QMS_K_LEAF, (to_buf ? 4 : 2) * m * ES);
     launched();
   }
@@ -284,8 +287,8 @@ class Sorter {
     for (int l = 0; l < levels; ++l) {
       const uint64_t L = TL << l;
       prof_.begin(st_);
-      k_merge_split3<K, HV, CNT><<<grid_of((mtiles + 255) / 256), 256, 0, st_>>>(
-          keys_, X, m, L, xf_, ws_.splits, ws_.desc);
+      launch(k_merge_split3<K, HV, CNT>, grid_of((mtiles + 255) / 256), 256, 0,
+             static_cast<const K*>(keys_), X, m, L, xf_, ws_.splits, ws_.desc);
       prof_.end(st_, QMS_K_MERGE_SPLIT, 0);
       prof_.begin(st_);
       launch_merge(X, Y, m, L, mtiles);
@@ -334,8 +337,8 @@ class Sorter {
       if (k > static_cast<uint64_t>(SAMPLE_MAX)) k = SAMPLE_MAX;
       if (k < 1) k = 1;
       const uint64_t step = n / k;
-      k_pivot_sample<K, HV, CNT><<<1, SAMPLE_T, tile_smem_bytes<K, true, SAMPLE_T, V>(), st_>>>(
-          keys_, vals_, b, e, static_cast<int>(k), step, xf_, ws_.desc);
+      launch(k_pivot_sample<K, HV, CNT>, 1, SAMPLE_T, tile_smem_bytes<K, true, SAMPLE_T, V>(), keys_, vals_,
+             b, e, static_cast<int>(k), step, xf_, ws_.desc);
       launched();
     } else if (rule == QMS_PIVOT_MOM) {
       const uint64_t t = n / 3;
@@ -358,7 +361,7 @@ class Sorter {
       launched(2);
       ++mom_rounds;
     } else {
-      k_pivot_m3<K, HV, CNT><<<1, 32, 0, st_>>>(keys_, vals_, b, e, xf_, ws_.desc);
+      launch(k_pivot_m3<K, HV, CNT>, 1, 32, 0, keys_, vals_, b, e, xf_, ws_.desc);
       launched();
     }
     prof_.end(st_, QMS_K_PIVOT, 0);
@@ -371,37 +374,44 @@ class Sorter {
     const uint64_t n = hi - lo;
     const uint64_t nt = (n + PT - 1) / PT;
     if (n > 0) {
-      ck(cudaMemsetAsync(&ws_.desc->L, 0, sizeof(unsigned long long), st_));
+      // L starts at zero: reset by the pivot kernel before a round's first
+      // pass and by k_report after it (else here)
+      if (!report_) ck(cudaMemsetAsync(&ws_.desc->L, 0, sizeof(unsigned long long), st_));
       prof_.begin(st_);
-      k_part_local<K, HV, CNT><<<grid_of(nt), PNT, 0, st_>>>(keys_, vals_, lo, hi, le ? 1 : 0, xf_,
-                                                             ws_.desc, ws_.counts);
+      launch(k_part_local<K, HV, CNT>, grid_of(nt), PNT, 0, keys_, vals_, lo, hi, le ? 1 : 0, xf_,
+             ws_.desc, ws_.counts);
       prof_.end(st_, QMS_K_PART_LOCAL, 2 * n * ES);
       const uint64_t ch = scan_chunk(nt);
       const unsigned nch = static_cast<unsigned>((nt + ch - 1) / ch);
       prof_.begin(st_);
-      k_part_chunks<<<nch, NT, 0, st_>>>(lo, hi, ws_.counts, ws_.desc);
-      k_part_prefix<<<nch, NT, 0, st_>>>(lo, hi, ws_.counts, ws_.pml, ws_.pmr, ws_.wtl, ws_.wtr,
-                                         ws_.desc);
+      launch(k_part_chunks, nch, NT, 0, lo, hi, static_cast<const uint32_t*>(ws_.counts), ws_.desc);
+      launch(k_part_prefix, nch, NT, 0, lo, hi, static_cast<const uint32_t*>(ws_.counts), ws_.pml,
+             ws_.pmr, ws_.wtl, ws_.wtr, ws_.desc);
       prof_.end(st_, QMS_K_PART_SCAN, nt * 20);
       launched();
       const uint64_t maxmis = n / 2 + 1;
       const uint64_t per = static_cast<uint64_t>(EXB) * EXW;
       prof_.begin(st_);
+      const unsigned gx = grid_of((maxmis + per - 1) / per);
+      const uint32_t* cnts = ws_.counts;
+      const uint64_t* pl = ws_.pml;
+      const uint64_t* pr = ws_.pmr;
+      const uint32_t* tl = ws_.wtl;
+      const uint32_t* tr = ws_.wtr;
+      const Desc* dc = ws_.desc;
       if (n < (1ull << 32)) {
-        k_part_exchange<K, HV, uint32_t><<<grid_of((maxmis + per - 1) / per), EXB, 0, st_>>>(
-            keys_, vals_, lo, ws_.counts, ws_.pml, ws_.pmr, ws_.wtl, ws_.wtr, ws_.desc);
+        launch(k_part_exchange<K, HV, uint32_t>, gx, EXB, 0, keys_, vals_, lo, cnts, pl, pr, tl, tr, dc);
       } else {
-        k_part_exchange<K, HV, uint64_t><<<grid_of((maxmis + per - 1) / per), EXB, 0, st_>>>(
-            keys_, vals_, lo, ws_.counts, ws_.pml, ws_.pmr, ws_.wtl, ws_.wtr, ws_.desc);
+        launch(k_part_exchange<K, HV, uint64_t>, gx, EXB, 0, keys_, vals_, lo, cnts, pl, pr, tl, tr, dc);
       }
       prof_.end(st_, QMS_K_PART_EXCHANGE, 0);  // bytes added once mis is known
       launched(3);
-    } else {
+    } else if (!report_) {
       ck(cudaMemsetAsync(&ws_.desc->L, 0, sizeof(unsigned long long), st_));
     }
     if (parked != ~0ull) {
       prof_.begin(st_);
-      k_place_pivot<K, HV><<<1, 32, 0, st_>>>(keys_, vals_, lo, parked, ws_.desc);
+      launch(k_place_pivot<K, HV>, 1, 32, 0, keys_, vals_, lo, parked, ws_.desc);
       prof_.end(st_, QMS_K_PIVOT, 0);
       launched();
     }
@@ -413,7 +423,7 @@ class Sorter {
       // A kernel stores the round's result into mapped host memory: no copy
       // engine is involved, so the read-back does not queue behind large
       // copies that other streams may have in flight.
-      k_report<<<1, 32, 0, st_>>>(ws_.desc, report_);
+      launch(k_report, 1, 32, 0, ws_.desc, report_);
       ck(cudaStreamSynchronize(st_));
       const volatile unsigned long long* r = report_;
       h.L = r[0];
@@ -478,22 +488,32 @@ class Sorter {
 
   void launched(int c = 1) { launches += c; }
 
-  // One swap-merge level; unless its time is being profiled, with a
-  // programmatic dependency on the split step before it (the merge blocks
-  // start early and load their buffer tiles while the split runs).
-  void launch_merge(uint64_t X, uint64_t Y, uint64_t m, uint64_t L, uint64_t mtiles) {
+  // Launches a kernel of the round loop.  Unless its time is being
+  // profiled, with a programmatic dependency on the kernel before it: the
+  // kernel's blocks may start during the previous kernel's last wave and
+  // wait (grid_dep_wait) for its results, which hides the launch gap; the
+  // merge kernel loads its buffer tile before that wait.
+  template <class... KA, class... A>
+  void launch(void (*k)(KA...), unsigned grid, unsigned block, size_t smem, A... args) {
     cudaLaunchConfig_t cfg{};
-    cfg.gridDim = dim3(grid_of(mtiles));
-    cfg.blockDim = dim3(MBT);
-    cfg.dynamicSmemBytes = 0;
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
     cfg.stream = st_;
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     at[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = at;
-    cfg.numAttrs = (prof_.active() || std::getenv("QMS_NO_PDL")) ? 0 : 1;
-    ck(cudaLaunchKernelEx(&cfg, k_merge_level3<K, HV, CNT>, keys_, vals_, X, Y, m, L,
-                          static_cast<const uint64_t*>(ws_.splits), xf_, ws_.desc));
+    cfg.numAttrs = (prof_.active() || no_pdl()) ? 0 : 1;
+    ck(cudaLaunchKernelEx(&cfg, k, static_cast<KA>(args)...));
+  }
+  static bool no_pdl() {
+    static const bool v = std::getenv("QMS_NO_PDL") != nullptr;
+    return v;
+  }
+  void launch_merge(uint64_t X, uint64_t Y, uint64_t m, uint64_t L, uint64_t mtiles) {
+    launch(k_merge_level3<K, HV, CNT>, grid_of(mtiles), MBT, 0, keys_, vals_, X, Y, m, L,
+           static_cast<const uint64_t*>(ws_.splits), xf_, ws_.desc);
   }
 
  private:

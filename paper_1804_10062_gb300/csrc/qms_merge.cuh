@@ -103,18 +103,6 @@ __device__ __forceinline__ void merge_staged_out(const K* sin, K* sout, const ui
   });
 }
 
-// Programmatic dependent launch.  A kernel launched with a programmatic
-// dependency on the one before it may start while that one still runs;
-// grid_dep_wait() returns once the earlier grid has finished and its writes
-// are visible (at once when there is no such dependency).
-// grid_dep_trigger() lets the next kernel start early.
-__device__ __forceinline__ void grid_dep_wait() {
-  asm volatile("griddepcontrol.wait;" ::: "memory");
-}
-__device__ __forceinline__ void grid_dep_trigger() {
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-}
-
 // One output tile per block.  Element i of the tile (i = j*MBT + thread) is
 // loaded from the A/B slices and from the buffer tile by the same thread,
 // which then stores its buffer value into that X slot: the tile's consumed
@@ -160,7 +148,10 @@ __device__ __forceinline__ void merge_level_tile(K* keys, uint32_t* vals, uint64
       if (HV) yv[j] = gyv[i];
     }
   }
-  if (wait) grid_dep_wait();
+  if (wait) {
+    grid_dep_wait();
+    grid_dep_trigger();
+  }
   const uint64_t a_lo = splits[t];
   const uint64_t a_hi = (gm.d1 == gm.la + gm.lb) ? gm.la : splits[t + 1];
   const int na = static_cast<int>(a_hi - a_lo);
@@ -296,6 +287,7 @@ template <class K, bool HV, bool CNT>
 __global__ void __launch_bounds__(256) k_merge_split3(const K* keys, uint64_t X, uint64_t m,
                                                       uint64_t L, int xf, uint64_t* splits,
                                                       Desc* desc) {
+  grid_dep_wait();     // the runs of the level are complete
   grid_dep_trigger();  // the merge may start and load its buffer tiles
   uint64_t cmp = 0;
   split_group<K, HV, CNT>(keys, X, m, L, xf, splits,
