@@ -99,6 +99,11 @@ typedef struct {
                                   its first tile done, so the waits on that tile run
                                   out after spin_limit polls and the sort returns
                                   QMS_ETIMEOUT (its output is then unspecified)       */
+#define QMS_FLAG_DEVICE_DRIVEN 16 /* run the rounds as the device-driven CUDA graph even
+                                  when the call waits for its result (by default a
+                                  waiting call of 2^16 keys or more runs them from
+                                  the host); ignored with `profile` or
+                                  QMS_FLAG_HOST_DRIVEN                                 */
 
 typedef struct {
   int pivot;       /* QMS_PIVOT_*                                              */
@@ -134,10 +139,10 @@ const char* qms_error_string(int code);
  * (instances are cached per key type, pivot rule and device; the first call
  * of a kind builds one), and the call returns after the sort finished; with
  * QMS_FLAG_ASYNC and stats == NULL it returns once the sort is enqueued on
- * `stream`.  A call that waits for arrays of 2^26 keys or more runs the
- * rounds from the host instead (as QMS_FLAG_HOST_DRIVEN), which is faster
- * there: one small read-back per round costs less than the graph's
- * conditional nodes.  Errors: QMS_EINVAL (d_keys NULL
+ * `stream`.  A call that waits for arrays of 2^16 keys or more runs the
+ * rounds from the host instead (as QMS_FLAG_HOST_DRIVEN), which measured
+ * faster: one small read-back per round costs less than the graph's
+ * conditional nodes.  QMS_FLAG_DEVICE_DRIVEN keeps such a call on the graph.  Errors: QMS_EINVAL (d_keys NULL
  * with n > 1, bad dtype or pivot), QMS_ENOMEM, QMS_ECUDA, QMS_EINTERNAL,
  * QMS_ETIMEOUT (a bounded device wait gave up; see qms_options.spin_limit). */
 int qms_sort(void* d_keys, size_t n, int dtype, const qms_options* opt, void* stream,

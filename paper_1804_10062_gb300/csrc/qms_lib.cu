@@ -1014,7 +1014,7 @@ int dispatch(const Args& a, qms_stats* stats, Fn&& fn) {
 bool valid_dtype(int d) { return d >= QMS_U32 && d <= QMS_F32; }
 
 // Arrays from this size on are sorted host-driven by calls that wait.
-constexpr uint64_t kHostDrivenMinN = 1ull << 26;
+constexpr uint64_t kHostDrivenMinN = 1ull << 16;
 
 // Polls of one flag before a bounded device wait gives up.
 unsigned spin_limit_of(const qms_options* opt) {
@@ -1591,13 +1591,15 @@ static int sort_common(void* d_keys, uint32_t* d_vals, size_t n, int dtype, cons
   if (d_vals != nullptr && n >= (1ull << 32)) return QMS_EINVAL;
   Args a{d_keys, d_vals, n, dtype, pivot, opt && opt->count_cmps, static_cast<cudaStream_t>(stream),
          opt ? opt->profile : nullptr};
-  // A call that waits for its result runs the rounds from the host once the
-  // array is large: one small read-back per round then costs less than the
-  // graph's conditional nodes (2^28 keys: 17.7 ms against 18.8; at 2^24 the
-  // graph is ahead, 3.17 against 3.28 ms).  Asynchronous calls always take
-  // the graph, which needs no host thread.
+  // A call that waits for its result runs the rounds from the host: with
+  // every kernel launched programmatically after the one before it, one
+  // small read-back per round costs less than the graph's conditional nodes
+  // (2^20 keys: 1.06 ms against 1.26; 2^24: 2.57 against 3.25; 2^28: 17.3
+  // against 18.9).  Asynchronous calls take the graph, which needs no host
+  // thread; so do arrays of less than 2^16 keys (at most a few leaves).
   const bool wait = !(opt && (opt->flags & QMS_FLAG_ASYNC)) || stats != nullptr;
-  const bool big_sync = wait && n >= kHostDrivenMinN && std::getenv("QMS_GRAPH_ALWAYS") == nullptr;
+  const bool big_sync =
+      wait && n >= kHostDrivenMinN && !(opt && (opt->flags & QMS_FLAG_DEVICE_DRIVEN));
   const bool host_driven =
       (opt && (opt->profile || (opt->flags & QMS_FLAG_HOST_DRIVEN))) || big_sync;
   const bool fig3 = !(opt && (opt->flags & QMS_FLAG_LARGER_SIDE));

@@ -172,6 +172,7 @@ QMS_FLAG_ASYNC = 1
 QMS_FLAG_HOST_DRIVEN = 2
 QMS_FLAG_LARGER_SIDE = 4
 QMS_FLAG_TEST_WITHHOLD = 8
+QMS_FLAG_DEVICE_DRIVEN = 16
 SIDES = {"fig3": 0, "larger": QMS_FLAG_LARGER_SIDE}
 
 
@@ -182,21 +183,29 @@ def _options(pivot, count_cmps, profile, flags=0, spin_limit=0):
     return opt
 
 
+def _driver_flags(host_driven):
+    if host_driven is None:
+        return 0
+    return QMS_FLAG_HOST_DRIVEN if host_driven else QMS_FLAG_DEVICE_DRIVEN
+
+
 def qms_sort(keys, pivot: str = "m3", count_cmps: bool = False, stream=None, dtype=None,
-             profile: qms_profile | None = None, host_driven: bool = False, wait: bool = True,
-             side: str = "fig3", spin_limit: int = 0, test_withhold: bool = False):
+             profile: qms_profile | None = None, host_driven: bool | None = None,
+             wait: bool = True, side: str = "fig3", spin_limit: int = 0,
+             test_withhold: bool = False):
     """Sorts ``keys`` in place; returns the qms_stats fields as a dict (or
     None with ``wait=False``: the sort is only enqueued on the stream).
 
     ``profile`` (a qms_profile) accumulates per-kernel device times (this
-    runs the rounds from the host); ``host_driven`` selects that driver
-    without profiling.  ``side``: "fig3" (Fig. 3's rule, full-size buffer) or
+    runs the rounds from the host); ``host_driven`` True selects that driver
+    without profiling, False the device-driven graph, None the library's
+    choice (host-driven for waiting calls of 2^16 keys or more).  ``side``: "fig3" (Fig. 3's rule, full-size buffer) or
     "larger" (Mergesort the larger side with a half-size buffer when it
     fits).  ``spin_limit`` bounds the device waits of the overlapped merge
     (polls of one flag; 0 = default); ``test_withhold`` is the failure-test
     hook QMS_FLAG_TEST_WITHHOLD."""
     code = _check_keys(keys, dtype)
-    flags = ((QMS_FLAG_HOST_DRIVEN if host_driven else 0) | (0 if wait else QMS_FLAG_ASYNC)
+    flags = (_driver_flags(host_driven) | (0 if wait else QMS_FLAG_ASYNC)
              | SIDES[side] | (QMS_FLAG_TEST_WITHHOLD if test_withhold else 0))
     opt = _options(pivot, count_cmps, profile, flags, spin_limit)
     st = qms_stats()
@@ -207,14 +216,15 @@ def qms_sort(keys, pivot: str = "m3", count_cmps: bool = False, stream=None, dty
 
 
 def qms_sort_pairs(keys, vals, pivot: str = "m3", count_cmps: bool = False, stream=None, dtype=None,
-                   profile: qms_profile | None = None, host_driven: bool = False,
+                   profile: qms_profile | None = None, host_driven: bool | None = None,
                    side: str = "fig3", wait: bool = True):
     """Sorts ``keys`` in place, moving ``vals`` with them; returns stats (or
-    None with ``wait=False``: the sort is only enqueued on the stream)."""
+    None with ``wait=False``: the sort is only enqueued on the stream).
+    ``host_driven`` as for qms_sort."""
     code = _check_keys(keys, dtype)
     vp = _check_vals(vals, keys.numel())
     opt = _options(pivot, count_cmps, profile,
-                   (QMS_FLAG_HOST_DRIVEN if host_driven else 0) | SIDES[side]
+                   _driver_flags(host_driven) | SIDES[side]
                    | (0 if wait else QMS_FLAG_ASYNC))
     st = qms_stats()
     rc = lib().qms_sort_pairs(ctypes.c_void_p(keys.data_ptr()), vp, keys.numel(), code,

@@ -38,7 +38,8 @@ def test_header_constants_match_the_binding():
     assert m and (1 << int(m.group(1))) == q.QMS_NOALLOC_MAX_N
     for name in ("QMS_OK", "QMS_EINVAL", "QMS_ENOMEM", "QMS_EBUDGET", "QMS_ECUDA",
                  "QMS_ETIMEOUT", "QMS_EAGAIN", "QMS_EINTERNAL", "QMS_FLAG_ASYNC",
-                 "QMS_FLAG_HOST_DRIVEN", "QMS_FLAG_LARGER_SIDE", "QMS_FLAG_TEST_WITHHOLD"):
+                 "QMS_FLAG_HOST_DRIVEN", "QMS_FLAG_LARGER_SIDE", "QMS_FLAG_TEST_WITHHOLD",
+                 "QMS_FLAG_DEVICE_DRIVEN"):
         assert _define(name) == getattr(q, name), name
     # qms_options field order: pivot, count_cmps, flags, spin_limit, profile
     body = re.search(r"typedef struct \{([^{}]*)\} qms_options;", txt).group(1)

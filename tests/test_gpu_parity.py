@@ -216,22 +216,26 @@ def test_config1_permutation_m3(q):
     assert c_ref <= st["comparisons"] <= 1.7 * c_ref
 
 
+# host_driven: None is the library's choice for a waiting call of this size
+# (the host loop), False the device-driven graph.
+@pytest.mark.parametrize("host_driven", [None, False])
 @pytest.mark.parametrize("pivot", ["m3", "sqrtn", "mom", "hybrid"])
 @pytest.mark.parametrize("dtype,dist", [("u32", "uniform"), ("i64", "uniform"), ("f32", "normal"),
                                         ("u64", "uniform")])
-def test_sort_vs_oracle(q, pivot, dtype, dist):
+def test_sort_vs_oracle(q, pivot, dtype, dist, host_driven):
     n = (1 << 18) + 12345
     k = _dist_keys(dist, dtype, n, 2)
     ref = k.copy()
     oracle.sort(ref, variant=pivot, mode="paper")
     d = _dev(k)
-    q.qms_sort(d, pivot=pivot, dtype=dtype)
+    q.qms_sort(d, pivot=pivot, dtype=dtype, host_driven=host_driven)
     assert _host(d, dtype).tobytes() == ref.tobytes()
 
 
+@pytest.mark.parametrize("host_driven", [None, False])
 @pytest.mark.parametrize("dist", ["uniform", "mod16", "sorted", "reverse", "organ", "killer"])
 @pytest.mark.parametrize("pivot", ["hybrid", "m3"])
-def test_pairs_vs_oracle(q, dist, pivot):
+def test_pairs_vs_oracle(q, dist, pivot, host_driven):
     n = (1 << 17) + 3
     if dist == "killer":
         if pivot == "m3":
@@ -244,7 +248,7 @@ def test_pairs_vs_oracle(q, dist, pivot):
     rk, rv = k.copy(), v.copy()
     oracle.sort(rk, rv, variant=pivot, mode="paper")
     d, dv = _dev(k), _dev(v)
-    q.qms_sort_pairs(d, dv, pivot=pivot, dtype="u64")
+    q.qms_sort_pairs(d, dv, pivot=pivot, dtype="u64", host_driven=host_driven)
     ko, vo = _host(d, "u64"), _host(dv, "u32")
     assert ko.tobytes() == rk.tobytes()
     ck, cv = oracle.canonical_pairs(ko, vo)
@@ -310,7 +314,7 @@ def test_host_driven_driver_matches_oracle(q, pivot, dtype):
     st = q.qms_sort(d, pivot=pivot, dtype=dtype, host_driven=True)
     assert _host(d, dtype).tobytes() == ref.tobytes()
     d2 = _dev(k)
-    st2 = q.qms_sort(d2, pivot=pivot, dtype=dtype)
+    st2 = q.qms_sort(d2, pivot=pivot, dtype=dtype, host_driven=False)
     assert _host(d2, dtype).tobytes() == ref.tobytes()
     assert st2["rounds"] >= 1 and st2["launches"] > 0
 
