@@ -760,19 +760,23 @@ def run_qms(args):
         hout = torch.empty(n, dtype=tdt, pin_memory=True)
         dbuf = [torch.empty(n, dtype=tdt, device="cuda") for _ in range(2)]
         s_up, s_sort, s_down = (torch.cuda.Stream() for _ in range(3))
-        # the link alone: one upload and one download of a whole array
+        # the link alone: uploads and downloads of a whole array (the best of
+        # three; the first copy on a fresh buffer can be several times slower)
         link = {}
         for name, dst, src, stream in (("h2d_GBps", dbuf[0], hbuf, s_up),
                                        ("d2h_GBps", hout, dbuf[0], s_down)):
-            torch.cuda.synchronize()
-            c0 = torch.cuda.Event(enable_timing=True)
-            c1 = torch.cuda.Event(enable_timing=True)
-            with torch.cuda.stream(stream):
-                c0.record(stream)
-                dst.copy_(src, non_blocking=True)
-                c1.record(stream)
-            torch.cuda.synchronize()
-            link[name] = n * esz / (c0.elapsed_time(c1) / 1e3) / 1e9
+            best = 0.0
+            for _ in range(3):
+                torch.cuda.synchronize()
+                c0 = torch.cuda.Event(enable_timing=True)
+                c1 = torch.cuda.Event(enable_timing=True)
+                with torch.cuda.stream(stream):
+                    c0.record(stream)
+                    dst.copy_(src, non_blocking=True)
+                    c1.record(stream)
+                torch.cuda.synchronize()
+                best = max(best, n * esz / (c0.elapsed_time(c1) / 1e3) / 1e9)
+            link[name] = best
         ksteps = max(8, min(args.steps, 16))
 
         def pipeline(steps):

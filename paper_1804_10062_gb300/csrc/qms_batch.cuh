@@ -47,41 +47,46 @@ __device__ __forceinline__ void group_sort_seg(K* g, uint32_t* gv, int cnt, K* s
     if (HV) sv[sv_i(i)] = (i < cnt) ? gv[i] : 0xffffffffu;
   }
   group_sync<GT>(grp);
-  K k[VV];
-  uint32_t v[VV];
-  if (lt < P) {
-#pragma unroll
-    for (int j = 0; j < VV; ++j) {
-      k[j] = sk[sk_i<K>(lt * VV + j)];
-      if (HV) v[j] = sv[sv_i(lt * VV + j)];
-    }
-    net_sort<K, HV, VV>(k, v);
-    if (CNT) cmp += kNet<VV>.len;
-#pragma unroll
-    for (int j = 0; j < VV; ++j) {
-      sk[sk_i<K>(lt * VV + j)] = k[j];
-      if (HV) sv[sv_i(lt * VV + j)] = v[j];
-    }
-  }
-  group_sync<GT>(grp);
-  for (int sp = 1; sp < P; sp <<= 1) {
-    const int L = sp * VV;
-    const int pr = lt / (2 * sp), r = lt - pr * 2 * sp;
-    const int a0 = pr * 2 * L, b0 = a0 + L;
-    const int d = r * VV;
-    if (lt < P) {
-      const int ia = merge_path_smem<K, CNT>(sk, a0, L, b0, L, d, cmp);
-      serial_merge_kv<K, HV, CNT, VV>(sk, sv, a0 + ia, a0 + L, b0 + d - ia, b0 + L, k, v, cmp);
-    }
-    group_sync<GT>(grp);  // every read of the round is done before any write
+  if constexpr (!HV) {
+    tile_sort_keys<K, CNT, VV>(sk, lt, P, [grp](int) { group_sync<GT>(grp); }, cmp);
+    group_sync<GT>(grp);  // the last round's writes are visible
+  } else {
+    K k[VV];
+    uint32_t v[VV];
     if (lt < P) {
 #pragma unroll
       for (int j = 0; j < VV; ++j) {
-        sk[sk_i<K>(a0 + d + j)] = k[j];
-        if (HV) sv[sv_i(a0 + d + j)] = v[j];
+        k[j] = sk[sk_i<K>(lt * VV + j)];
+        if (HV) v[j] = sv[sv_i(lt * VV + j)];
+      }
+      net_sort<K, HV, VV>(k, v);
+      if (CNT) cmp += kNet<VV>.len;
+#pragma unroll
+      for (int j = 0; j < VV; ++j) {
+        sk[sk_i<K>(lt * VV + j)] = k[j];
+        if (HV) sv[sv_i(lt * VV + j)] = v[j];
       }
     }
     group_sync<GT>(grp);
+    for (int sp = 1; sp < P; sp <<= 1) {
+      const int L = sp * VV;
+      const int pr = lt / (2 * sp), r = lt - pr * 2 * sp;
+      const int a0 = pr * 2 * L, b0 = a0 + L;
+      const int d = r * VV;
+      if (lt < P) {
+        const int ia = merge_path_smem<K, CNT>(sk, a0, L, b0, L, d, cmp);
+        serial_merge_kv<K, HV, CNT, VV>(sk, sv, a0 + ia, a0 + L, b0 + d - ia, b0 + L, k, v, cmp);
+      }
+      group_sync<GT>(grp);  // every read of the round is done before any write
+      if (lt < P) {
+#pragma unroll
+        for (int j = 0; j < VV; ++j) {
+          sk[sk_i<K>(a0 + d + j)] = k[j];
+          if (HV) sv[sv_i(a0 + d + j)] = v[j];
+        }
+      }
+      group_sync<GT>(grp);
+    }
   }
   for (int i = lt; i < cnt; i += GT) {
     g[i] = dec_key(sk[sk_i<K>(i)], xf);

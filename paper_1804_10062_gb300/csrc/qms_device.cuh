@@ -423,10 +423,94 @@ __device__ __forceinline__ void tile_sync(int threads) {
 // 63 comparators for V = 16), then log2(NT) rounds of merge-path merges in
 // shared memory.
 
+// Keys without payloads: the runs of every round alternate between
+// ascending and descending order, so each pair of runs to merge lies in
+// shared memory as one bitonic sequence (A ascending, then B descending).
+// From its merge-path split a thread repeatedly takes the smaller of the two
+// ends of its remaining range: that range stays bitonic, so its minimum is
+// at one end, and the two ends never pass each other before the thread's VV
+// outputs are out, so the loop needs no bound checks.  Equal keys are equal
+// bit patterns here, so which of two equal keys goes first does not matter.
+// Thread lt (< P) of the P threads holding data sorts sk[0, P * VV);
+// sync(t) is a barrier among the groups of t threads that share a run pair
+// (every thread of the caller's group calls it).
+template <class K, bool CNT, int VV, class Sync>
+__device__ __forceinline__ void tile_sort_keys(K* sk, int lt, int P, Sync&& sync, uint64_t& cmp) {
+  static_assert((128 / static_cast<int>(sizeof(K))) % VV == 0,
+                "a thread's VV keys must share one padded row");
+  K k[VV];
+  if (lt < P) {
+    const int base = sk_i<K>(lt * VV);
+#pragma unroll
+    for (int j = 0; j < VV; ++j) k[j] = sk[base + j];
+    uint32_t none[VV];
+    net_sort<K, false, VV>(k, none);
+    if (CNT) cmp += kNet<VV>.len;
+    // the odd thread of each first-round pair stores its keys descending
+    const bool desc = (lt & 1) && P > 1;
+    const int b2 = desc ? base + VV - 1 : base;
+    const int step = desc ? -1 : 1;
+#pragma unroll
+    for (int j = 0; j < VV; ++j) sk[b2 + j * step] = k[j];
+  }
+  sync(2);
+  for (int sp = 1; sp < P; sp <<= 1) {
+    const int L = sp * VV;
+    const int g = lt / (2 * sp), r = lt - g * 2 * sp;
+    const int a0 = g * 2 * L;
+    const int d = r * VV;
+    if (lt < P) {
+      // A = sk[a0, a0 + L) ascending; B[q] = sk[a0 + 2L - 1 - q].
+      int lo = d > L ? d - L : 0, hi = d < L ? d : L;
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (CNT) ++cmp;
+        if (!(sk[sk_i<K>(a0 + 2 * L - d + mid)] < sk[sk_i<K>(a0 + mid)])) lo = mid + 1; else hi = mid;
+      }
+      int i = a0 + lo;                    // next A key
+      int j = a0 + 2 * L - 1 - (d - lo);  // next B key
+      K ka = sk[sk_i<K>(i)];
+      K kb = sk[sk_i<K>(j)];
+#pragma unroll
+      for (int t = 0; t < VV; ++t) {
+        if (CNT) ++cmp;
+        const bool tb = kb < ka;
+        k[t] = tb ? kb : ka;
+        if (t + 1 < VV) {  // after the last output the range may be empty
+          i += tb ? 0 : 1;
+          j -= tb ? 1 : 0;
+          const K nk = sk[sk_i<K>(tb ? j : i)];
+          ka = tb ? ka : nk;
+          kb = tb ? nk : kb;
+        }
+      }
+    }
+    sync(2 * sp);  // the pair's reads are done before its writes
+    if (lt < P) {
+      // The merged run is the next round's B (stored descending) when its
+      // index is odd and a next round exists: k[t] goes to a0 + d + t, or
+      // to a0 + 2L - 1 - d - t.
+      const bool desc = (g & 1) && 4 * sp <= P;
+      const int base = desc ? sk_i<K>(a0 + 2 * L - 1 - d) : sk_i<K>(a0 + d);
+      const int step = desc ? -1 : 1;
+#pragma unroll
+      for (int t = 0; t < VV; ++t) sk[base + t * step] = k[t];
+    }
+    if (2 * sp < P) sync(4 * sp);  // the next round's pairs see the writes
+  }
+}
+
 template <class K, bool HV, bool CNT, int LT = NT, int VV = V>
 __device__ void block_sort_tile(TileSmem<K, HV, LT, VV> s, uint64_t& cmp, int P = LT) {
   // P (a power of two <= LT): threads holding data; items beyond the data
   // are padding keys, so the first P*VV items end up sorted.
+  if constexpr (!HV) {
+    __syncthreads();
+    tile_sort_keys<K, CNT, VV>(s.k, static_cast<int>(threadIdx.x), P,
+                               [](int t) { tile_sync<LT>(t); }, cmp);
+    __syncthreads();  // the whole sorted tile is visible to the block
+    return;
+  }
   const int tid = threadIdx.x;
   K k[VV];
   uint32_t v[VV];
