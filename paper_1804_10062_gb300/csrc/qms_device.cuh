@@ -642,6 +642,38 @@ __device__ uint64_t merge_path_halfwarp(const K* A, uint64_t la, const K* B, uin
   const unsigned lane = threadIdx.x & 31u, g = lane & 15u, half = lane >> 4;
   uint64_t lo = d > lb ? d - lb : 0;
   uint64_t hi = d < la ? d : la;
+  {
+    // First a round that tries the window of +-delta around the answer's
+    // guess d * la / (la + lb), delta = 4 sqrt(d) + 64 (on random keys the
+    // answer strays from the guess by about sqrt(d) / 2): when the guess is
+    // good the 16-probe rounds start from that window, else from one side.
+    const uint64_t delta = 4 * static_cast<uint64_t>(sqrtf(static_cast<float>(d))) + 64;
+    const bool use = hi > lo && hi - lo > 64 * delta;
+    bool p = false;
+    uint64_t m1 = 0, m2 = 0;
+    if (use) {
+      uint64_t gs = static_cast<uint64_t>(static_cast<double>(d) * la / static_cast<double>(la + lb));
+      gs = gs < lo ? lo : (gs >= hi ? hi - 1 : gs);
+      m1 = gs > lo + delta ? gs - delta : lo;
+      m2 = gs + delta < hi ? gs + delta : hi - 1;
+      const uint64_t m = g == 0 ? m1 : m2;
+      if (g < 2) {
+        if (CNT) ++cmp;
+        p = !(enc_key(B[d - 1 - m], xf) < enc_key(A[m], xf));
+      }
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, p) >> (half * 16u);
+    if (use) {
+      if (!(bal & 1u)) {
+        hi = m1;
+      } else if (bal & 2u) {
+        lo = m2 + 1;
+      } else {
+        lo = m1 + 1;
+        hi = m2;
+      }
+    }
+  }
   bool done = !(hi > lo);
   while (__any_sync(0xffffffffu, !done)) {
     uint64_t step = 1;

@@ -201,11 +201,32 @@ __global__ void __launch_bounds__(MBT, MergeCfg<K, HV>::MINB)
 // inside [lo, hi]: three probes per step, whose six loads are issued
 // together, narrow the window four-fold, so a window of w takes about
 // log4(w) dependent round trips (a binary search takes log2(w)).
+//
+// With delta > 0 a first round tries the window [g - delta, g + delta]
+// around a guess g of the answer (its two probes' loads issued together):
+// the window shrinks to it when the guess is good, else to one side of it.
 template <class K, bool CNT>
 __device__ __forceinline__ uint64_t merge_path_lane4(const K* A, const K* B, uint64_t d,
                                                      uint64_t lo, uint64_t hi, int xf,
-                                                     uint64_t& cmp) {
+                                                     uint64_t& cmp, uint64_t g = 0,
+                                                     uint64_t delta = 0) {
   // P(m) = !(B[d-1-m] < A[m]) holds below the answer and fails from it on.
+  if (delta > 0 && hi > lo && hi - lo > 4 * delta) {
+    g = g < lo ? lo : (g >= hi ? hi - 1 : g);
+    const uint64_t m1 = g > lo + delta ? g - delta : lo;
+    const uint64_t m2 = g + delta < hi ? g + delta : hi - 1;
+    const bool p1 = !(enc_key(B[d - 1 - m1], xf) < enc_key(A[m1], xf));
+    const bool p2 = !(enc_key(B[d - 1 - m2], xf) < enc_key(A[m2], xf));
+    if (CNT) cmp += 2;
+    if (!p1) {
+      hi = m1;
+    } else if (p2) {
+      lo = m2 + 1;
+    } else {
+      lo = m1 + 1;
+      hi = m2;
+    }
+  }
   while (hi - lo >= 4) {
     const uint64_t q = (hi - lo) / 4;
     const uint64_t m1 = lo + q, m2 = m1 + q, m3 = m2 + q;  // all < hi
@@ -272,14 +293,21 @@ __device__ __forceinline__ void split_group(const K* keys, uint64_t X, uint64_t 
     const K* B = A + g.la;
     const uint64_t d = g.d0;
     uint64_t lo = d > g.lb ? d - g.lb : 0, hi = d < g.la ? d : g.la;
+    // guess of the answer: the split at the same fraction of the group's
+    // advance as at its ends, else the runs' proportion
+    uint64_t guess = static_cast<uint64_t>(static_cast<double>(d) * g.la /
+                                           static_cast<double>(g.la + g.lb));
+    uint64_t delta = 4 * static_cast<uint64_t>(sqrtf(static_cast<float>(d))) + 64;
     if (grouped) {
       const uint64_t lo2 = (a1 > d1 - d) ? a1 - (d1 - d) : 0;
       const uint64_t hi2 = a0 + (d - d0);
       const uint64_t l3 = a0 > lo2 ? a0 : lo2, h3 = a1 < hi2 ? a1 : hi2;
       lo = lo > l3 ? lo : l3;
       hi = hi < h3 ? hi : h3;
+      guess = a0 + (a1 - a0) * (d - d0) / (d1 - d0);
+      delta = 256;
     }
-    splits[t] = merge_path_lane4<K, CNT>(A, B, d, lo, hi, xf, cmp);
+    splits[t] = merge_path_lane4<K, CNT>(A, B, d, lo, hi, xf, cmp, guess, delta);
   }
 }
 
