@@ -694,9 +694,10 @@ def run_qms(args):
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for i in range(args.steps):
-        # the plain API: each call returns once its sort has finished (arrays
-        # this large run their rounds from the host; smaller ones as one
-        # device-driven CUDA graph)
+        # the plain API: each call returns once its sort has finished (a
+        # waiting call of 2^16 keys or more runs its rounds from the host,
+        # every kernel launched with a programmatic dependency on the one
+        # before it)
         q.qms_sort(bufs[i], pivot=args.pivot, dtype=args.dtype)
     e1.record(stream)
     torch.cuda.synchronize()
@@ -739,8 +740,9 @@ def run_qms(args):
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                 "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
                 "timing": "CUDA events around every launch, in a profiled pass of the same K "
-                          "sorts run right after the timed region (the timed pass runs the same "
-                          "kernels inside one CUDA graph per sort)",
+                          "sorts run right after the timed region (the timed pass launches the "
+                          "same kernels from the host loop without events, each with a "
+                          "programmatic dependency on the one before it)",
                 "traffic": (tpb * per_launch_alg) if tpb is not None else None,
                 "alg_bytes_per_launch": per_launch_alg,
                 "kernels": {k: {"ms": round(v["ms"] / args.steps, 4),

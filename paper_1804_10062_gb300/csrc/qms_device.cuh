@@ -969,6 +969,12 @@ __device__ __forceinline__ void exchange_ranks(K* keys, uint32_t* vals, uint64_t
 // one per 128-thread block, so that many blocks per SM keep loads in flight.
 
 constexpr int PNT = 128;        // threads per partition block
+// Resident blocks per SM the local-partition kernels are built for (4-byte
+// keys without payloads: 40 registers, 12 blocks).
+template <class K, bool HV>
+constexpr int part_minb() {
+  return sizeof(K) == 4 ? (HV ? 5 : 12) : (HV ? 4 : 6);
+}
 constexpr int PT = PNT * V;     // keys per partition tile
 constexpr int PNWARP = PNT / 32;
 

@@ -294,7 +294,7 @@ __global__ void k_g_mom_place(DState* S) {
 
 // Partition pass over [lo, hi) (mode le), grid striding over partition tiles.
 template <class K, bool HV, bool CNT>
-__global__ void __launch_bounds__(PNT) k_g_part_local(DState* S) {
+__global__ void __launch_bounds__(PNT, (part_minb<K, HV>())) k_g_part_local(DState* S) {
   count_launch(S);
   DState& s = *S;
   if (!s.active) return;

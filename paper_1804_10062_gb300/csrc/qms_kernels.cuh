@@ -255,7 +255,7 @@ __global__ void k_mom_place(K* keys, uint32_t* vals, uint64_t b, uint64_t e, uin
 // Step 1: local partition of every partition tile (PT keys, PNT threads),
 // left count per tile.
 template <class K, bool HV, bool CNT>
-__global__ void __launch_bounds__(PNT) k_part_local(K* keys, uint32_t* vals, uint64_t lo, uint64_t hi,
+__global__ void __launch_bounds__(PNT, (part_minb<K, HV>())) k_part_local(K* keys, uint32_t* vals, uint64_t lo, uint64_t hi,
                                                     int le, int xf, Desc* desc, uint32_t* counts) {
   grid_dep_wait();
   grid_dep_trigger();
