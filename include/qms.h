@@ -169,10 +169,11 @@ int qms_sort_batched(void* d_keys, uint32_t* d_vals, const uint64_t* d_offsets, 
 /* ---- Batched form: plan and autotuner ------------------------------------
  * qms_sort_batched maps every segment length bin b (segments of
  * (2^(b-1), 2^b] keys, b < QMS_BATCH_BINS; b = 0 holds single keys) to a
- * kernel configuration.  Configurations QMS_BCFG_G32 .. QMS_BCFG_G512W sort
- * a segment that fits their tile with the base case (Fig. 3's driver never
- * partitions a range of one tile or less) inside one group of threads --
- * a warp, or a block-sized group -- several groups per block;
+ * kernel configuration.  The group configurations (QMS_BCFG_G32 ..
+ * QMS_BCFG_G512W and QMS_BCFG_G1024W) sort a segment that fits their tile
+ * with the base case (Fig. 3's driver never partitions a range of one tile
+ * or less) inside one group of threads -- a warp, or a block-sized group --
+ * several groups per block up to 512 threads;
  * QMS_BCFG_QMS runs the QuickMergesort rounds of a segment in one block.
  * Segments longer than 2^(QMS_BATCH_BINS-1) keys always take the rounds.
  * The default plan takes, per bin, the smallest group whose tile holds it.
@@ -182,7 +183,7 @@ int qms_sort_batched(void* d_keys, uint32_t* d_vals, const uint64_t* d_offsets, 
  *   $QMS_AUTOTUNE_DIR/batched_k<4|8>_v<0|1>_sm<count>.json
  * (default directory $HOME/.cache/qms_gb300), which later processes read on
  * their first batched call.  The paper has no batched form. */
-#define QMS_BATCH_BINS 15
+#define QMS_BATCH_BINS 16
 #define QMS_BCFG_G32 0    /* one warp, 16 keys per thread: up to 512 keys   */
 #define QMS_BCFG_G64 1    /* 64 threads x 16: up to 1024                    */
 #define QMS_BCFG_G128 2   /* 128 x 16: up to 2048                           */
@@ -191,6 +192,8 @@ int qms_sort_batched(void* d_keys, uint32_t* d_vals, const uint64_t* d_offsets, 
 #define QMS_BCFG_G256W 5  /* 256 x 32: up to 8192 (4-byte keys, no payload) */
 #define QMS_BCFG_G512W 6  /* 512 x 32: up to 16384 (4-byte keys, no payload)*/
 #define QMS_BCFG_QMS 7    /* one block per segment, QuickMergesort rounds   */
+#define QMS_BCFG_G1024W 8 /* 1024 x 32, one group per block: up to 32768
+                             (4-byte keys, no payload)                      */
 
 /* Times every configuration per length bin on the current device (about a
  * second of GPU work), installs the fastest plan for (dtype's key width,

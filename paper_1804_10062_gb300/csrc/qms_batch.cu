@@ -8,16 +8,17 @@
 namespace qms {
 
 int batch_cfg_threads(int c) {
-  static const int t[BC_COUNT] = {32, 64, 128, 256, 512, 256, 512, NT};
+  static const int t[BC_COUNT] = {32, 64, 128, 256, 512, 256, 512, NT, 1024};
   return (c >= 0 && c < BC_COUNT) ? t[c] : 0;
 }
 int batch_cfg_keys_per_thread(int c) {
-  static const int v[BC_COUNT] = {V, V, V, V, V, 2 * V, 2 * V, V};
+  static const int v[BC_COUNT] = {V, V, V, V, V, 2 * V, 2 * V, V, 2 * V};
   return (c >= 0 && c < BC_COUNT) ? v[c] : 0;
 }
 const char* batch_cfg_name(int c) {
   static const char* n[BC_COUNT] = {"group32x16", "group64x16", "group128x16", "group256x16",
-                                    "group512x16", "group256x32", "group512x32", "block_qms"};
+                                    "group512x16", "group256x32", "group512x32", "block_qms",
+                                    "group1024x32"};
   return (c >= 0 && c < BC_COUNT) ? n[c] : "invalid";
 }
 
@@ -26,18 +27,19 @@ namespace {
 template <class K, bool HV, bool CNT, int GT, int VV>
 cudaError_t launch_one(void* keys, uint32_t* vals, const uint64_t* offsets, const uint32_t* order,
                        uint32_t nseg, unsigned int* ticket, int xf, Desc* desc, cudaStream_t st) {
-  constexpr size_t smem = group_smem_bytes<K, HV, GT, VV>() * (NT / GT);
+  constexpr int BT = group_block_threads(GT);
+  constexpr size_t smem = group_smem_bytes<K, HV, GT, VV>() * (BT / GT);
   auto f = k_batched_group<K, HV, CNT, GT, VV>;
   cudaError_t e = smem_attr(reinterpret_cast<const void*>(f), smem);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0, occ = 0;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, f, NT, smem)) != cudaSuccess) return e;
-  const uint64_t groups = (nseg + (NT / GT) - 1) / (NT / GT);
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, f, BT, smem)) != cudaSuccess) return e;
+  const uint64_t groups = (nseg + (BT / GT) - 1) / (BT / GT);
   const uint64_t resident = static_cast<uint64_t>(sms) * (occ > 0 ? occ : 1);
   const unsigned grid = static_cast<unsigned>(groups < resident ? (groups > 0 ? groups : 1) : resident);
-  f<<<grid, NT, smem, st>>>(static_cast<K*>(keys), vals, offsets, order, nseg, ticket, xf, desc);
+  f<<<grid, BT, smem, st>>>(static_cast<K*>(keys), vals, offsets, order, nseg, ticket, xf, desc);
   return cudaGetLastError();
 }
 
@@ -58,6 +60,8 @@ cudaError_t launch_typed(int c, void* keys, uint32_t* vals, const uint64_t* offs
       return launch_one<K, HV, CNT, 256, 2 * V>(keys, vals, offsets, order, nseg, ticket, xf, desc, st);
     if (c == BC_G512W)
       return launch_one<K, HV, CNT, 512, 2 * V>(keys, vals, offsets, order, nseg, ticket, xf, desc, st);
+    if (c == BC_G1024W)
+      return launch_one<K, HV, CNT, 1024, 2 * V>(keys, vals, offsets, order, nseg, ticket, xf, desc, st);
   }
   return cudaErrorInvalidValue;
 }

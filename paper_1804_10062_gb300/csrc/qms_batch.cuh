@@ -1,5 +1,5 @@
 // Batched form, short segments: thread groups of GT threads (GT a power of
-// two, 32 = one warp, up to one 512-thread block) each sort one segment of
+// two, 32 = one warp, up to one 1024-thread block) each sort one segment of
 // at most GT * VV keys by themselves, entirely in shared memory.  A segment
 // that short is finished by QuickMergesort's base case (the driver loop of
 // Fig. 3, arXiv 1804.10062, never partitions a range of one leaf tile or
@@ -13,6 +13,9 @@
 #include "qms_kernels.cuh"
 
 namespace qms {
+
+// Threads of a block of groups of GT threads: NT, or one group of GT > NT.
+__host__ __device__ constexpr int group_block_threads(int GT) { return GT > NT ? GT : NT; }
 
 // Barrier of the GT threads of group g of a block: the warp for GT = 32,
 // named barrier 1 + g otherwise (at most 8 groups of at least 64 threads in
@@ -48,7 +51,16 @@ __device__ __forceinline__ void group_sort_seg(K* g, uint32_t* gv, int cnt, K* s
   }
   group_sync<GT>(grp);
   if constexpr (!HV) {
-    tile_sort_keys<K, CNT, VV>(sk, lt, P, [grp](int) { group_sync<GT>(grp); }, cmp);
+    // run pairs of at most 32 threads lie within one warp
+    tile_sort_keys<K, CNT, VV>(
+        sk, lt, P,
+        [grp](int t) {
+          if (t <= 32)
+            __syncwarp();
+          else
+            group_sync<GT>(grp);
+        },
+        cmp);
     group_sync<GT>(grp);  // the last round's writes are visible
   } else {
     K k[VV];
@@ -98,11 +110,10 @@ __device__ __forceinline__ void group_sort_seg(K* g, uint32_t* gv, int cnt, K* s
 // One launch per length bin: groups take segments order[0, nseg) from an
 // atomic ticket (the host lists a bin's segments longest first).
 template <class K, bool HV, bool CNT, int GT, int VV>
-__global__ void __launch_bounds__(NT) k_batched_group(K* keys, uint32_t* vals,
-                                                      const uint64_t* offsets, const uint32_t* order,
-                                                      uint32_t nseg, unsigned int* ticket, int xf,
-                                                      Desc* desc) {
-  constexpr int NG = NT / GT;
+__global__ void __launch_bounds__(group_block_threads(GT))
+    k_batched_group(K* keys, uint32_t* vals, const uint64_t* offsets, const uint32_t* order,
+                    uint32_t nseg, unsigned int* ticket, int xf, Desc* desc) {
+  constexpr int NG = group_block_threads(GT) / GT;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ uint32_t gseg[NG];
   const int grp = threadIdx.x / GT, lt = threadIdx.x % GT;

@@ -24,12 +24,13 @@ enum BatchCfg : int {
   BC_G256W,     // 256 x 32: up to 8192 (4-byte keys without payloads)
   BC_G512W,     // 512 x 32: up to 16384 (4-byte keys without payloads)
   BC_QMS,       // one block per segment, QuickMergesort rounds (any length)
+  BC_G1024W,    // 1024 x 32: up to 32768 (4-byte keys without payloads)
   BC_COUNT
 };
 
-// Length bins: bin b holds the segments of (2^(b-1), 2^b] keys, b <= 14;
+// Length bins: bin b holds the segments of (2^(b-1), 2^b] keys, b <= 15;
 // longer segments always take BC_QMS (or the grid driver).
-constexpr int BATCH_BINS = 15;
+constexpr int BATCH_BINS = 16;
 
 int batch_cfg_threads(int c);
 int batch_cfg_keys_per_thread(int c);
@@ -39,7 +40,7 @@ inline int batch_cfg_capacity(int c) {
 // Whether configuration c exists for keys of ksize bytes (with payloads: hv).
 inline bool batch_cfg_valid(int c, int ksize, bool hv) {
   if (c < 0 || c >= BC_COUNT) return false;
-  if (c == BC_G256W || c == BC_G512W) return ksize == 4 && !hv;
+  if (c == BC_G256W || c == BC_G512W || c == BC_G1024W) return ksize == 4 && !hv;
   return true;
 }
 const char* batch_cfg_name(int c);

@@ -1039,8 +1039,8 @@ BatchPlan default_plan(int ksize, bool hv) {
   BatchPlan p{};
   for (int b = 0; b < BATCH_BINS; ++b) {
     int best = BC_QMS;
-    for (int c = 0; c < BC_QMS; ++c) {
-      if (!batch_cfg_valid(c, ksize, hv) || batch_cfg_capacity(c) < (1 << b)) continue;
+    for (int c = 0; c < BC_COUNT; ++c) {
+      if (c == BC_QMS || !batch_cfg_valid(c, ksize, hv) || batch_cfg_capacity(c) < (1 << b)) continue;
       if (best == BC_QMS || batch_cfg_capacity(c) < batch_cfg_capacity(best)) best = c;
     }
     p.cfg[b] = best;

@@ -7,7 +7,8 @@ import os
 import pytest
 
 CAPACITY = {"group32x16": 512, "group64x16": 1024, "group128x16": 2048, "group256x16": 4096,
-            "group512x16": 8192, "group256x32": 8192, "group512x32": 16384}
+            "group512x16": 8192, "group256x32": 8192, "group512x32": 16384,
+            "group1024x32": 32768}
 
 
 @pytest.fixture(scope="module")
@@ -20,7 +21,7 @@ def q():
 def _default(q, wide):
     out = []
     for b in range(q.QMS_BATCH_BINS):
-        fits = [c for c in q.BATCH_CONFIGS[:-1] if CAPACITY[c] >= (1 << b)
+        fits = [c for c in q.BATCH_CONFIGS if c in CAPACITY and CAPACITY[c] >= (1 << b)
                 and (wide or not c.endswith("x32"))]
         out.append(min(fits, key=lambda c: (CAPACITY[c], q.BATCH_CONFIGS.index(c)))
                    if fits else "block_qms")
@@ -53,10 +54,11 @@ def test_plan_file_round_trip(q, tmp_path):
 def test_plan_file_entries_that_do_not_fit_keep_the_default(q, tmp_path):
     p = tmp_path / "bad.json"
     lines = ['{"key_bytes": 8, "payload": 0, "sm_count": 152,', ' "bins": [']
-    for b in range(15):
+    nb = q.QMS_BATCH_BINS
+    for b in range(nb):
         cfg = "group512x32" if b == 10 else ("group32x16" if b == 12 else "group512x16")
         lines.append('  {"bin": %d, "max_len": %d, "config": "%s", "ns_per_key": 0.1}%s'
-                     % (b, 1 << b, cfg, "," if b < 14 else ""))
+                     % (b, 1 << b, cfg, "," if b < nb - 1 else ""))
     lines.append(" ]}")
     p.write_text("\n".join(lines) + "\n")
     got, found = q.qms_batched_plan_read(str(p), "u64", False, 152)
