@@ -170,7 +170,7 @@ int qms_sort_batched(void* d_keys, uint32_t* d_vals, const uint64_t* d_offsets, 
  * qms_sort_batched maps every segment length bin b (segments of
  * (2^(b-1), 2^b] keys, b < QMS_BATCH_BINS; b = 0 holds single keys) to a
  * kernel configuration.  The group configurations (QMS_BCFG_G32 ..
- * QMS_BCFG_G512W and QMS_BCFG_G1024W) sort a segment that fits their tile
+ * QMS_BCFG_G512W, QMS_BCFG_G1024W, QMS_BCFG_PAIR) sort a segment that fits their tile
  * with the base case (Fig. 3's driver never partitions a range of one tile
  * or less) inside one group of threads -- a warp, or a block-sized group --
  * several groups per block up to 512 threads;
@@ -183,7 +183,7 @@ int qms_sort_batched(void* d_keys, uint32_t* d_vals, const uint64_t* d_offsets, 
  *   $QMS_AUTOTUNE_DIR/batched_k<4|8>_v<0|1>_sm<count>.json
  * (default directory $HOME/.cache/qms_gb300), which later processes read on
  * their first batched call.  The paper has no batched form. */
-#define QMS_BATCH_BINS 16
+#define QMS_BATCH_BINS 17
 #define QMS_BCFG_G32 0    /* one warp, 16 keys per thread: up to 512 keys   */
 #define QMS_BCFG_G64 1    /* 64 threads x 16: up to 1024                    */
 #define QMS_BCFG_G128 2   /* 128 x 16: up to 2048                           */
@@ -194,6 +194,9 @@ int qms_sort_batched(void* d_keys, uint32_t* d_vals, const uint64_t* d_offsets, 
 #define QMS_BCFG_QMS 7    /* one block per segment, QuickMergesort rounds   */
 #define QMS_BCFG_G1024W 8 /* 1024 x 32, one group per block: up to 32768
                              (4-byte keys, no payload)                      */
+#define QMS_BCFG_PAIR 9   /* a cluster of two 1024 x 32 blocks, merged through
+                             distributed shared memory: up to 65536 (4-byte
+                             keys, no payload)                              */
 
 /* Times every configuration per length bin on the current device (about a
  * second of GPU work), installs the fastest plan for (dtype's key width,

@@ -8,17 +8,17 @@
 namespace qms {
 
 int batch_cfg_threads(int c) {
-  static const int t[BC_COUNT] = {32, 64, 128, 256, 512, 256, 512, NT, 1024};
+  static const int t[BC_COUNT] = {32, 64, 128, 256, 512, 256, 512, NT, 1024, 1024};
   return (c >= 0 && c < BC_COUNT) ? t[c] : 0;
 }
 int batch_cfg_keys_per_thread(int c) {
-  static const int v[BC_COUNT] = {V, V, V, V, V, 2 * V, 2 * V, V, 2 * V};
+  static const int v[BC_COUNT] = {V, V, V, V, V, 2 * V, 2 * V, V, 2 * V, 2 * V};
   return (c >= 0 && c < BC_COUNT) ? v[c] : 0;
 }
 const char* batch_cfg_name(int c) {
   static const char* n[BC_COUNT] = {"group32x16", "group64x16", "group128x16", "group256x16",
                                     "group512x16", "group256x32", "group512x32", "block_qms",
-                                    "group1024x32"};
+                                    "group1024x32", "pair1024x32"};
   return (c >= 0 && c < BC_COUNT) ? n[c] : "invalid";
 }
 
@@ -43,6 +43,36 @@ cudaError_t launch_one(void* keys, uint32_t* vals, const uint64_t* offsets, cons
   return cudaGetLastError();
 }
 
+// The two-block cluster configuration: as many clusters as fit the GPU at
+// once (at most one per two segments' worth of work), each looping over
+// segments from the ticket.
+template <class K, bool CNT>
+cudaError_t launch_pair(void* keys, const uint64_t* offsets, const uint32_t* order, uint32_t nseg,
+                        unsigned int* ticket, int xf, Desc* desc, cudaStream_t st) {
+  constexpr size_t smem = group_smem_bytes<K, false, PAIR_T, PAIR_VV>();
+  auto f = k_batched_pair<K, CNT>;
+  cudaError_t e = smem_attr(reinterpret_cast<const void*>(f), smem);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.blockDim = dim3(PAIR_T);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int clusters = 0;
+  cfg.gridDim = dim3(2);
+  if ((e = cudaOccupancyMaxActiveClusters(&clusters, f, &cfg)) != cudaSuccess) return e;
+  if (clusters < 1) return cudaErrorInvalidConfiguration;
+  const unsigned nc = nseg < static_cast<uint32_t>(clusters) ? nseg : static_cast<unsigned>(clusters);
+  cfg.gridDim = dim3(2 * nc);
+  return cudaLaunchKernelEx(&cfg, f, static_cast<K*>(keys), offsets, order, nseg, ticket, xf, desc);
+}
+
 template <class K, bool HV, bool CNT>
 cudaError_t launch_typed(int c, void* keys, uint32_t* vals, const uint64_t* offsets,
                          const uint32_t* order, uint32_t nseg, unsigned int* ticket, int xf,
@@ -62,6 +92,7 @@ cudaError_t launch_typed(int c, void* keys, uint32_t* vals, const uint64_t* offs
       return launch_one<K, HV, CNT, 512, 2 * V>(keys, vals, offsets, order, nseg, ticket, xf, desc, st);
     if (c == BC_G1024W)
       return launch_one<K, HV, CNT, 1024, 2 * V>(keys, vals, offsets, order, nseg, ticket, xf, desc, st);
+    if (c == BC_PAIR) return launch_pair<K, CNT>(keys, offsets, order, nseg, ticket, xf, desc, st);
   }
   return cudaErrorInvalidValue;
 }

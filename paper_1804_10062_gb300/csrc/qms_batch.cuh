@@ -10,6 +10,8 @@
 // (qms_batched_autotune).
 #pragma once
 
+#include <cooperative_groups.h>
+
 #include "qms_kernels.cuh"
 
 namespace qms {
@@ -134,6 +136,97 @@ __global__ void __launch_bounds__(group_block_threads(GT))
       group_sort_seg<K, HV, CNT, GT, VV>(keys + b, HV ? vals + b : nullptr, cnt, sk, sv, lt, grp, xf,
                                          cmp);
   }
+  if (CNT) flush_count(cmp, &desc->cmp);
+}
+
+// Segments of (PH, 2 PH] keys, PH = 32768, 4-byte keys without payloads:
+// a cluster of two 1024-thread blocks.  Block r sorts part r of the segment
+// (its first PH keys, or the rest) in its own shared memory with the base
+// case; then every thread merges 32 outputs of the whole segment, reading
+// both sorted parts through distributed shared memory (block r produces
+// outputs [r PH, r PH + PH)), and the block writes its outputs back.  Rank
+// 0 takes the segment from the ticket.  Both blocks pass every cluster
+// barrier the same number of times: they read the same ticket value and
+// leave the loop together, and meet once more before either exits.
+constexpr int PAIR_T = 1024;           // threads per block
+constexpr int PAIR_VV = 2 * V;         // keys per thread
+constexpr int PAIR_H = PAIR_T * PAIR_VV;  // keys per block (32768)
+
+template <class K, bool CNT>
+__global__ void __launch_bounds__(PAIR_T, 1)
+    k_batched_pair(K* keys, const uint64_t* offsets, const uint32_t* order, uint32_t nseg,
+                   unsigned int* ticket, int xf, Desc* desc) {
+  static_assert(sizeof(K) == 4, "4-byte keys");
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ uint32_t seg_t;
+  K* sk = reinterpret_cast<K*>(smem);
+  const unsigned rank = cluster.block_rank();
+  const int tid = threadIdx.x;
+  uint64_t cmp = 0;
+  while (true) {
+    if (rank == 0 && tid == 0) seg_t = atomicAdd(ticket, 1u);
+    cluster.sync();
+    const uint32_t t = *cluster.map_shared_rank(&seg_t, 0);
+    if (t >= nseg) break;  // both blocks read the same t
+    const uint32_t sg = order[t];
+    const uint64_t b = offsets[sg];
+    const int n = static_cast<int>(offsets[sg + 1] - b);
+    const int la = n < PAIR_H ? n : PAIR_H;  // part 0
+    const int lb = n - la;                   // part 1
+    const int cnt = rank == 0 ? la : lb;
+    K* g = keys + b + (rank == 0 ? 0 : PAIR_H);
+    int P = 1;
+    while (P * PAIR_VV < cnt) P <<= 1;
+    for (int i = tid; i < P * PAIR_VV; i += PAIR_T) sk[sk_i<K>(i)] = i < cnt ? enc_key(g[i], xf) : key_max<K>();
+    __syncthreads();
+    tile_sort_keys<K, CNT, PAIR_VV>(sk, tid, P, [](int th) { tile_sync<PAIR_T>(th); }, cmp);
+    cluster.sync();  // both parts sorted and visible to the cluster
+    // merge outputs [d, d + VV) of the segment: A = part 0, B = part 1
+    const int d = static_cast<int>(rank) * PAIR_H + tid * PAIR_VV;
+    K k[PAIR_VV];
+    if (d < n) {
+      const K* sA = cluster.map_shared_rank(sk, 0);
+      const K* sB = cluster.map_shared_rank(sk, 1);
+      int lo = d > lb ? d - lb : 0, hi = d < la ? d : la;
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (CNT) ++cmp;
+        if (!(sB[sk_i<K>(d - 1 - mid)] < sA[sk_i<K>(mid)])) lo = mid + 1; else hi = mid;
+      }
+      int ai = lo, bi = d - lo;
+      K ka = ai < la ? sA[sk_i<K>(ai)] : key_max<K>();
+      K kb = bi < lb ? sB[sk_i<K>(bi)] : key_max<K>();
+#pragma unroll
+      for (int j = 0; j < PAIR_VV; ++j) {
+        const bool a_ok = ai < la, b_ok = bi < lb;
+        if (CNT && a_ok && b_ok) ++cmp;
+        const bool tb = b_ok && (!a_ok || kb < ka);
+        k[j] = tb ? kb : ka;
+        if (tb) {
+          ++bi;
+          kb = bi < lb ? sB[sk_i<K>(bi)] : key_max<K>();
+        } else {
+          ++ai;
+          ka = ai < la ? sA[sk_i<K>(ai)] : key_max<K>();
+        }
+      }
+    }
+    cluster.sync();  // every read of both parts is done
+    if (d < n) {
+      const int base = sk_i<K>(tid * PAIR_VV);
+#pragma unroll
+      for (int j = 0; j < PAIR_VV; ++j) sk[base + j] = k[j];
+    }
+    __syncthreads();
+    const int outn = rank == 0 ? la : lb;
+    for (int i = tid; i < outn; i += PAIR_T) g[i] = dec_key(sk[sk_i<K>(i)], xf);
+    __syncthreads();  // the tile is free for the next segment
+  }
+  // Rank 1 has read the last ticket from rank 0's shared memory before
+  // rank 0 may exit.
+  cluster.sync();
   if (CNT) flush_count(cmp, &desc->cmp);
 }
 

@@ -25,22 +25,24 @@ enum BatchCfg : int {
   BC_G512W,     // 512 x 32: up to 16384 (4-byte keys without payloads)
   BC_QMS,       // one block per segment, QuickMergesort rounds (any length)
   BC_G1024W,    // 1024 x 32: up to 32768 (4-byte keys without payloads)
+  BC_PAIR,      // a cluster of two 1024 x 32 blocks: up to 65536 (4-byte keys, no payloads)
   BC_COUNT
 };
 
-// Length bins: bin b holds the segments of (2^(b-1), 2^b] keys, b <= 15;
+// Length bins: bin b holds the segments of (2^(b-1), 2^b] keys, b <= 16;
 // longer segments always take BC_QMS (or the grid driver).
-constexpr int BATCH_BINS = 16;
+constexpr int BATCH_BINS = 17;
 
 int batch_cfg_threads(int c);
 int batch_cfg_keys_per_thread(int c);
 inline int batch_cfg_capacity(int c) {
-  return c == BC_QMS ? (1 << 30) : batch_cfg_threads(c) * batch_cfg_keys_per_thread(c);
+  return c == BC_QMS ? (1 << 30)
+                     : batch_cfg_threads(c) * batch_cfg_keys_per_thread(c) * (c == BC_PAIR ? 2 : 1);
 }
 // Whether configuration c exists for keys of ksize bytes (with payloads: hv).
 inline bool batch_cfg_valid(int c, int ksize, bool hv) {
   if (c < 0 || c >= BC_COUNT) return false;
-  if (c == BC_G256W || c == BC_G512W || c == BC_G1024W) return ksize == 4 && !hv;
+  if (c == BC_G256W || c == BC_G512W || c == BC_G1024W || c == BC_PAIR) return ksize == 4 && !hv;
   return true;
 }
 const char* batch_cfg_name(int c);

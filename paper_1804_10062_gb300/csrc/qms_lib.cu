@@ -1365,7 +1365,9 @@ int autotune_typed(cudaStream_t st, char* report, size_t report_len) {
   ck(cudaGetDevice(&dev));
   ck(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   constexpr uint64_t kMaxKeys = 1ull << 24;
-  const uint64_t cap_keys = kMaxKeys + (1ull << 15);
+  // a bin's draw stops at the first total of at least kMaxKeys keys, so it
+  // can pass it by one segment of the last bin, 2^(BATCH_BINS-1) keys
+  const uint64_t cap_keys = kMaxKeys + (1ull << (BATCH_BINS - 1));
   const uint64_t max_seg = kMaxKeys / 2 + 2;
   // one allocation: keys, payloads, offsets, order, descriptor and tickets
   const size_t kb = cap_keys * sizeof(K), vb = HV ? cap_keys * 4 : 0;
@@ -1408,6 +1410,7 @@ int autotune_typed(cudaStream_t st, char* report, size_t report_len) {
     while (off.back() < target && off.size() < max_seg) off.push_back(off.back() + len(rng));
     const uint32_t nseg = static_cast<uint32_t>(off.size() - 1);
     const uint64_t n = off.back();
+    if (n > cap_keys || nseg > max_seg) throw Err{QMS_EINTERNAL};  // the buffers hold them
     std::vector<uint32_t> order(nseg);
     for (uint32_t i = 0; i < nseg; ++i) order[i] = i;
     std::sort(order.begin(), order.end(), [&](uint32_t x, uint32_t y) {

@@ -289,9 +289,9 @@ def qms_mergesort_half(keys, m: int, buf: int, vals=None, stream=None, dtype=Non
     _raise(rc, "qms_mergesort_half")
 
 
-QMS_BATCH_BINS = 16
+QMS_BATCH_BINS = 17
 BATCH_CONFIGS = ["group32x16", "group64x16", "group128x16", "group256x16", "group512x16",
-                 "group256x32", "group512x32", "block_qms", "group1024x32"]
+                 "group256x32", "group512x32", "block_qms", "group1024x32", "pair1024x32"]
 BCFG = {name: i for i, name in enumerate(BATCH_CONFIGS)}
 
 

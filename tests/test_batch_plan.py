@@ -8,7 +8,7 @@ import pytest
 
 CAPACITY = {"group32x16": 512, "group64x16": 1024, "group128x16": 2048, "group256x16": 4096,
             "group512x16": 8192, "group256x32": 8192, "group512x32": 16384,
-            "group1024x32": 32768}
+            "group1024x32": 32768, "pair1024x32": 65536}
 
 
 @pytest.fixture(scope="module")

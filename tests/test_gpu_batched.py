@@ -150,7 +150,7 @@ def test_batched_full_size_sampled(q):
 
 CAPACITY = {"group32x16": 512, "group64x16": 1024, "group128x16": 2048, "group256x16": 4096,
             "group512x16": 8192, "group256x32": 8192, "group512x32": 16384,
-            "group1024x32": 32768}
+            "group1024x32": 32768, "pair1024x32": 65536}
 
 
 def _forced_plan(q, cfg, dtype, payload):
@@ -165,7 +165,7 @@ def test_every_group_configuration_vs_oracle(q, cfg):
     # Lengths across every bin up to the tile and a little beyond.
     L = [0, 1, 2, 3, 5, 16, 17, 31, 32, 33, 100, 511, 512, 513, 1000, 1024, 1025, 2047, 2048,
          2049, 4095, 4096, 4097, 8191, 8192, 8193, 12000, 16384, 16385, 20000, 32767, 32768,
-         32769]
+         32769, 40000, 65535, 65536, 65537]
     L = np.array(L * 3, dtype=np.int64)
     np.random.default_rng(2).shuffle(L)
     off = gen.offsets_of(L)
