@@ -131,6 +131,15 @@ int qms_version(void);
 /* Static string for an error code. */
 const char* qms_error_string(int code);
 
+/* Frees, on the current device, the cached instances of the device-driven
+ * sort (one instantiated CUDA graph per key type, payload, counting mode and
+ * pivot rule, each with a workspace for the largest array it has sorted,
+ * about n/27 bytes for at least 2^20 keys) after their last launches have
+ * finished.  An instance another host thread is setting up is kept.  Later
+ * calls build what they need again.  The paper has no counterpart.
+ * Errors: QMS_ECUDA. */
+int qms_release_cached(void);
+
 /* Sorts d_keys[0, n) in place, ascending (the QuickMergesort driver loop of
  * Fig. 3: partition, Mergesort the side left of the midpoint test, continue
  * on the other side; a last range of at most one Mergesort leaf -- 16384

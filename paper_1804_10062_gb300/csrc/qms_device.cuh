@@ -970,10 +970,10 @@ __device__ __forceinline__ void exchange_ranks(K* keys, uint32_t* vals, uint64_t
 
 constexpr int PNT = 128;        // threads per partition block
 // Resident blocks per SM the local-partition kernels are built for (4-byte
-// keys without payloads: 40 registers, 12 blocks).
+// keys without payloads: 48 registers, 10 blocks).
 template <class K, bool HV>
 constexpr int part_minb() {
-  return sizeof(K) == 4 ? (HV ? 5 : 12) : (HV ? 4 : 6);
+  return sizeof(K) == 4 ? (HV ? 5 : 10) : (HV ? 4 : 6);
 }
 constexpr int PT = PNT * V;     // keys per partition tile
 constexpr int PNWARP = PNT / 32;
@@ -1006,7 +1006,9 @@ __device__ __forceinline__ uint32_t pblock_excl_scan(uint32_t x, uint32_t* scrat
 // Local partition of one partition tile g[0, cnt) (cnt <= PT): left keys
 // (key < piv, or key <= piv when le) gathered at the front; returns their
 // number.  Shared: sk (pk_len), sv (pv_len), scratch (PNWARP + 1 words).
-template <class K, bool HV, bool CNT>
+// FULL: cnt == PT (every tile but a range's last), no per-element bound
+// checks.
+template <class K, bool HV, bool CNT, bool FULL = false>
 __device__ __forceinline__ uint32_t part_local_small(K* g, uint32_t* gv, int cnt, K piv, bool le,
                                                      int xf, K* sk, uint32_t* sv, uint32_t* scratch,
                                                      uint64_t& cmp) {
@@ -1016,7 +1018,7 @@ __device__ __forceinline__ uint32_t part_local_small(K* g, uint32_t* gv, int cnt
 #pragma unroll
   for (int j = 0; j < V; ++j) {
     const int i = j * PNT + threadIdx.x;
-    if (i < cnt) {
+    if (FULL || i < cnt) {
       x[j] = g[i];
       if (HV) y[j] = gv[i];
     }
@@ -1025,15 +1027,16 @@ __device__ __forceinline__ uint32_t part_local_small(K* g, uint32_t* gv, int cnt
 #pragma unroll
     for (int j = 0; j < V; ++j) {
       const int i = j * PNT + threadIdx.x;
-      if (i < cnt) {
+      if (FULL || i < cnt) {
         const K u = enc_key(x[j], xc);
         const bool l = le ? !(piv < u) : (u < piv);
         flags |= static_cast<uint32_t>(l) << j;
         lc += l;
-        ++nc;
+        if (!FULL) ++nc;
       }
     }
   });
+  if (FULL) nc = V;
   if (CNT) cmp += nc;
   uint32_t tot;
   const uint32_t ex = pblock_excl_scan(lc | ((nc - lc) << 16), scratch, &tot);
@@ -1043,18 +1046,21 @@ __device__ __forceinline__ uint32_t part_local_small(K* g, uint32_t* gv, int cnt
 #pragma unroll
   for (int j = 0; j < V; ++j) {
     const int i = j * PNT + threadIdx.x;
-    if (i < cnt) {
+    if (FULL || i < cnt) {
       const uint32_t dst = ((flags >> j) & 1u) ? offL++ : offR++;
       sk[sk_i<K>(dst)] = x[j];
       if (HV) sv[sv_i(dst)] = y[j];
     }
   }
   __syncthreads();
+  // element j * PNT + t sits at padded index j * (PNT + PNT / PE) + pad(t)
+  constexpr int PE = 128 / static_cast<int>(sizeof(K));
+  const int pt = static_cast<int>(threadIdx.x) + static_cast<int>(threadIdx.x) / PE;
 #pragma unroll
   for (int j = 0; j < V; ++j) {
     const int i = j * PNT + threadIdx.x;
-    if (i < cnt) {
-      g[i] = sk[sk_i<K>(i)];
+    if (FULL || i < cnt) {
+      g[i] = sk[pt + j * (PNT + PNT / PE)];
       if (HV) gv[i] = sv[sv_i(i)];
     }
   }

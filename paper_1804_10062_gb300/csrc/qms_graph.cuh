@@ -309,8 +309,11 @@ __global__ void __launch_bounds__(PNT, (part_minb<K, HV>())) k_g_part_local(DSta
     const uint64_t off = t * PT;
     const int cnt = static_cast<int>((n - off) < static_cast<uint64_t>(PT) ? (n - off) : PT);
     __syncthreads();
-    const uint32_t c = part_local_small<K, HV, CNT>(keys + lo + off, HV ? s.vals + lo + off : nullptr,
-                                                    cnt, piv, s.le != 0, s.xf, sk, sv, scr, cmp);
+    K* const g = keys + lo + off;
+    uint32_t* const gv = HV ? s.vals + lo + off : nullptr;
+    const uint32_t c =
+        cnt == PT ? part_local_small<K, HV, CNT, true>(g, gv, cnt, piv, s.le != 0, s.xf, sk, sv, scr, cmp)
+                  : part_local_small<K, HV, CNT>(g, gv, cnt, piv, s.le != 0, s.xf, sk, sv, scr, cmp);
     if (threadIdx.x == 0) {
       s.counts[t] = c;
       atomicAdd(&s.desc->L, static_cast<unsigned long long>(c));

@@ -269,8 +269,11 @@ __global__ void __launch_bounds__(PNT, (part_minb<K, HV>())) k_part_local(K* key
     const uint64_t off = t * PT;
     const int cnt = static_cast<int>((n - off) < static_cast<uint64_t>(PT) ? (n - off) : PT);
     __syncthreads();
-    const uint32_t c = part_local_small<K, HV, CNT>(keys + lo + off, HV ? vals + lo + off : nullptr, cnt,
-                                                    piv, le != 0, xf, sk, sv, scr, cmp);
+    K* const g = keys + lo + off;
+    uint32_t* const gv = HV ? vals + lo + off : nullptr;
+    const uint32_t c =
+        cnt == PT ? part_local_small<K, HV, CNT, true>(g, gv, cnt, piv, le != 0, xf, sk, sv, scr, cmp)
+                  : part_local_small<K, HV, CNT>(g, gv, cnt, piv, le != 0, xf, sk, sv, scr, cmp);
     if (threadIdx.x == 0) {
       counts[t] = c;
       atomicAdd(&desc->L, static_cast<unsigned long long>(c));

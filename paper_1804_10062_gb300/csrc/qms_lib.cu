@@ -1569,6 +1569,37 @@ extern "C" {
 
 int qms_version(void) { return 10000; }
 
+int qms_release_cached(void) {
+  try {
+    int dev = 0;
+    ck(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(g_graph_mu);
+    for (auto& kv : g_graphs) {
+      if (std::get<5>(kv.first) != dev) continue;
+      auto& pool = kv.second;
+      std::vector<GraphInst*> keep;
+      for (GraphInst* gi : pool) {
+        if (gi->busy) {  // another thread is setting up a sort with it
+          keep.push_back(gi);
+          continue;
+        }
+        if (gi->used) ck(cudaEventSynchronize(gi->done));
+        if (gi->exec) ck(cudaGraphExecDestroy(gi->exec));
+        if (gi->graph) ck(cudaGraphDestroy(gi->graph));
+        if (gi->ws) ck(cudaFree(gi->ws));
+        ck(cudaFree(gi->d_state));
+        ck(cudaFreeHost(gi->h_state));
+        ck(cudaEventDestroy(gi->done));
+        delete gi;
+      }
+      pool.swap(keep);
+    }
+    return QMS_OK;
+  } catch (const Err& e) {
+    return e.code;
+  }
+}
+
 const char* qms_error_string(int code) {
   switch (code) {
     case QMS_OK: return "ok";

@@ -89,6 +89,7 @@ def lib():
             sig = {
                 "qms_version": ([], i),
                 "qms_error_string": ([i], ctypes.c_char_p),
+                "qms_release_cached": ([], i),
                 "qms_sort": ([vp, sz, i, ctypes.POINTER(qms_options), vp, ctypes.POINTER(qms_stats)], i),
                 "qms_sort_pairs": ([vp, vp, sz, i, ctypes.POINTER(qms_options), vp,
                                     ctypes.POINTER(qms_stats)], i),
@@ -127,6 +128,12 @@ def lib():
 
 def error_string(code: int) -> str:
     return lib().qms_error_string(code).decode()
+
+
+def qms_release_cached():
+    """Frees the device-driven sort's cached graph instances and workspaces
+    on the current device (later calls rebuild them)."""
+    _raise(lib().qms_release_cached(), "qms_release_cached")
 
 
 def _dtype_code(t, dtype):

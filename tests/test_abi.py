@@ -20,7 +20,7 @@ def test_header_declares_entry_points():
     for want in ("qms_sort", "qms_sort_pairs", "qms_tile_sort", "qms_partition", "qms_mergesort",
                  "qms_mergesort_half", "qms_sort_batched", "qms_server_create",
                  "qms_server_submit", "qms_server_poll", "qms_server_destroy",
-                 "qms_sort_noalloc"):
+                 "qms_sort_noalloc", "qms_release_cached"):
         assert want in names, want
 
 

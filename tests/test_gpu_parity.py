@@ -319,6 +319,18 @@ def test_host_driven_driver_matches_oracle(q, pivot, dtype):
     assert st2["rounds"] >= 1 and st2["launches"] > 0
 
 
+def test_release_cached_then_sort_again(q):
+    # The device-driven sort's cached instances can be freed between calls;
+    # the next call builds a new one.
+    for rep in range(2):
+        k = gen.keys("uniform", "u32", (1 << 18) + rep, 31 + rep)
+        d = _dev(k)
+        q.qms_sort(d, dtype="u32", wait=False)
+        q.qms_release_cached()  # waits for that sort's launch, then frees
+        assert _host(d, "u32").tobytes() == oracle.reference_sorted(k).tobytes()
+    q.qms_release_cached()  # nothing cached: still fine
+
+
 def test_async_sorts_growing_and_two_streams(q):
     # Back-to-back sorts whose sizes grow (the reused instance's workspace is
     # replaced while its previous sort may still run) on two streams at once.
