@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the batched and served forms")
+    ap.add_argument("--forms", default="batched,served",
+                    help="which of the batched and served forms to run (comma list)")
     ap.add_argument("--no-configs", action="store_true",
                     help="skip the per-configuration records (C1-C3 workloads)")
     ap.add_argument("--batched-segments", type=int, default=65536)
@@ -851,8 +853,12 @@ def run_qms(args):
         bufs, work = [], None
         torch.cuda.empty_cache()
         ranks = Ranks(ws, rank, dist)
-        forms = {"batched": bench_batched(args, q, torch, np, ranks),
-                 "served": bench_served(args, q, torch, np, ranks)}
+        which = [f.strip() for f in args.forms.split(",") if f.strip()]
+        forms = {}
+        if "batched" in which:
+            forms["batched"] = bench_batched(args, q, torch, np, ranks)
+        if "served" in which:
+            forms["served"] = bench_served(args, q, torch, np, ranks)
 
     if rank == 0:
         line = {"metric": METRIC,
