@@ -178,12 +178,14 @@ int qms_sort_batched(void* d_keys, uint32_t* d_vals, const uint64_t* d_offsets, 
 /* ---- Batched form: plan and autotuner ------------------------------------
  * qms_sort_batched maps every segment length bin b (segments of
  * (2^(b-1), 2^b] keys, b < QMS_BATCH_BINS; b = 0 holds single keys) to a
- * kernel configuration.  The group configurations (QMS_BCFG_G32 ..
- * QMS_BCFG_G512W, QMS_BCFG_G1024W, QMS_BCFG_PAIR) sort a segment that fits their tile
+ * kernel configuration.  The group configurations QMS_BCFG_G32 ..
+ * QMS_BCFG_G512W and QMS_BCFG_G1024W sort a segment that fits their tile
  * with the base case (Fig. 3's driver never partitions a range of one tile
- * or less) inside one group of threads -- a warp, or a block-sized group --
- * several groups per block up to 512 threads;
- * QMS_BCFG_QMS runs the QuickMergesort rounds of a segment in one block.
+ * or less) inside one group of threads -- a warp, or a block-sized group;
+ * groups of at most 512 threads share a block.  QMS_BCFG_PAIR sorts the two
+ * halves of a segment in a cluster of two blocks and merges them through
+ * distributed shared memory.  QMS_BCFG_QMS runs the QuickMergesort rounds
+ * of a segment in one block.
  * Segments longer than 2^(QMS_BATCH_BINS-1) keys always take the rounds.
  * The default plan takes, per bin, the smallest group whose tile holds it.
  * The autotuner times every admissible configuration per bin on the
