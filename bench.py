@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--batched-segments", type=int, default=65536)
     ap.add_argument("--served-requests", type=int, default=20000)
     ap.add_argument("--served-lg-max", type=float, default=26.0)
+    ap.add_argument("--served-workers", type=int, default=8,
+                    help="worker threads (one stream each) of the request server")
     ap.add_argument("--served-loads", default="0.5,0.8,0.95",
                     help="offered loads as fractions of the plain FIFO throughput")
     return ap.parse_args()
@@ -431,7 +433,7 @@ def bench_served(args, q, torch, np, ranks):
     def run(rate_gkeys):
         ranks.barrier()
         lam = None if rate_gkeys is None else rate_gkeys * 1e9 / mean_n
-        srv = q.QmsServer(budget, max_slots=1024, workers=4, max_batch=4096)
+        srv = q.QmsServer(budget, max_slots=1024, workers=args.served_workers, max_batch=4096)
         tickets, live, infos = [], [], {}
         head = 0
         rng = np.random.default_rng(9)
