@@ -16,8 +16,12 @@ the worst-case bound of Sec. 4, the Fig. 1 worked example and a library sort;
 for the median-of-medians machinery of Sec. 4: the median of five on every
 permutation and tied word, the selection against the order statistic and the
 BFPRT discard bound (tight on a constructed input), the 2 floor(n/6) pivot
-rank of every MoM round, the 2n/3 partition, the hybrid's switching rule; and
-for the move counter, closed forms of Fig. 3's moves on reverse input).
+rank of every MoM round, the 2n/3 partition, the hybrid's switching rule;
+for the move counter, closed forms of Fig. 3's moves on reverse input; for
+the four-way swap-merge Mergesort of Sec. 6's future work: every small
+permutation, buffer preservation, comparisons equal to an independent
+two-level merge sort, an exact move recurrence and the lg(n!) average
+bound).
 """
 from __future__ import annotations
 
@@ -102,6 +106,12 @@ def lib():
             L.qms_ref_out_x_u32.argtypes = [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_size_t,
                                             ctypes.c_size_t, ctypes.c_int, ctypes.c_size_t, u64p]
             L.qms_ref_out_x_u32.restype = ctypes.c_int
+            L.qms_ref_sort4_u32.argtypes = [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int,
+                                            ctypes.c_int, u64p, u64p, u64p]
+            L.qms_ref_sort4_u32.restype = ctypes.c_int
+            L.qms_ref_msort4_u32.argtypes = [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_size_t,
+                                             ctypes.c_size_t, ctypes.c_int, ctypes.c_int, u64p, u64p]
+            L.qms_ref_msort4_u32.restype = ctypes.c_int
             _lib = L
     return _lib
 
@@ -165,6 +175,35 @@ def out_moves_u32(a: np.ndarray, b: int, e: int, temp: int, mode: str = "analysi
                                      ctypes.byref(m))
     if rc != 0:
         raise RuntimeError("qms_ref_out_moves_u32 failed: %d" % rc)
+    return c.value, m.value
+
+
+def sort4_u32(keys: np.ndarray, variant: str = "m3", mode: str = "analysis"):
+    """QuickMergesort whose Mergesort step is the four-way swap-merge (the
+    multi-way merging of Sec. 6) on uint32 ``keys``, in place.
+
+    Returns ``(comparisons, rounds, moves)``.
+    """
+    assert keys.dtype == np.uint32 and keys.flags.c_contiguous
+    c, r, m = ctypes.c_uint64(0), ctypes.c_uint64(0), ctypes.c_uint64(0)
+    rc = lib().qms_ref_sort4_u32(keys.ctypes.data, len(keys), VARIANTS[variant], MODES[mode],
+                                 ctypes.byref(c), ctypes.byref(r), ctypes.byref(m))
+    if rc != 0:
+        raise RuntimeError("qms_ref_sort4_u32 failed: %d" % rc)
+    return c.value, r.value, m.value
+
+
+def msort4_u32(a: np.ndarray, b: int, n: int, t: int, to_target: bool = False,
+               mode: str = "analysis"):
+    """The four-way swap-merge Mergesort alone on ``a`` (changed in place):
+    ``a[b:b+n]`` sorted in place with the buffer ``a[t:t+n]``, or into
+    ``a[t:t+n]`` with ``to_target``.  Returns ``(comparisons, moves)``."""
+    assert a.dtype == np.uint32 and a.flags.c_contiguous
+    c, m = ctypes.c_uint64(0), ctypes.c_uint64(0)
+    rc = lib().qms_ref_msort4_u32(a.ctypes.data, b, n, t, 1 if to_target else 0, MODES[mode],
+                                  ctypes.byref(c), ctypes.byref(m))
+    if rc != 0:
+        raise RuntimeError("qms_ref_msort4_u32 failed: %d" % rc)
     return c.value, m.value
 
 

@@ -30,6 +30,12 @@
 //     block with X = CleverQuicksort (median-of-3 quicksort: the same sort3,
 //     Lomuto partition and recursion on both sides), then moves it into its
 //     target; the paper's QMQS takes x_thresh near sqrt(n).
+//   * The multi-way merging that Sec. 6 names as future work, as an option:
+//     a four-way swap-merge Mergesort in the full-buffer form (four parts
+//     sorted into the other region, merged back by a tournament over the
+//     pairs (0, 1) and (2, 3), each output swapped with a buffer element
+//     through one hole), and QuickMergesort with it as the Mergesort step
+//     (the side with a buffer at least as large as itself is sorted).
 //   * The MoM details of Sec. 4 as an option ("faithful" MoM): adaptive
 //     selection inside the median-of-medians routine, and a partition of
 //     only the 2n/3 elements that are not medians of triples (the medians
@@ -165,6 +171,8 @@ class QuickMergesort {
 
   uint64_t comparisons() const { return cmps_; }
   uint64_t rounds() const { return rounds_; }
+  // 2: Fig. 3's two-way Mergesort; 4: the four-way swap-merge (Sec. 6).
+  void set_kway(int k) { kway_ = k; }
   std::vector<RoundRec>* round_log = nullptr;  // filled when set
   std::vector<SelRec>* select_log = nullptr;   // filled when set
 
@@ -194,7 +202,10 @@ class QuickMergesort {
       }
       const size_t nl = s.lt - b, nr = e - s.gt;
       bool left;
-      if (s.mom || side_ == 1) {
+      if (kway_ == 4 && (s.mom || side_ == 1 || s.gt != s.lt + 1)) {
+        // The four-way Mergesort takes a buffer as large as its input.
+        left = nl <= nr;
+      } else if (s.mom || side_ == 1) {
         // Larger side if its ceil(m/2) buffer fits in the other side.
         const size_t big = std::max(nl, nr), small = std::min(nl, nr);
         const bool big_fits = (big + 1) / 2 <= small;
@@ -212,10 +223,10 @@ class QuickMergesort {
                                       cmps_ - c0 - part, part, left ? 1u : 0u});
       }
       if (left) {
-        out(b, s.lt, s.gt);
+        if (kway_ == 4) msort4_in(b, s.lt - b, s.gt); else out(b, s.lt, s.gt);
         b = s.gt;
       } else {
-        out(s.gt, e, b);
+        if (kway_ == 4) msort4_in(s.gt, e - s.gt, b); else out(s.gt, e, b);
         e = s.lt;
       }
     }
@@ -224,6 +235,44 @@ class QuickMergesort {
     } else if (e - b == 2) {
       if (lt(a_[b + 1], a_[b])) std::swap(a_[b], a_[b + 1]);
     }
+  }
+
+  // Four-way swap-merge Mergesort (the multi-way merging that Sec. 6 names
+  // as future work), in the full-buffer form: the buffer has as many slots
+  // as the input.  A range is cut into four parts of n/4 elements (the first
+  // n mod 4 parts one more); the parts are sorted into the other region and
+  // merged back by a four-way merge whose every output takes the place of a
+  // buffer element, which moves into the slot the output came from.
+  //
+  // msort4_in: sorts a[b, b + n) in place; a[t, t + n) is the buffer (its
+  // contents are permuted).  msort4_to: sorts a[b, b + n) into a[t, t + n);
+  // the old buffer contents end up in a[b, b + n).  Base: in "paper" mode
+  // insertion sort below 10 elements, else single elements.
+  void msort4_in(size_t b, size_t n, size_t t) {
+    const size_t leaf = (mode_ == PAPER) ? 10 : 2;
+    if (n < leaf) {
+      if (mode_ == PAPER) insertion_sort(b, b + n);
+      return;
+    }
+    size_t off[5];
+    quarters(n, off);
+    for (int i = 0; i < 4; ++i) msort4_to(b + off[i], off[i + 1] - off[i], t + off[i]);
+    merge4(t, off, b);
+  }
+  void msort4_to(size_t b, size_t n, size_t t) {
+    const size_t leaf = (mode_ == PAPER) ? 10 : 2;
+    if (n < leaf) {
+      if (mode_ == PAPER) insertion_sort(b, b + n);
+      if (n > 0) {
+        size_t off1[5] = {0, n, n, n, n};  // one run: a plain block move
+        merge4(b, off1, t);
+      }
+      return;
+    }
+    size_t off[5];
+    quarters(n, off);
+    for (int i = 0; i < 4; ++i) msort4_in(b + off[i], off[i + 1] - off[i], t + off[i]);
+    merge4(b, off, t);
   }
 
   // Internal Mergesort of a[b, e) using the ceil(n/2) slots at a[temp, ...)
@@ -262,6 +311,53 @@ class QuickMergesort {
       ++i1;
     }
     a_[i1 - 1] = temp;
+  }
+
+  // Part boundaries of a four-way split of n: off[0] = 0 <= ... <= off[4] = n.
+  static void quarters(size_t n, size_t off[5]) {
+    off[0] = 0;
+    for (int i = 0; i < 4; ++i) off[i + 1] = off[i] + n / 4 + (static_cast<size_t>(i) < n % 4 ? 1 : 0);
+  }
+
+  // Four-way merge: run i is a[s + off[i], s + off[i+1]); the n = off[4]
+  // outputs go to a[d, d + n), which holds buffer elements (disjoint from the
+  // runs).  Each output moves into the hole left by the previous step and
+  // the next buffer element moves into the consumed run slot (one hole, as
+  // in Fig. 3's merge: two moves per output).  The smallest head is found by
+  // a tournament over the pairs (0, 1) and (2, 3): after an output only the
+  // consumed run's pair and the final match are replayed, one comparison
+  // each while both sides have elements left; equal keys go to the lower
+  // run.
+  void merge4(size_t s, const size_t off[5], size_t d) {
+    const size_t n = off[4];
+    if (n == 0) return;
+    size_t h[4], end[4];
+    for (int i = 0; i < 4; ++i) {
+      h[i] = s + off[i];
+      end[i] = s + off[i + 1];
+    }
+    auto alive = [&](int i) { return i >= 0 && h[i] != end[i]; };
+    auto match = [&](int x, int y) {  // winner of runs x < y (or -1)
+      const bool ax = alive(x), ay = alive(y);
+      if (ax && ay) return lt(a_[h[y]], a_[h[x]]) ? y : x;
+      return ax ? x : (ay ? y : -1);
+    };
+    int w01 = match(0, 1), w23 = match(2, 3);
+    int win = match_winners(w01, w23, h, end);
+    E temp = a_[d];
+    for (size_t p = 0; p < n; ++p) {
+      const size_t src = h[win]++;
+      a_[d + p] = a_[src];
+      a_[src] = (p + 1 < n) ? a_[d + p + 1] : temp;
+      if (p + 1 == n) break;
+      if (win < 2) w01 = match(0, 1); else w23 = match(2, 3);
+      win = match_winners(w01, w23, h, end);
+    }
+  }
+  int match_winners(int x, int y, const size_t* h, const size_t* end) {
+    const bool ax = x >= 0 && h[x] != end[x], ay = y >= 0 && h[y] != end[y];
+    if (ax && ay) return lt(a_[h[y]], a_[h[x]]) ? y : x;
+    return ax ? x : (ay ? y : -1);
   }
 
   // Fig. 3 "msort": sorts a[b, e) into a[t, t + n); the old target contents
@@ -542,6 +638,7 @@ class QuickMergesort {
   Less less_;
   int variant_, mode_, side_, mom_;
   size_t x_thresh_;
+  int kway_ = 2;
   uint64_t cmps_ = 0;
   uint64_t rounds_ = 0;
   uint64_t part_cmps_ = 0;  // comparisons of the last MoM round's partition
@@ -662,6 +759,46 @@ int qms_ref_moves_u32(uint32_t* keys, size_t n, int variant, int mode, int side,
   if (n > 1) s.sort(0, n);
   const uint64_t mv = CountedU32::moves;
   for (size_t i = 0; i < n; ++i) keys[i] = e[i].v;
+  if (cmps) *cmps = s.comparisons();
+  if (moves) *moves = mv;
+  return 0;
+}
+
+// QuickMergesort with the four-way swap-merge Mergesort (Sec. 6's
+// multi-way merging) on uint32 keys; comparisons, rounds and element moves
+// (a swap counts three) are reported.
+int qms_ref_sort4_u32(uint32_t* keys, size_t n, int variant, int mode, uint64_t* cmps,
+                      uint64_t* rounds, uint64_t* moves) {
+  if (keys == nullptr && n > 0) return -1;
+  if (variant < 0 || variant > 3 || mode < 0 || mode > 1) return -1;
+  std::vector<CountedU32> e(n);
+  for (size_t i = 0; i < n; ++i) e[i].v = keys[i];
+  CountedU32::moves = 0;
+  QuickMergesort<CountedU32, LessCounted> s(e.data(), LessCounted{}, variant, mode, 0);
+  s.set_kway(4);
+  if (n > 1) s.sort(0, n);
+  const uint64_t mv = CountedU32::moves;
+  for (size_t i = 0; i < n; ++i) keys[i] = e[i].v;
+  if (cmps) *cmps = s.comparisons();
+  if (rounds) *rounds = s.rounds();
+  if (moves) *moves = mv;
+  return 0;
+}
+
+// The four-way Mergesort alone: a[b, b + n) sorted in place with the buffer
+// a[t, t + n) (to_target = 0), or into a[t, t + n) (to_target = 1).
+int qms_ref_msort4_u32(uint32_t* a, size_t b, size_t n, size_t t, int to_target, int mode,
+                       uint64_t* cmps, uint64_t* moves) {
+  if (a == nullptr || mode < 0 || mode > 1) return -1;
+  if (t < b + n && b < t + n) return -1;  // the regions must not overlap
+  const size_t len = std::max(b + n, t + n);
+  std::vector<CountedU32> v(len);
+  for (size_t i = 0; i < len; ++i) v[i].v = a[i];
+  CountedU32::moves = 0;
+  QuickMergesort<CountedU32, LessCounted> s(v.data(), LessCounted{}, M3, mode, 0);
+  if (to_target) s.msort4_to(b, n, t); else s.msort4_in(b, n, t);
+  const uint64_t mv = CountedU32::moves;
+  for (size_t i = 0; i < len; ++i) a[i] = v[i].v;
   if (cmps) *cmps = s.comparisons();
   if (moves) *moves = mv;
   return 0;
